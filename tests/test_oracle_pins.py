@@ -1,0 +1,360 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every expected value comes from a
+closed form, a textbook identity, an independent library routine (SVD least
+squares, normal equations, finite differences, brute-force grids) or a value
+printed in the paper (tests/golden/).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import dls, fit, lbfgs, models, pso, rng, varpro
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def grid(f_lo=1e6, f_hi=1e10, K=200):
+    return W.log_grid(f_lo, f_hi, K)
+
+
+# ---------------------------------------------------------------- targets (Eqs. 3-7)
+
+def test_hn_alpha_beta_one_is_debye():
+    om = grid(1e5, 1e11, 300)
+    hn = models.havriliak_negami(om, 3.0, 12.0, 2e-10, 1.0, 1.0)
+    # Debye written out in real form: eps' = ei + de/(1+x^2), eps'' = de x/(1+x^2)
+    x = om * 2e-10
+    np.testing.assert_allclose(hn.real, 3.0 + 12.0 / (1 + x * x), rtol=1e-15, atol=0)
+    np.testing.assert_allclose(-hn.imag, 12.0 * x / (1 + x * x), rtol=1e-14, atol=0)
+
+
+def test_cole_cole_at_relaxation_frequency():
+    # (1 + j^alpha)^-1 = 1/2 - (j/2) tan(alpha pi / 4) at w tau0 = 1
+    for alpha in (0.3, 0.55, 0.91, 1.0):
+        tau0 = 3.3e-9
+        e = models.cole_cole(np.array([1.0 / tau0]), 2.0, 7.0, tau0, alpha)
+        assert abs(e.real[0] - (2.0 + 3.5)) < 1e-13
+        assert abs(-e.imag[0] - 3.5 * math.tan(alpha * math.pi / 4)) < 1e-13
+
+
+def test_cole_davidson_closed_form():
+    # eps - eps_inf = d_eps cos^beta(phi) exp(-j beta phi), phi = atan(w tau0)
+    om = grid(1e5, 1e11, 100)
+    tau0, beta = 1.7e-9, 0.45
+    e = models.cole_davidson(om, 4.0, 20.0, tau0, beta)
+    phi = np.arctan(om * tau0)
+    ref = 4.0 + 20.0 * np.cos(phi) ** beta * np.exp(-1j * beta * phi)
+    np.testing.assert_allclose(e, ref, rtol=1e-13)
+
+
+def test_hn_real_form():
+    # Textbook modulus/argument form of Eq. 4
+    om = grid(1e5, 1e11, 200)
+    ei, de, tau0, a, b = 2.7, 5.9, 9.4e-10, 0.91, 0.45
+    e = models.havriliak_negami(om, ei, de, tau0, a, b)
+    wt = (om * tau0) ** a
+    rr = 1 + 2 * wt * math.cos(a * math.pi / 2) + wt * wt
+    th = np.arctan2(wt * math.sin(a * math.pi / 2), 1 + wt * math.cos(a * math.pi / 2))
+    np.testing.assert_allclose(e.real, ei + de * rr ** (-b / 2) * np.cos(b * th), rtol=1e-14)
+    np.testing.assert_allclose(-e.imag, de * rr ** (-b / 2) * np.sin(b * th), rtol=1e-13)
+
+
+def test_debye_loss_peak_at_relaxation_frequency():
+    # eps'' peaks at f0 = 1/(2 pi tau0) with value d_eps/2 (Sec. II-B, Fig. 1)
+    tau0 = 0.1e-9
+    f = np.logspace(8, 11, 30001)
+    e = models.debye(2 * math.pi * f, 1.0, 14.0, tau0)
+    k = np.argmax(-e.imag)
+    assert abs(math.log10(f[k]) - math.log10(1 / (2 * math.pi * tau0))) < 2e-4
+    assert abs(-e.imag[k] - 7.0) < 1e-6
+
+
+def test_crim_special_cases():
+    om = grid()
+    water = W.WATER
+    e1 = models.crim(om, [1.0, 0.0, 0.0], [water, W.SAND, W.AIR])
+    np.testing.assert_allclose(e1, models.debye(om, *water), rtol=1e-14)
+    e2 = models.crim(om, [0.3, 0.7], [W.SAND, W.AIR])
+    assert np.allclose(e2, (0.3 * math.sqrt(4.5) + 0.7) ** 2, rtol=1e-14)
+
+
+def test_jonscher_loss_ratio():
+    om = grid(1e6, 1e10, 80)
+    for n in (0.3, 0.6, 0.9):
+        e = models.jonscher(om, 5.0, 3.0, W.OMEGA_P, n)
+        np.testing.assert_allclose(-e.imag / (e.real - 5.0), 1 / math.tan(n * math.pi / 2), rtol=1e-12)
+        e5 = models.jonscher_eq5(om, 5.0, 3.0, W.OMEGA_P, n)
+        np.testing.assert_allclose(-e5.imag / (e5.real - 5.0), math.tan(n * math.pi / 2), rtol=1e-12)
+
+
+def test_synthesize_dispatch_matches_model_functions():
+    b = W.mixed_batch(S=40, seed=3)
+    re, im = models.synthesize(b)
+    for s in range(b.S):
+        a, c = b.offsets[s], b.offsets[s + 1]
+        p = b.params[s]
+        if b.model[s] == W.MODEL_HN:
+            e = models.havriliak_negami(b.omega[a:c], *p[:5])
+            np.testing.assert_array_equal(re[a:c], e.real)
+    assert np.all(im > 0)   # every drawn model is lossy at every frequency
+
+
+# ---------------------------------------------------------------- damped LS cost (Sec. III)
+
+def _debye_sum_target(om, ei, de, tau):
+    e = models.multi_debye(om, ei, de, tau)
+    return models.split(e)
+
+
+def test_undamped_solve_matches_svd_lstsq():
+    om = grid()
+    rng_ = np.random.default_rng(0)
+    re, im = models.split(models.havriliak_negami(om, 3.0, 30.0, 1e-9, 0.7, 0.6))
+    for _ in range(10):
+        th = np.sort(rng_.uniform(-11, -7, 4))
+        A = dls.basis(om, th)
+        b = dls.target(re, im)
+        x = dls.damped_solve(A, b, 0.0)
+        x_ref = np.linalg.lstsq(A, b, rcond=None)[0]   # SVD (gelsd)
+        np.testing.assert_allclose(x, x_ref, rtol=1e-7, atol=1e-9 * np.abs(x_ref).max())
+
+
+def test_damped_cost_is_min_of_augmented_system():
+    # min_x ||A x - b||^2 + lam ||D x||^2 = squared residual of [A; sqrt(lam) D] x ~ [b; 0],
+    # solved independently by SVD least squares
+    om = grid(1e6, 1e10, 120)
+    re, im = models.split(models.havriliak_negami(om, 4.0, 50.0, 3e-10, 0.5, 0.8))
+    rng_ = np.random.default_rng(1)
+    for lam in (1e-3, 1e-5, 1e-1):
+        for _ in range(8):
+            th = rng_.uniform(-12, -6, 5)
+            A = dls.basis(om, th)
+            b = dls.target(re, im)
+            D = np.diag(np.linalg.norm(A, axis=0))
+            aug = np.vstack([A, math.sqrt(lam) * D])
+            xs, *_ = np.linalg.lstsq(aug, np.concatenate([b, np.zeros(A.shape[1])]), rcond=None)
+            ref_min = float(np.sum((aug @ xs - np.concatenate([b, np.zeros(A.shape[1])])) ** 2))
+            x = dls.damped_solve(A, b, lam)
+            if np.all(x[1:] >= 0):
+                assert abs(dls.cost(om, re, im, th, lam) - ref_min) <= 1e-10 * ref_min
+            np.testing.assert_allclose(x, xs, rtol=1e-8, atol=1e-10 * np.abs(xs).max())
+
+
+def test_damped_solve_matches_normal_equations():
+    om = grid(1e6, 1e10, 300)
+    re, im = models.split(models.cole_cole(om, 3.0, 20.0, 1e-9, 0.8))
+    th = np.array([-10.5, -9.0, -7.5])
+    A = dls.basis(om, th)
+    b = dls.target(re, im)
+    G = A.T @ A
+    lam = 1e-3
+    assert np.linalg.cond(G) < 1e4
+    x_ne = np.linalg.solve(G + lam * np.diag(np.diag(G)), A.T @ b)
+    np.testing.assert_allclose(dls.damped_solve(A, b, lam), x_ne, rtol=1e-10)
+
+
+def test_exact_recovery_of_debye_sum():
+    om = grid(1e6, 1e10, 400)
+    tau = np.array([3e-11, 4e-10, 6e-9])
+    de = np.array([5.0, 12.0, 30.0])
+    re, im = _debye_sum_target(om, 2.5, de, tau)
+    c, w = dls.cost(om, re, im, np.log10(tau), 0.0, return_weights=True)
+    b = dls.target(re, im)
+    assert c <= 1e-20 * float(b @ b)
+    np.testing.assert_allclose(w, np.concatenate([[2.5], de]), rtol=1e-9)
+
+
+def test_flip_keeps_eps_inf_sign():
+    # eps_inf < 0 is not a 'negative weight' of a Debye pole: no penalty
+    om = grid(1e6, 1e10, 200)
+    tau = np.array([1e-10, 1e-8])
+    re, im = _debye_sum_target(om, -1.0, np.array([4.0, 9.0]), tau)
+    c = dls.cost(om, re, im, np.log10(tau), 0.0)
+    assert c <= 1e-20 * float(re @ re + im @ im)
+
+
+def test_flip_penalises_negative_weight():
+    # target with a negative pole: the flipped misfit must equal the misfit of |x|
+    om = grid(1e6, 1e10, 200)
+    tau = np.array([1e-10, 1e-8])
+    re, im = _debye_sum_target(om, 3.0, np.array([4.0, -2.0]), tau)
+    b = dls.target(re, im)
+    c = dls.cost(om, re, im, np.log10(tau), 0.0)
+    A = dls.basis(om, np.log10(tau))
+    x_ls = np.linalg.lstsq(A, b, rcond=None)[0]
+    assert x_ls[2] < 0
+    xa = np.array([x_ls[0], abs(x_ls[1]), abs(x_ls[2])])
+    assert abs(c - float(np.sum((A @ xa - b) ** 2))) <= 1e-9 * c
+    # the penalty is 4 x_2^2 ||a_2||^2 (the flipped column's contribution)
+    assert abs(c - 4 * x_ls[2] ** 2 * float(A[:, 2] @ A[:, 2])) <= 1e-7 * c
+
+
+def test_cost_invariances():
+    om = grid(1e6, 1e10, 150)
+    re, im = models.split(models.havriliak_negami(om, 3.0, 25.0, 5e-10, 0.6, 0.7))
+    th = np.array([-10.2, -9.1, -8.3, -7.0])
+    c0 = dls.cost(om, re, im, th, 1e-3)
+    # scaling b by s scales the cost by s^2
+    assert abs(dls.cost(om, 3 * re, 3 * im, th, 1e-3) - 9 * c0) <= 1e-11 * 9 * c0
+    # permuting the poles leaves the cost unchanged
+    assert abs(dls.cost(om, re, im, th[::-1], 1e-3) - c0) <= 1e-11 * c0
+    # w -> c w with tau -> tau / c leaves the cost unchanged
+    assert abs(dls.cost(om * 100.0, re, im, th - 2.0, 1e-3) - c0) <= 1e-9 * c0
+
+
+# ---------------------------------------------------------------- gradient (VarPro)
+
+@pytest.mark.parametrize("lam", [1e-3, 1e-6])
+def test_gradient_matches_central_differences(lam):
+    om = grid(1e6, 1e10, 200)
+    re, im = models.split(models.havriliak_negami(om, 3.0, 25.0, 5e-10, 0.6, 0.7))
+    rng_ = np.random.default_rng(5)
+    n_flip = 0
+    for _ in range(20):
+        th = rng_.uniform(-12, -6, 4)
+        x = dls.damped_solve(dls.basis(om, th), dls.target(re, im), lam)
+        if np.min(np.abs(x[1:])) < 1e-8:
+            continue
+        n_flip += bool(np.any(x[1:] < 0))
+        c, g = varpro.cost_grad(om, re, im, th, lam)
+        h = 1e-6
+        fd = np.array([(dls.cost(om, re, im, th + h * e, lam) - dls.cost(om, re, im, th - h * e, lam))
+                       / (2 * h) for e in np.eye(4)])
+        assert np.max(np.abs(g - fd)) <= 1e-6 * max(1.0, np.max(np.abs(fd))) + 1e-6 * c
+    assert n_flip > 0   # the penalised branch was exercised
+
+
+def test_gradient_zero_at_exact_fit():
+    om = grid(1e6, 1e10, 300)
+    tau = np.array([2e-10, 5e-9])
+    re, im = _debye_sum_target(om, 2.0, np.array([6.0, 10.0]), tau)
+    c, g = varpro.cost_grad(om, re, im, np.log10(tau), 0.0)
+    assert c < 1e-18 and np.max(np.abs(g)) < 1e-7
+
+
+# ---------------------------------------------------------------- random numbers
+
+def test_splitmix64_reference_outputs():
+    vals = [int(l, 16) for l in open(os.path.join(GOLDEN, "splitmix64.txt"))
+            if l.strip() and not l.startswith("#")]
+    state = 0
+    for v in vals:
+        assert rng.mix(state) == v   # mix(state) = output of a generator at 'state'
+        state = (state + 0x9E3779B97F4A7C15) & rng.MASK
+
+
+def test_uniform_array_matches_scalar():
+    u = rng.uniform_array(7, rng.TAG_R1, 3, 11, 5, 4)
+    for p in range(5):
+        for d in range(4):
+            assert u[p, d] == rng.uniform(7, rng.TAG_R1, 3, 11, p, d)
+    big = rng.uniform_array(0, 1, 0, 0, 1000, 20)
+    assert 0.0 <= big.min() and big.max() < 1.0 and abs(big.mean() - 0.5) < 0.01
+
+
+# ---------------------------------------------------------------- search
+
+def test_pso_finds_quadratic_minimum():
+    target = np.array([-9.3, -7.7])
+    def f(th):
+        return np.sum((th - target) ** 2, axis=1)
+    pbx, pbc, gi, trace = pso.pso(f, 2, -13, -5, 32, 200, seed=1)
+    assert np.all(np.diff(trace) <= 0)
+    np.testing.assert_allclose(pbx[gi], target, atol=1e-4)
+
+
+def test_lbfgs_box_quadratic_and_bound():
+    Q = np.array([[3.0, 1.0], [1.0, 2.0]])
+    c = np.array([-9.0, -8.0])
+    def fg(t):
+        d = t - c
+        return float(d @ Q @ d), 2 * Q @ d
+    th, f, _ = lbfgs.polish(fg, np.array([-12.0, -12.0]), -13, -5, iters=100)
+    np.testing.assert_allclose(th, c, atol=1e-6)
+    # minimiser outside the box: lands on the bound
+    th2, _, _ = lbfgs.polish(lambda t: (float((t + 4.0) @ (t + 4.0)), 2 * (t + 4.0)),
+                             np.array([-12.0, -10.0]), -13, -5, iters=100)
+    np.testing.assert_allclose(th2, [-5.0, -5.0], atol=1e-9)
+
+
+def _brute_force_n1(om, re, im, lam):
+    from scipy.optimize import minimize_scalar
+    th = np.linspace(-13, -6, 7001)
+    c, _ = dls.cost_population(om, re, im, th[:, None], lam, chunk=2048)
+    k = int(np.argmin(c))
+    res = minimize_scalar(lambda t: float(dls.cost(om, re, im, np.array([t]), lam)),
+                          bracket=(th[max(k - 1, 0)], th[k], th[min(k + 1, 7000)]),
+                          method="golden", tol=1e-10)
+    return min(float(res.fun), float(c[k]))
+
+
+def _brute_force_n2(om, re, im, lam, n=301):
+    from scipy.optimize import minimize
+    t = np.linspace(-13, -6, n)
+    a, b = np.meshgrid(t, t, indexing="ij")
+    m = a <= b
+    cand = np.stack([a[m], b[m]], axis=1)
+    c, _ = dls.cost_population(om, re, im, cand, lam, chunk=4096)
+    best = float(np.min(c))
+    for k in np.argsort(c)[:5]:
+        res = minimize(lambda x: float(dls.cost(om, re, im, x, lam)), cand[k], method="Nelder-Mead",
+                       options={"xatol": 1e-9, "fatol": 1e-14, "maxiter": 4000})
+        best = min(best, float(res.fun))
+    return best
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_search_reaches_brute_force_minimum(N):
+    b = W.single_hn(K=50, N=N)
+    re, im = models.synthesize(b)
+    lam = dls.LAM_SEARCH
+    bf = _brute_force_n1(b.omega, re, im, lam) if N == 1 else _brute_force_n2(b.omega, re, im, lam)
+    r = fit.fit_spectrum(b.omega, re, im, N, -13.0, -6.0, 64, 100, topk=8)
+    assert r["cost_search"] <= (1 + 1e-6) * bf
+
+
+def test_fit_is_passive_and_sorted():
+    b = W.single_hn()
+    re, im = models.synthesize(b)
+    r = fit.fit_spectrum(b.omega, re, im, 3, -13.0, -6.0, 64, 60, topk=4)
+    assert np.all(r["d_eps"] >= 0) and np.all(np.diff(r["tau"]) >= 0)
+    om = W.log_grid(1e6, 1e12, 2000)
+    e = fit.fitted_eps(om, r)
+    assert np.all(-e.imag >= 0) and np.all(np.diff(e.real) <= 1e-12)
+
+
+# ---------------------------------------------------------------- the paper's worked example
+
+def _listing2():
+    ei, poles = None, []
+    for line in open(os.path.join(GOLDEN, "paper_listing2.txt")):
+        if line.startswith("eps_inf"):
+            ei = float(line.split()[1])
+        elif line.startswith("pole"):
+            poles.append((float(line.split()[1]), float(line.split()[2])))
+    return ei, np.array(poles)
+
+
+def test_paper_example_weights_at_printed_tau():
+    ei, poles = _listing2()
+    pe = W.paper_example(K=1000)
+    re, im = models.synthesize(pe)
+    c, w = dls.cost(pe.omega, re, im, np.log10(poles[:, 1]), 0.0, return_weights=True)
+    assert abs(w[0] - ei) / ei < 0.01
+    assert np.max(np.abs(w[1:] - poles[:, 0]) / poles[:, 0]) < 0.01
+
+
+def test_paper_example_fit_beats_printed_result():
+    ei, poles = _listing2()
+    pe = W.paper_example(K=200)
+    re, im = models.synthesize(pe)
+    lam = dls.LAM_SEARCH
+    printed = float(dls.cost(pe.omega, re, im, np.log10(poles[:, 1]), lam))
+    r = fit.fit_spectrum(pe.omega, re, im, 5, -13.0, -6.0, 64, 100, topk=8)
+    assert r["cost_search"] <= printed
+    # Sec. IV: the PSO-DLS fit of this example stays below 10 % average fractional error
+    assert r["avg_frac_err"] < 10.0
