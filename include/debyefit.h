@@ -1,0 +1,203 @@
+/*
+ * debyefit -- batched multi-Debye fitting of dielectric spectra on GB300 (sm_103a).
+ *
+ * C ABI of libdebyefit.so. The method is the hybrid linear/non-linear fit of
+ * Majchrowska et al., "Modelling Arbitrary Complex Dielectric Properties -- an
+ * automated implementation for gprMax" (arXiv:2109.01928):
+ *   - a target spectrum eps(w) = eps'(w) - j eps''(w)                      (Eq. 1)
+ *     given by a relaxation model (Debye, Havriliak-Negami, Cole-Cole,
+ *     Cole-Davidson, Jonscher, CRIM: Eqs. 3-6) or by tabulated values (Sec. III-A);
+ *   - is approximated by the multi-pole Debye expansion
+ *     eps_inf + sum_n d_eps_n / (1 + j w tau_n)                             (Eq. 7);
+ *   - a global optimiser (particle swarm) searches the relaxation times, and for
+ *     each candidate the weights (eps_inf, d_eps_n) come from damped least squares
+ *     over the real and imaginary parts, with negative weights sign-flipped as a
+ *     penalty (Sec. III-A, III-B);
+ *   - the result is eps_inf and (d_eps_n, tau_n), n = 1..N (Listing 2).
+ *
+ * Conventions for every entry point
+ *   - Array arguments are caller-owned DEVICE memory unless the name ends in
+ *     _host. The library reads and writes them in stream order on `stream` and
+ *     keeps no reference after the call returns.
+ *   - Candidates are log10(tau) vectors theta. A population is theta[S][P][n_max]
+ *     (float64, row-major); entries n >= N_s of spectrum s are ignored.
+ *   - Weights are x = (eps_inf, d_eps_1..d_eps_N) laid out [S][P][n_max+1];
+ *     entries beyond N_s+1 are written as 0.
+ *   - Every call returns a status: DEBYE_OK (0) or a negative DEBYE_E* code. No
+ *     exception or exit crosses the ABI. debye_last_error() describes the last
+ *     failure of a handle. Errors detected on the device (non-finite input, a
+ *     work-list bound violated) are recorded in a device status word and returned
+ *     by the next debye_sync().
+ *   - A candidate whose damped normal matrix is not positive definite gets cost
+ *     +inf; that is a result, not a call error.
+ *   - Calls on one handle must not overlap in time (one host thread at a time);
+ *     different handles are independent.
+ */
+#ifndef DEBYEFIT_H
+#define DEBYEFIT_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define DEBYE_OK          0
+#define DEBYE_EINVAL     -1   /* bad argument (null pointer, size, bounds, N) */
+#define DEBYE_ECUDA      -2   /* a CUDA runtime call failed */
+#define DEBYE_ENOMEM     -3   /* device workspace allocation failed */
+#define DEBYE_ETIMEOUT   -4   /* a bounded device-side wait gave up */
+#define DEBYE_EINTERNAL  -5   /* inconsistent internal state */
+#define DEBYE_ENOTFINITE -6   /* non-finite frequency or target value on the device */
+#define DEBYE_EBOUNDS    -7   /* a device-side index check failed */
+
+/* ------------------------------------------------------------------ precision */
+#define DEBYE_PREC_FP64  0    /* FP64 basis, Gram, solve and residual */
+#define DEBYE_PREC_MIXED 1    /* FP32 basis and Gram, FP64 solve, float-float residual */
+
+#define DEBYE_MAX_POLES 20    /* largest N accepted */
+
+/* ------------------------------------------------------------------ models (target synthesis) */
+#define DEBYE_MODEL_DEBYE        0  /* Eq. 3 */
+#define DEBYE_MODEL_HN           1  /* Eq. 4 */
+#define DEBYE_MODEL_CC           2  /* Eq. 4, beta = 1 */
+#define DEBYE_MODEL_CD           3  /* Eq. 4, alpha = 1 */
+#define DEBYE_MODEL_JONSCHER     4  /* eps_inf + a_p (w/w_p)^(n-1) [1 - j cot(n pi/2)] */
+#define DEBYE_MODEL_JONSCHER_EQ5 5  /* Eq. 5 as printed: eps_inf + A_p (-j w/w_p)^n */
+#define DEBYE_MODEL_CRIM         6  /* Eq. 6 over up to 3 Debye components */
+#define DEBYE_MODEL_DEBYE_SUM    7  /* Eq. 7 source poles + Jonscher tail + noise */
+#define DEBYE_N_PARAMS          16  /* float64 parameter record per spectrum */
+
+typedef struct debye_ctx* debye_handle;
+
+/* Solver options. debye_default_options() fills the documented defaults. */
+typedef struct {
+  int32_t precision;      /* DEBYE_PREC_FP64 or DEBYE_PREC_MIXED (default MIXED) */
+  int32_t refine_steps;   /* refinement passes after the first solve, 1..4 (default 1) */
+  double  lam_search;     /* Marquardt damping of search and polish (default 1e-3) */
+  double  lam_final;      /* damping of the reported weights (default 1e-3 = lam_search) */
+  double  pso_omega;      /* swarm inertia (default 0.5) */
+  double  pso_phi_p;      /* cognitive coefficient (default 0.5) */
+  double  pso_phi_g;      /* social coefficient (default 0.5) */
+  int32_t lbfgs_m;        /* L-BFGS history pairs, 1..8 (default 8) */
+  int32_t lbfgs_max_trials; /* backtracking halvings per iteration, 1..40 (default 20) */
+  double  lbfgs_c1;       /* Armijo constant (default 1e-4) */
+  int32_t cands_per_block;/* candidates per thread block, 32..128, multiple of 32; 0 = autotune */
+  int32_t use_graphs;     /* capture the generation and polish loops in CUDA graphs (default 1) */
+} debye_options;
+
+/* A ragged batch of S spectra, CSR over frequency (all device memory unless _host). */
+typedef struct {
+  int64_t        S;          /* number of spectra, >= 0 */
+  const int64_t* offsets;    /* [S+1]; spectrum s owns samples offsets[s] .. offsets[s+1]-1 */
+  const double*  omega;      /* [offsets[S]] angular frequency (rad/s), > 0 */
+  const double*  eps_re;     /* [offsets[S]] eps'  (Eq. 1) */
+  const double*  eps_im;     /* [offsets[S]] eps'' (Eq. 1; a lossy sample has eps'' > 0) */
+  const int32_t* n_poles;    /* [S] Debye poles N_s to fit, 1..DEBYE_MAX_POLES */
+  const double*  lo;         /* [S] lower bound of log10(tau) */
+  const double*  hi;         /* [S] upper bound of log10(tau), > lo */
+  const int64_t* offsets_host;  /* optional host copy of offsets (avoids a device read) */
+  const int32_t* n_poles_host;  /* optional host copy of n_poles */
+} debye_spectra;
+
+/* Search settings of debye_fit_batch. */
+typedef struct {
+  int32_t  P;             /* particles per spectrum, 1..32768 */
+  int32_t  iters;         /* swarm generations after the initial one, >= 0 */
+  uint64_t seed;          /* seed of the counter-based generator */
+  int32_t  polish_topk;   /* personal bests polished per spectrum, 0..min(P,64) */
+  int32_t  polish_iters;  /* L-BFGS iterations per polished candidate, >= 0 */
+  double*  trace;         /* optional [S][iters+1] device: global-best cost per generation */
+  double*  evals;         /* optional [1] device: candidate evaluations x K performed */
+} debye_search;
+
+/* Fill *opt with the defaults listed above. */
+void debye_default_options(debye_options* opt);
+
+/* Create a handle on the current CUDA device. opt may be NULL (defaults).
+ * Returns DEBYE_EINVAL for out-of-range options, DEBYE_ECUDA if no device. */
+int debye_fit_init(debye_handle* out, const debye_options* opt);
+
+/* Release a handle and its device workspaces. NULL is accepted. */
+int debye_fit_destroy(debye_handle h);
+
+/* Target synthesis (Eqs. 3-7): write eps', eps'' of every spectrum from its model
+ * id [S] and parameter record params[S][DEBYE_N_PARAMS] (layout per model id:
+ * Debye/HN/CC/CD [eps_inf, d_eps, tau0, alpha, beta]; Jonscher [eps_inf, a_p,
+ * omega_p, n_p]; CRIM [a, m, f_1..f_3, (eps_inf_i, d_eps_i, tau_i) x 3];
+ * Debye sum [eps_inf, a_p, omega_p, n_p, sigma] with source poles
+ * pole_tau/pole_deps over pole_offsets[S+1] and multiplicative noise
+ * eps'(1 + sigma z_re), eps''(1 + sigma z_im), z given in noise_re/noise_im
+ * [offsets[S]] (NULL = no noise)). offsets and omega as in debye_spectra. */
+int debye_synth_targets(debye_handle h, int64_t S, const int64_t* offsets, const double* omega,
+                        const int32_t* model, const double* params, const int64_t* pole_offsets,
+                        const double* pole_tau, const double* pole_deps, const double* noise_re,
+                        const double* noise_im, double* eps_re, double* eps_im,
+                        cudaStream_t stream);
+
+/* DLS cost of a fed-in population (Sec. III-B): for every candidate theta[s][p],
+ * the damped least-squares weights at damping lam_search, the sign flip of
+ * negative d_eps, and cost = ||A x_hat - b||^2 + lam sum_j G_jj x_hat_j^2 over the
+ * stacked real/imaginary rows. cost [S][P]; weights [S][P][n_max+1] or NULL.
+ * n_max >= max_s N_s. */
+int debye_eval_population(debye_handle h, const debye_spectra* spectra, int32_t P, int32_t n_max,
+                          const double* theta, double* cost, double* weights, cudaStream_t stream);
+
+/* Cost (as debye_eval_population) and its exact gradient d cost / d theta
+ * (variable projection, including the flipped case), grad [S][P][n_max]. */
+int debye_cost_grad(debye_handle h, const debye_spectra* spectra, int32_t P, int32_t n_max,
+                    const double* theta, double* cost, double* grad, cudaStream_t stream);
+
+/* Whole fit (Sec. III-B, IV): seeded particle swarm over log10(tau) with DLS
+ * weights, projected L-BFGS polish of the best polish_topk personal bests, the
+ * best result re-solved in FP64 at damping lam_final with the sign flip, poles
+ * sorted by ascending tau. Outputs eps_inf [S], d_eps [S][n_max], tau [S][n_max]
+ * (seconds; entries beyond N_s are 0) and final_cost [S] (cost at lam_final). */
+int debye_fit_batch(debye_handle h, const debye_spectra* spectra, const debye_search* search,
+                    int32_t n_max, double* eps_inf, double* d_eps, double* tau,
+                    double* final_cost, cudaStream_t stream);
+
+/* Wait for `stream`, then return and clear the device status word
+ * (DEBYE_OK, DEBYE_ENOTFINITE, DEBYE_EBOUNDS or DEBYE_ETIMEOUT). */
+int debye_sync(debye_handle h, cudaStream_t stream);
+
+/* ------------------------------------------------------------------ kernel timing
+ * For measurement tools. While enabled, every kernel launch of the evaluation
+ * (Gram pass, residual/refinement pass, gradient pass, FP64 solve and finish) is
+ * bracketed by CUDA events recorded on the stream it is launched on, and CUDA-graph
+ * capture is switched off. Per kernel kind the library accumulates the number of
+ * launches, the summed event time (ms) and the algorithmic FLOPs of the launched
+ * work: per candidate and frequency sample, 4N + 2(N+2)^2 for the Gram pass (basis
+ * build plus the unique Gram/right-hand-side products) and 67N + 25 for the
+ * float-float residual pass (FMA counted as 2). Launches restricted by an
+ * activity mask (the polish line search) count their time but no FLOPs. */
+#define DEBYE_KERNEL_GRAM   0
+#define DEBYE_KERNEL_REFINE 1
+#define DEBYE_KERNEL_GRAD   2
+#define DEBYE_KERNEL_SOLVE  3
+#define DEBYE_KERNEL_FINISH 4
+#define DEBYE_KERNEL_KINDS  5
+
+/* Number of kernel launches the handle has enqueued (a CUDA-graph replay counts
+ * each of its kernel nodes); reset != 0 sets the counter to zero afterwards. */
+int debye_launch_count(debye_handle h, int64_t* count, int32_t reset);
+
+/* Enable (1) or disable (0) kernel timing; enabling clears the totals. */
+int debye_profile_enable(debye_handle h, int32_t enable);
+
+/* Totals of kernel kind `kind` since timing was enabled (waits for the recorded
+ * events). Any output pointer may be NULL. */
+int debye_profile_read(debye_handle h, int32_t kind, int64_t* launches, double* ms, double* flops);
+
+/* Message of the last failed call on h (never NULL; "" if none). */
+const char* debye_last_error(debye_handle h);
+
+/* Library version string. */
+const char* debye_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEBYEFIT_H */

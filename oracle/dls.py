@@ -21,7 +21,10 @@ from __future__ import annotations
 import numpy as np
 
 LAM_SEARCH = 1e-3
-LAM_FINAL = 1e-12
+# The reported weights are the DLS weights of the found relaxation times, at the
+# same damping as the search (an undamped re-solve can turn a nearly repeated
+# pole pair into huge opposite weights that the sign flip then penalises).
+LAM_FINAL = LAM_SEARCH
 
 
 def basis(omega: np.ndarray, theta: np.ndarray) -> np.ndarray:

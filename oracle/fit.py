@@ -4,7 +4,9 @@ Sequence (Sec. III-B, IV): particle swarm over log10(tau) with DLS weights per
 particle (damping LAM_SEARCH), projected L-BFGS polish of the best `topk`
 personal bests (lowest cost first, lowest particle index on ties), the best
 polished candidate (lowest cost, lowest rank on ties) re-solved with damping
-LAM_FINAL and the sign flip, poles sorted by ascending tau. The result is the
+LAM_FINAL (by default the search damping: the reported weights are the DLS
+weights of the found relaxation times) and the sign flip, poles sorted by
+ascending tau. The result is the
 record the paper emits (Listing 2): eps_inf, then (d_eps_n, tau_n).
 """
 from __future__ import annotations

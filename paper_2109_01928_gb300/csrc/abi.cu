@@ -1,0 +1,489 @@
+// Host side of libdebyefit: handle, device workspaces, work-unit scheduling and
+// the C ABI entry points declared in include/debyefit.h.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "host.h"
+
+using namespace debyefit;
+
+// ------------------------------------------------------------------ handle utilities
+int debye_ctx::fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  err = buf;
+  return code;
+}
+
+int debye_ctx::ensure(Buf& b, size_t bytes, const char* what) {
+  if (b.n >= bytes && b.p) return DEBYE_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (capturing_stream) cudaStreamIsCapturing(capturing_stream, &cs);
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(DEBYE_EINTERNAL, "workspace '%s' must grow during stream capture", what);
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.n = 0;
+  size_t want = std::max<size_t>(bytes, 256);
+  if (alloc_hook && alloc_hook(want)) return fail(DEBYE_ENOMEM, "allocation of %zu bytes for '%s' refused", want, what);
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    cudaGetLastError();
+    return fail(DEBYE_ENOMEM, "cudaMalloc(%zu) for '%s': %s", want, what, cudaGetErrorString(e));
+  }
+  b.n = want;
+  return DEBYE_OK;
+}
+
+int debye_ctx::check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(DEBYE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  return DEBYE_OK;
+}
+
+// ------------------------------------------------------------------ kernel timing
+cudaEvent_t debye_ctx::prof_event() {
+  if (!prof_pool.empty()) {
+    cudaEvent_t e = prof_pool.back();
+    prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void debye_ctx::prof_begin(int kind, double flops, cudaStream_t st, ProfEntry& e) {
+  e.kind = kind;
+  e.flops = flops;
+  e.a = prof_event();
+  e.b = prof_event();
+  cudaEventRecord(e.a, st);
+}
+
+void debye_ctx::prof_end(ProfEntry& e, cudaStream_t st) {
+  cudaEventRecord(e.b, st);
+  prof_pending.push_back(e);
+}
+
+int debye_ctx::prof_collect() {
+  int rc = DEBYE_OK;
+  for (ProfEntry& e : prof_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(e.b) != cudaSuccess || cudaEventElapsedTime(&ms, e.a, e.b) != cudaSuccess) {
+      cudaGetLastError();
+      rc = DEBYE_ECUDA;
+    }
+    prof_launches[e.kind] += 1;
+    prof_ms[e.kind] += ms;
+    prof_flops[e.kind] += e.flops;
+    prof_pool.push_back(e.a);
+    prof_pool.push_back(e.b);
+  }
+  prof_pending.clear();
+  return rc;
+}
+
+// Algorithmic FLOPs per candidate and sample of the Gram and residual passes.
+static double flops_per_cand_k(int kind, int N) {
+  if (kind == DEBYE_KERNEL_GRAM) return 4.0 * N + 2.0 * (N + 2) * (N + 2);
+  if (kind == DEBYE_KERNEL_REFINE) return 67.0 * N + 25.0;
+  return 0.0;
+}
+
+// ------------------------------------------------------------------ spectra plan
+int debye_ctx::load_plan(const debye_spectra* sp, Plan& pl, cudaStream_t st) {
+  if (!sp) return fail(DEBYE_EINVAL, "spectra is NULL");
+  if (sp->S < 0) return fail(DEBYE_EINVAL, "S = %lld < 0", (long long)sp->S);
+  pl.S = sp->S;
+  pl.offs.assign(pl.S + 1, 0);
+  pl.npol.assign(pl.S, 0);
+  if (pl.S == 0) return DEBYE_OK;
+  if (!sp->offsets || !sp->omega || !sp->eps_re || !sp->eps_im || !sp->n_poles || !sp->lo || !sp->hi)
+    return fail(DEBYE_EINVAL, "a spectra array pointer is NULL");
+  if (sp->offsets_host) {
+    std::memcpy(pl.offs.data(), sp->offsets_host, sizeof(int64_t) * (pl.S + 1));
+  } else {
+    cudaError_t e = cudaMemcpyAsync(pl.offs.data(), sp->offsets, sizeof(int64_t) * (pl.S + 1),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(DEBYE_ECUDA, "reading offsets: %s", cudaGetErrorString(e));
+  }
+  if (sp->n_poles_host) {
+    std::memcpy(pl.npol.data(), sp->n_poles_host, sizeof(int32_t) * pl.S);
+  } else {
+    cudaError_t e = cudaMemcpyAsync(pl.npol.data(), sp->n_poles, sizeof(int32_t) * pl.S,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(DEBYE_ECUDA, "reading n_poles: %s", cudaGetErrorString(e));
+  }
+  if (pl.offs[0] != 0) return fail(DEBYE_EINVAL, "offsets[0] = %lld, expected 0", (long long)pl.offs[0]);
+  pl.nmax_seen = 0;
+  for (int64_t s = 0; s < pl.S; ++s) {
+    if (pl.offs[s + 1] < pl.offs[s])
+      return fail(DEBYE_EINVAL, "offsets not non-decreasing at spectrum %lld", (long long)s);
+    if (pl.offs[s + 1] - pl.offs[s] > (int64_t)1 << 30)
+      return fail(DEBYE_EINVAL, "spectrum %lld has too many samples", (long long)s);
+    if (pl.npol[s] < 1 || pl.npol[s] > NMAX)
+      return fail(DEBYE_EINVAL, "n_poles[%lld] = %d outside 1..%d", (long long)s, pl.npol[s], NMAX);
+    pl.nmax_seen = std::max(pl.nmax_seen, pl.npol[s]);
+  }
+  pl.n_samples = pl.offs[pl.S];
+  return DEBYE_OK;
+}
+
+int debye_ctx::prep_spectra(const debye_spectra* sp, const Plan& pl, cudaStream_t st) {
+  int rc;
+  if ((rc = ensure(ws_kf32, sizeof(float4) * std::max<int64_t>(pl.n_samples, 1), "kf32"))) return rc;
+  if ((rc = ensure(ws_kff, sizeof(float4) * std::max<int64_t>(pl.n_samples, 1), "kff"))) return rc;
+  if ((rc = ensure(ws_h0, sizeof(double) * std::max<int64_t>(pl.S, 1), "h0"))) return rc;
+  launch_prep(pl.n_samples, pl.S, sp->offsets, sp->omega, sp->eps_re, sp->eps_im, sp->lo, sp->hi,
+              (float4*)ws_kf32.p, (float4*)ws_kff.p, (double*)ws_h0.p, d_status, sms, st);
+  launches += (pl.n_samples > 0) + (pl.S > 0);
+  return check_launch("prep");
+}
+
+// Units over candidate ranges [qb[s], qe[s]) of each spectrum, grouped by pole
+// bucket and, within a bucket, heaviest first (work ~ K (N+2)^2 per candidate).
+void debyefit::build_units(const Plan& pl, const std::vector<int32_t>& qb, const std::vector<int32_t>& qe,
+                 int cb, UnitGroups& g) {
+  std::vector<std::vector<Unit>> per(N_BUCKETS);
+  for (int64_t s = 0; s < pl.S; ++s) {
+    const int N = pl.npol[s];
+    for (int32_t q = qb[s]; q < qe[s]; q += cb) {
+      Unit u;
+      u.s = (int32_t)s;
+      u.q0 = q;
+      u.q1 = std::min(qe[s], q + cb);
+      u.N = N;
+      u.k0 = pl.offs[s];
+      u.k1 = pl.offs[s + 1];
+      per[bucket_of(N)].push_back(u);
+    }
+  }
+  g.units.clear();
+  for (int b = 0; b < N_BUCKETS; ++b) {
+    auto& v = per[b];
+    std::stable_sort(v.begin(), v.end(), [](const Unit& x, const Unit& y) {
+      const double wx = (double)(x.k1 - x.k0) * (x.q1 - x.q0) * (x.N + 2) * (x.N + 2);
+      const double wy = (double)(y.k1 - y.k0) * (y.q1 - y.q0) * (y.N + 2) * (y.N + 2);
+      return wx > wy;
+    });
+    g.begin[b] = (int)g.units.size();
+    g.units.insert(g.units.end(), v.begin(), v.end());
+  }
+  g.begin[N_BUCKETS] = (int)g.units.size();
+}
+
+int debye_ctx::upload_units(const UnitGroups& g, Buf& dst, cudaStream_t st) {
+  int rc;
+  const size_t bytes = sizeof(Unit) * std::max<size_t>(g.units.size(), 1);
+  if ((rc = ensure(dst, bytes, "units"))) return rc;
+  if (g.units.empty()) return DEBYE_OK;
+  cudaError_t e = cudaMemcpyAsync(dst.p, g.units.data(), sizeof(Unit) * g.units.size(),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(DEBYE_ECUDA, "uploading work units: %s", cudaGetErrorString(e));
+  return DEBYE_OK;
+}
+
+int debye_ctx::ensure_scratch(int64_t Q, int nmax, ScratchBufs& sb, Scratch& sc) {
+  const int nm1 = nmax + 1;
+  const int npk = nm1 * (nm1 + 1) / 2;
+  const int ng = npk + nm1;
+  const size_t q = (size_t)std::max<int64_t>(Q, 1);
+  int rc;
+  if ((rc = ensure(sb.G, sizeof(double) * ng * q, "G"))) return rc;
+  if ((rc = ensure(sb.L, sizeof(double) * npk * q, "L"))) return rc;
+  if ((rc = ensure(sb.vec, sizeof(double) * 5 * nm1 * q, "vectors"))) return rc;
+  if ((rc = ensure(sb.rt, sizeof(double) * (nm1 + 1) * q, "rt"))) return rc;
+  if ((rc = ensure(sb.fail, sizeof(int32_t) * q, "fail"))) return rc;
+  sc.Q = Q;
+  sc.nmax = nmax;
+  sc.ng = ng;
+  sc.G = (double*)sb.G.p;
+  sc.L = (double*)sb.L.p;
+  double* v = (double*)sb.vec.p;
+  sc.dinv = v;
+  sc.x = v + (size_t)nm1 * q;
+  sc.xh = v + (size_t)2 * nm1 * q;
+  sc.w = v + (size_t)3 * nm1 * q;
+  sb.g1 = v + (size_t)4 * nm1 * q;
+  sc.rt = (double*)sb.rt.p;
+  sc.gt = (double*)sb.G.p;  // the gradient pass reuses the Gram storage (>= 4 nmax doubles)
+  sc.fail = (int32_t*)sb.fail.p;
+  return DEBYE_OK;
+}
+
+// The whole evaluation of one candidate set: Gram pass, FP64 solve,
+// `refine_steps` residual passes with refinement, flip and cost, and optionally
+// the gradient. Units must already be on the device (a.units).
+int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, double* cost,
+                        double* weights, double* grad, double* g1, int cb, cudaStream_t st) {
+  auto per_bucket = [&](int phase) -> int {
+    for (int b = 0; b < N_BUCKETS; ++b) {
+      const int n = g.begin[b + 1] - g.begin[b];
+      if (!n) continue;
+      EvalArgs ab = a;
+      ab.units = a.units + g.begin[b];
+      ab.n_units = n;
+      const int grid = std::max(1, std::min(n, sms * 16));
+      ProfEntry pe;
+      if (prof_on) {
+        double fl = 0.0;
+        if (!a.active)
+          for (int u = g.begin[b]; u < g.begin[b + 1]; ++u) {
+            const Unit& x = g.units[u];
+            fl += (double)(x.q1 - x.q0) * (double)(x.k1 - x.k0) * flops_per_cand_k(phase, x.N);
+          }
+        prof_begin(phase, fl, st, pe);
+      }
+      switch (b) {
+        case 0: launch_pass_b0(phase, mixed, ab, grid, cb, st); break;
+        case 1: launch_pass_b1(phase, mixed, ab, grid, cb, st); break;
+        case 2: launch_pass_b2(phase, mixed, ab, grid, cb, st); break;
+        case 3: launch_pass_b3(phase, mixed, ab, grid, cb, st); break;
+        default: launch_pass_b4(phase, mixed, ab, grid, cb, st); break;
+      }
+      if (prof_on) prof_end(pe, st);
+      ++launches;
+    }
+    return check_launch("pass");
+  };
+  auto timed = [&](int kind, auto launch) {
+    ProfEntry pe;
+    if (prof_on) prof_begin(kind, 0.0, st, pe);
+    launch();
+    if (prof_on) prof_end(pe, st);
+    ++launches;
+  };
+  int rc;
+  a.n_units = (int)g.units.size();
+  if (a.n_units == 0) return DEBYE_OK;
+  if ((rc = per_bucket(PH_GRAM))) return rc;
+  timed(DEBYE_KERNEL_SOLVE, [&] { launch_solve(a, cb, sms, st); });
+  if ((rc = check_launch("solve"))) return rc;
+  for (int it = 0; it < steps; ++it) {
+    if ((rc = per_bucket(PH_REFINE))) return rc;
+    const bool last = it + 1 == steps;
+    timed(DEBYE_KERNEL_FINISH, [&] { launch_finish(a, last ? 1 : 0, cost, weights, g1, cb, sms, st); });
+    if ((rc = check_launch("finish"))) return rc;
+  }
+  if (grad) {
+    timed(DEBYE_KERNEL_GRAD, [&] { launch_grad_prep(a, g1, cb, sms, st); });
+    if ((rc = per_bucket(PH_GRAD))) return rc;
+    timed(DEBYE_KERNEL_GRAD, [&] { launch_grad_finish(a, grad, cb, sms, st); });
+    if ((rc = check_launch("gradient"))) return rc;
+  }
+  return DEBYE_OK;
+}
+
+// Common path of debye_eval_population / debye_cost_grad.
+static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n_max,
+                      const double* theta, double* cost, double* weights, double* grad,
+                      cudaStream_t st) {
+  if (!h) return DEBYE_EINVAL;
+  h->err.clear();
+  if (P < 1) return h->fail(DEBYE_EINVAL, "P = %d < 1", P);
+  if (n_max < 1 || n_max > NMAX) return h->fail(DEBYE_EINVAL, "n_max = %d outside 1..%d", n_max, NMAX);
+  if (!sp) return h->fail(DEBYE_EINVAL, "spectra is NULL");
+  if ((int64_t)sp->S * P > ((int64_t)1 << 31) - 1) return h->fail(DEBYE_EINVAL, "S*P exceeds 2^31-1");
+  int rc;
+  Plan pl;
+  if ((rc = h->load_plan(sp, pl, st))) return rc;
+  if (pl.nmax_seen > n_max) return h->fail(DEBYE_EINVAL, "n_max = %d < largest N = %d", n_max, pl.nmax_seen);
+  if (pl.S == 0) return DEBYE_OK;
+  if (!theta || !cost) return h->fail(DEBYE_EINVAL, "theta or cost is NULL");
+  if ((rc = h->prep_spectra(sp, pl, st))) return rc;
+  std::vector<int32_t> qb(pl.S), qe(pl.S);
+  for (int64_t s = 0; s < pl.S; ++s) {
+    qb[s] = (int32_t)(s * P);
+    qe[s] = (int32_t)((s + 1) * P);
+  }
+  const int cb = h->block_size(pl);
+  UnitGroups g;
+  build_units(pl, qb, qe, cb, g);
+  if ((rc = h->upload_units(g, h->ws_units, st))) return rc;
+  ScratchBufs& sb = h->sb_eval;
+  EvalArgs a{};
+  const int64_t Q = pl.S * (int64_t)P;
+  if ((rc = h->ensure_scratch(Q, n_max, sb, a.sc))) return rc;
+  a.units = (const Unit*)h->ws_units.p;
+  a.theta = theta;
+  a.kf32 = (const float4*)h->ws_kf32.p;
+  a.kff = (const float4*)h->ws_kff.p;
+  a.omega = sp->omega;
+  a.eps_re = sp->eps_re;
+  a.eps_im = sp->eps_im;
+  a.h0 = (const double*)h->ws_h0.p;
+  a.active = nullptr;
+  a.lam = h->opt.lam_search;
+  a.status = h->d_status;
+  const bool mixed = h->opt.precision == DEBYE_PREC_MIXED;
+  return h->run_eval(a, g, mixed, h->eval_steps(grad != nullptr), cost, weights, grad, sb.g1, cb, st);
+}
+
+// Refinement passes of an evaluation. With the mixed precision the gradient is
+// first-order in the weights' error through w = M^-1 S g_hat (g_hat carries the
+// FP32 Gram's error times the last correction), so cost+gradient evaluations
+// take at least two passes.
+int debye_ctx::eval_steps(bool with_grad) const {
+  const bool mixed = opt.precision == DEBYE_PREC_MIXED;
+  return (with_grad && mixed) ? std::max(opt.refine_steps, 2) : opt.refine_steps;
+}
+
+int debye_ctx::block_size(const Plan&) const {
+  return opt.cands_per_block > 0 ? opt.cands_per_block : 64;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+void debye_default_options(debye_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = DEBYE_PREC_MIXED;
+  o->refine_steps = 1;
+  o->lam_search = 1e-3;
+  o->lam_final = 1e-3;
+  o->pso_omega = 0.5;
+  o->pso_phi_p = 0.5;
+  o->pso_phi_g = 0.5;
+  o->lbfgs_m = 8;
+  o->lbfgs_max_trials = 20;
+  o->lbfgs_c1 = 1e-4;
+  o->cands_per_block = 0;
+  o->use_graphs = 1;
+}
+
+int debye_fit_init(debye_handle* out, const debye_options* opt) {
+  if (!out) return DEBYE_EINVAL;
+  *out = nullptr;
+  debye_options o;
+  if (opt) o = *opt;
+  else debye_default_options(&o);
+  if (o.precision != DEBYE_PREC_FP64 && o.precision != DEBYE_PREC_MIXED) return DEBYE_EINVAL;
+  if (o.refine_steps < 1 || o.refine_steps > 4) return DEBYE_EINVAL;
+  if (!(o.lam_search >= 0.0) || !(o.lam_final >= 0.0)) return DEBYE_EINVAL;
+  if (o.lbfgs_m < 1 || o.lbfgs_m > 8) return DEBYE_EINVAL;
+  if (o.lbfgs_max_trials < 1 || o.lbfgs_max_trials > 40) return DEBYE_EINVAL;
+  if (o.cands_per_block != 0 &&
+      (o.cands_per_block < 32 || o.cands_per_block > MAX_BLOCK || o.cands_per_block % 32))
+    return DEBYE_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return DEBYE_ECUDA;
+  }
+  debye_ctx* h = new debye_ctx();
+  h->opt = o;
+  h->device = dev;
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (h->sms <= 0) h->sms = 1;
+  if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->work_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    h->release();
+    delete h;
+    return DEBYE_ECUDA;
+  }
+  *out = h;
+  return DEBYE_OK;
+}
+
+int debye_fit_destroy(debye_handle h) {
+  if (!h) return DEBYE_OK;
+  h->release();
+  delete h;
+  return DEBYE_OK;
+}
+
+int debye_eval_population(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n_max,
+                          const double* theta, double* cost, double* weights, cudaStream_t st) {
+  return eval_entry(h, sp, P, n_max, theta, cost, weights, nullptr, st);
+}
+
+int debye_cost_grad(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n_max,
+                    const double* theta, double* cost, double* grad, cudaStream_t st) {
+  if (h && !grad) return h->fail(DEBYE_EINVAL, "grad is NULL");
+  return eval_entry(h, sp, P, n_max, theta, cost, nullptr, grad, st);
+}
+
+int debye_synth_targets(debye_handle h, int64_t S, const int64_t* offsets, const double* omega,
+                        const int32_t* model, const double* params, const int64_t* pole_offsets,
+                        const double* pole_tau, const double* pole_deps, const double* noise_re,
+                        const double* noise_im, double* eps_re, double* eps_im, cudaStream_t st) {
+  if (!h) return DEBYE_EINVAL;
+  h->err.clear();
+  if (S < 0) return h->fail(DEBYE_EINVAL, "S < 0");
+  if (S == 0) return DEBYE_OK;
+  if (!offsets || !omega || !model || !params || !eps_re || !eps_im)
+    return h->fail(DEBYE_EINVAL, "a required pointer is NULL");
+  if ((noise_re == nullptr) != (noise_im == nullptr))
+    return h->fail(DEBYE_EINVAL, "noise_re and noise_im must both be given or both NULL");
+  launch_synth(S, offsets, omega, model, params, pole_offsets, pole_tau, pole_deps, noise_re,
+               noise_im, eps_re, eps_im, h->d_status, h->sms, st);
+  h->launches += 1;
+  return h->check_launch("synth");
+}
+
+int debye_sync(debye_handle h, cudaStream_t st) {
+  if (!h) return DEBYE_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return h->fail(DEBYE_ECUDA, "stream sync: %s", cudaGetErrorString(e));
+  int s = 0;
+  e = cudaMemcpy(&s, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return h->fail(DEBYE_ECUDA, "status read: %s", cudaGetErrorString(e));
+  if (s != 0) {
+    cudaMemset(h->d_status, 0, sizeof(int));
+    return h->fail(s, "device reported status %d", s);
+  }
+  return DEBYE_OK;
+}
+
+const char* debye_last_error(debye_handle h) { return h ? h->err.c_str() : "invalid handle"; }
+
+int debye_launch_count(debye_handle h, int64_t* count, int32_t reset) {
+  if (!h) return DEBYE_EINVAL;
+  if (count) *count = h->launches;
+  if (reset) h->launches = 0;
+  return DEBYE_OK;
+}
+
+int debye_profile_enable(debye_handle h, int32_t enable) {
+  if (!h) return DEBYE_EINVAL;
+  int rc = h->prof_collect();
+  h->prof_on = enable != 0;
+  if (h->prof_on)
+    for (int k = 0; k < DEBYE_KERNEL_KINDS; ++k) {
+      h->prof_launches[k] = 0;
+      h->prof_ms[k] = 0.0;
+      h->prof_flops[k] = 0.0;
+    }
+  return rc;
+}
+
+int debye_profile_read(debye_handle h, int32_t kind, int64_t* launches, double* ms, double* flops) {
+  if (!h) return DEBYE_EINVAL;
+  if (kind < 0 || kind >= DEBYE_KERNEL_KINDS) return h->fail(DEBYE_EINVAL, "kernel kind %d", kind);
+  int rc = h->prof_collect();
+  if (launches) *launches = h->prof_launches[kind];
+  if (ms) *ms = h->prof_ms[kind];
+  if (flops) *flops = h->prof_flops[kind];
+  return rc;
+}
+
+const char* debye_version(void) { return "debyefit 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,188 @@
+// Shared device-side definitions of libdebyefit (sm_103a).
+//
+// Work decomposition: every evaluation works on a flat list of candidates q.
+// Candidate q belongs to one spectrum; a Unit is a run of at most `cb`
+// consecutive candidates of one spectrum, processed by one thread block with
+// one thread per candidate. Per-candidate scratch is stored structure-of-arrays,
+// element e of candidate q at base[e * Q + q], so a warp's 32 candidates touch 32
+// consecutive doubles.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/debyefit.h"
+
+namespace debyefit {
+
+constexpr int NMAX = DEBYE_MAX_POLES;   // largest pole count
+constexpr int NMAX1 = NMAX + 1;         // unknowns: eps_inf + d_eps_1..N
+constexpr int NPACK_MAX = NMAX1 * (NMAX1 + 1) / 2;
+
+// Packed lower-triangular index of (I, J), J <= I.
+__host__ __device__ constexpr int pk(int I, int J) { return I * (I + 1) / 2 + J; }
+
+enum Phase { PH_GRAM = 0, PH_REFINE = 1, PH_GRAD = 2 };
+
+struct Unit {
+  int32_t s;    // spectrum
+  int32_t q0;   // first candidate
+  int32_t q1;   // one past the last candidate
+  int32_t N;    // poles of this spectrum
+  int64_t k0;   // first sample of the spectrum
+  int64_t k1;   // one past the last sample
+};
+
+// Per-call views of the candidate scratch (all device pointers).
+struct Scratch {
+  int64_t Q;        // candidates in this evaluation (SoA stride)
+  int32_t nmax;     // pole capacity of theta / weights rows
+  int32_t ng;       // per-candidate Gram record: packed (nmax+1) lower triangle + h
+  double* G;        // [ng][Q]   Gram (packed) followed by h = A^T b
+  double* L;        // [npk][Q]  Cholesky factor of the scaled damped matrix
+  double* dinv;     // [nmax+1][Q] 1 / sqrt(G_ii)
+  double* x;        // [nmax+1][Q] current (unflipped) weights
+  double* xh;       // [nmax+1][Q] flipped weights
+  double* w;        // [nmax+1][Q] adjoint solve M^-1 S g_hat (gradient only)
+  double* rt;       // [nmax+2][Q] rr = ||r||^2 then t = A^T r
+  double* gt;       // [4*nmax][Q] gradient projections
+  int32_t* fail;    // [Q] non-zero: candidate's damped matrix not positive definite
+};
+
+struct EvalArgs {
+  const Unit* units;
+  int32_t n_units;
+  const double* theta;     // [Q][nmax] log10 tau
+  const float4* kf32;      // [sum K] {omega_hi, eps'_hi, eps''_hi, 0}
+  const float4* kff;       // [sum K] {omega_lo, eps'_lo, eps''_lo, 0}
+  const double* omega;     // [sum K] FP64 inputs
+  const double* eps_re;
+  const double* eps_im;
+  const double* h0;        // [S] sum_k eps'_k
+  const uint8_t* active;   // [Q] optional candidate mask (nullptr: all)
+  double lam;
+  Scratch sc;
+  int* status;             // device status word
+};
+
+// ------------------------------------------------------------------ status word
+__device__ __forceinline__ void set_status(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// ------------------------------------------------------------------ float-float helpers
+// Error-free transformations (Dekker 1971; Knuth TAOCP vol. 2, 4.2.2). The
+// __f*_rn intrinsics keep the compiler from contracting the rounded operations
+// into FMAs, which would break the error terms.
+__device__ __forceinline__ float rcp_approx(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return r;
+}
+
+// s + e == a + b exactly (Knuth TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void split_double(double v, float& hi, float& lo) {
+  hi = __double2float_rn(v);
+  lo = __double2float_rn(v - (double)hi);
+}
+
+// Float-float Debye basis value c = 1/(1 + j x) with x = omega * tau:
+// re = 1/(1+x^2), im = x/(1+x^2), each as hi + lo (about 2^-44 relative).
+// The reciprocal is the hardware approximation refined by one Newton-Raphson
+// step on the float-float denominator: r = r0 + r0 (1 - d r0).
+__device__ __forceinline__ void basis_ff(float wh, float wl, float th, float tl,
+                                         float& reh, float& rel, float& imh, float& iml,
+                                         float& xh_out) {
+  float xh = __fmul_rn(wh, th);
+  float xl = __fmaf_rn(wh, th, -xh);
+  xl = __fmaf_rn(wh, tl, __fmaf_rn(wl, th, xl));
+  float sh = __fmul_rn(xh, xh);
+  float sl = __fmaf_rn(xh, xh, -sh);
+  sl = __fmaf_rn(__fmul_rn(2.0f, xh), xl, sl);
+  float dh, de;
+  two_sum(1.0f, sh, dh, de);
+  float dl = __fadd_rn(de, sl);
+  float r0 = rcp_approx(dh);
+  float e = __fmaf_rn(-dh, r0, 1.0f);
+  e = __fmaf_rn(-dl, r0, e);
+  reh = r0;
+  rel = __fmul_rn(r0, e);
+  imh = __fmul_rn(xh, reh);
+  iml = __fmaf_rn(xh, reh, -imh);
+  iml = __fmaf_rn(xh, rel, __fmaf_rn(xl, reh, iml));
+  xh_out = xh;
+}
+
+// acc (hi, lo) -= w * c, with w and c float-float.
+__device__ __forceinline__ void ff_sub_prod(float& ah, float& al, float wh, float wl, float ch,
+                                            float cl) {
+  float p = __fmul_rn(wh, ch);
+  float pe = __fmaf_rn(wh, ch, -p);
+  pe = __fmaf_rn(wh, cl, __fmaf_rn(wl, ch, pe));
+  float s, e;
+  two_sum(ah, -p, s, e);
+  ah = s;
+  al = __fadd_rn(al, __fsub_rn(e, pe));
+}
+
+// acc (hi, lo) += a * b, a and b float-float (one Dot2 step: TwoProduct by FMA,
+// TwoSum of the leading part, low-order terms gathered in lo).
+__device__ __forceinline__ void ff_add_prod(float& ah, float& al, float xh, float xl, float yh,
+                                            float yl) {
+  float p = __fmul_rn(xh, yh);
+  float pe = __fmaf_rn(xh, yh, -p);
+  pe = __fmaf_rn(xh, yl, __fmaf_rn(xl, yh, pe));
+  float s, e;
+  two_sum(ah, p, s, e);
+  ah = s;
+  al = __fadd_rn(al, __fadd_rn(e, pe));
+}
+
+// (hi, lo) renormalised so that hi = fl(hi + lo) (Fast2Sum, |hi| >= |lo|).
+__device__ __forceinline__ void ff_norm(float& h, float& l) {
+  const float s = __fadd_rn(h, l);
+  l = __fsub_rn(l, __fsub_rn(s, h));
+  h = s;
+}
+
+// acc (hi, lo) += v (single float), exactly up to the final rounding of lo.
+__device__ __forceinline__ void ff_add(float& ah, float& al, float v) {
+  float s, e;
+  two_sum(ah, v, s, e);
+  ah = s;
+  al = __fadd_rn(al, e);
+}
+
+// ------------------------------------------------------------------ SplitMix64
+// Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+// OOPSLA 2014: the SplitMix64 output function used as a key mixer.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Key prefix over (seed, tag, spectrum, generation).
+__host__ __device__ __forceinline__ uint64_t rng_prefix(uint64_t seed, uint64_t tag, uint64_t s,
+                                                        uint64_t g) {
+  uint64_t h = splitmix64(seed);
+  h = splitmix64(h ^ tag);
+  h = splitmix64(h ^ s);
+  return splitmix64(h ^ g);
+}
+
+// Uniform double in [0, 1) for (prefix, particle, dim).
+__host__ __device__ __forceinline__ double rng_uniform(uint64_t prefix, uint64_t p, uint64_t d) {
+  uint64_t h = splitmix64(splitmix64(prefix ^ p) ^ d);
+  return (double)(h >> 11) * (1.0 / 9007199254740992.0);
+}
+
+constexpr uint64_t TAG_INIT_POS = 1, TAG_INIT_VEL = 2, TAG_R1 = 3, TAG_R2 = 4;
+
+}  // namespace debyefit

@@ -1,0 +1,121 @@
+// Host-side state of a libdebyefit handle.
+#pragma once
+#include <cstdint>
+#include <functional>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+
+namespace debyefit {
+
+struct Buf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+// Host view of a ragged batch: sample offsets and pole counts.
+struct Plan {
+  int64_t S = 0;
+  int64_t n_samples = 0;
+  int32_t nmax_seen = 0;
+  std::vector<int64_t> offs;
+  std::vector<int32_t> npol;
+};
+
+// Work units grouped by pole bucket: bucket b owns units[begin[b] .. begin[b+1]).
+struct UnitGroups {
+  std::vector<Unit> units;
+  int begin[N_BUCKETS + 1] = {0};
+};
+
+struct ScratchBufs {
+  Buf G, L, vec, rt, fail;
+  double* g1 = nullptr;
+};
+
+void build_units(const Plan& pl, const std::vector<int32_t>& qb, const std::vector<int32_t>& qe,
+                 int cb, UnitGroups& g);
+
+}  // namespace debyefit
+
+struct debye_ctx {
+  debye_options opt{};
+  int device = 0;
+  int sms = 1;
+  int* d_status = nullptr;
+  std::string err;
+  cudaStream_t capturing_stream = nullptr;
+  // Test hook: return true to make the next workspace allocation fail.
+  std::function<bool(size_t)> alloc_hook;
+
+  cudaStream_t work_stream = nullptr;  // non-blocking stream of debye_fit_batch
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+
+  debyefit::Buf ws_kf32, ws_kff, ws_h0, ws_units;
+  debyefit::ScratchBufs sb_eval, sb_polish, sb_final;
+  std::map<std::string, debyefit::Buf> named_bufs;  // swarm / polish / result state
+
+  // kernel timing (debye_profile_*)
+  struct ProfEntry {
+    int kind;
+    double flops;
+    cudaEvent_t a, b;
+  };
+  int64_t launches = 0;  // kernel launches enqueued (graph replays count every node)
+  bool prof_on = false;
+  std::vector<ProfEntry> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  int64_t prof_launches[DEBYE_KERNEL_KINDS] = {0};
+  double prof_ms[DEBYE_KERNEL_KINDS] = {0};
+  double prof_flops[DEBYE_KERNEL_KINDS] = {0};
+  cudaEvent_t prof_event();
+  void prof_begin(int kind, double flops, cudaStream_t st, ProfEntry& e);
+  void prof_end(ProfEntry& e, cudaStream_t st);
+  int prof_collect();
+
+  int fail(int code, const char* fmt, ...);
+  int ensure(debyefit::Buf& b, size_t bytes, const char* what);
+  int check_launch(const char* what);
+  int load_plan(const debye_spectra* sp, debyefit::Plan& pl, cudaStream_t st);
+  int prep_spectra(const debye_spectra* sp, const debyefit::Plan& pl, cudaStream_t st);
+  int upload_units(const debyefit::UnitGroups& g, debyefit::Buf& dst, cudaStream_t st);
+  int ensure_scratch(int64_t Q, int nmax, debyefit::ScratchBufs& sb, debyefit::Scratch& sc);
+  int run_eval(debyefit::EvalArgs a, const debyefit::UnitGroups& g, bool mixed, int steps,
+               double* cost, double* weights, double* grad, double* g1, int cb, cudaStream_t st);
+  int block_size(const debyefit::Plan& pl) const;
+  int eval_steps(bool with_grad) const;
+  int named(const char* name, size_t bytes, void** out);
+
+  void free_buf(debyefit::Buf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+  }
+  void release() {
+    free_buf(ws_kf32);
+    free_buf(ws_kff);
+    free_buf(ws_h0);
+    free_buf(ws_units);
+    for (debyefit::ScratchBufs* sb : {&sb_eval, &sb_polish, &sb_final}) {
+      free_buf(sb->G);
+      free_buf(sb->L);
+      free_buf(sb->vec);
+      free_buf(sb->rt);
+      free_buf(sb->fail);
+    }
+    for (auto& kv : named_bufs) free_buf(kv.second);
+    named_bufs.clear();
+    if (d_status) cudaFree(d_status);
+    d_status = nullptr;
+    prof_collect();
+    for (cudaEvent_t e : prof_pool) cudaEventDestroy(e);
+    prof_pool.clear();
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (work_stream) cudaStreamDestroy(work_stream);
+    ev_in = ev_out = nullptr;
+    work_stream = nullptr;
+  }
+};

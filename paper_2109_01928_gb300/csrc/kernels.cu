@@ -1,0 +1,385 @@
+// N-generic kernels of libdebyefit: input preparation, the FP64 damped solve,
+// refinement/finish with the sign flip, gradient assembly, the particle swarm
+// and target synthesis.
+#include <cmath>
+
+#include "launch.h"
+#include "solve.cuh"
+
+namespace debyefit {
+
+// ------------------------------------------------------------------ input preparation
+// Per sample: float-float split of omega, eps', eps'' for the mixed passes and
+// finiteness checks; per spectrum: h0 = sum_k eps'_k (FP64).
+__global__ void k_prep_samples(int64_t n, const double* __restrict__ omega,
+                               const double* __restrict__ er, const double* __restrict__ ei,
+                               float4* __restrict__ kf32, float4* __restrict__ kff, int* status) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double w = omega[k], a = er[k], b = ei[k];
+    if (!(w > 0.0) || !isfinite(w) || !isfinite(a) || !isfinite(b)) set_status(status, DEBYE_ENOTFINITE);
+    float wh, wl, ah, al, bh, bl;
+    split_double(w, wh, wl);
+    split_double(a, ah, al);
+    split_double(b, bh, bl);
+    kf32[k] = make_float4(wh, ah, bh, 0.f);
+    kff[k] = make_float4(wl, al, bl, 0.f);
+  }
+}
+
+__global__ void k_prep_spectra(int64_t S, const int64_t* __restrict__ offsets,
+                               const double* __restrict__ er, const double* __restrict__ lo,
+                               const double* __restrict__ hi, double* __restrict__ h0,
+                               int* status) {
+  __shared__ double red[32];
+  for (int64_t s = blockIdx.x; s < S; s += gridDim.x) {
+    const int64_t a = offsets[s], b = offsets[s + 1];
+    double acc = 0.0;
+    for (int64_t k = a + threadIdx.x; k < b; k += blockDim.x) acc += er[k];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      acc = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (threadIdx.x == 0) {
+        h0[s] = acc;
+        if (!(lo[s] < hi[s]) || !isfinite(lo[s]) || !isfinite(hi[s])) set_status(status, DEBYE_EBOUNDS);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ damped solve
+// x0 = M^-1 h per candidate; stores L, D^-1, x0 and the failure flag.
+__global__ void __launch_bounds__(256) k_solve(EvalArgs a) {
+  const int64_t Q = a.sc.Q;
+  const int hb = (a.sc.nmax + 1) * (a.sc.nmax + 2) / 2;
+  for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
+    const Unit u = a.units[ui];
+    const int q = u.q0 + (int)threadIdx.x;
+    if (q >= u.q1 || (a.active && !a.active[q])) continue;
+    const int n = u.N + 1;
+    double L[NPACK_MAX], dinv[NMAX1], z[NMAX1];
+    for (int i = 0; i < n; ++i) dinv[i] = 1.0 / sqrt(a.sc.G[(int64_t)pk(i, i) * Q + q]);
+    for (int i = 0; i < n; ++i) {
+      for (int j = 0; j < i; ++j) L[pk(i, j)] = a.sc.G[(int64_t)pk(i, j) * Q + q] * dinv[i] * dinv[j];
+      L[pk(i, i)] = 1.0 + a.lam;
+    }
+    bool ok = cholesky_packed(L, n);
+    if (ok) {
+      for (int i = 0; i < n; ++i) z[i] = a.sc.G[(int64_t)(hb + i) * Q + q] * dinv[i];
+      llt_solve(L, z, n);
+      for (int i = 0; i < n; ++i) {
+        z[i] *= dinv[i];
+        ok = ok && isfinite(z[i]);
+      }
+    }
+    a.sc.fail[q] = ok ? 0 : 1;
+    if (!ok) continue;
+    const int npk = n * (n + 1) / 2;
+    for (int e = 0; e < npk; ++e) a.sc.L[(int64_t)e * Q + q] = L[e];
+    for (int i = 0; i < n; ++i) {
+      a.sc.dinv[(int64_t)i * Q + q] = dinv[i];
+      a.sc.x[(int64_t)i * Q + q] = z[i];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ refinement / finish
+// From the residual pass at x (rt: rr = ||b - A x||^2, t = A^T (b - A x)):
+//   g  = t - lam diag(G) x          (minus half the cost gradient in x)
+//   dx = M^-1 g,  x1 = x + dx       (one step of iterative refinement)
+// final == 0: store x1 and return.
+// final == 1: cost(x1) by the exact quadratic identity
+//   cost(y) = cost(x) - 2 (y - x)^T g + (y - x)^T M (y - x),  cost(x) = rr + lam sum G_ii x_i^2,
+// then the sign flip x_hat = x1 + e (e_i = -2 x1_i where d_eps_i < 0, Sec. III-B) and
+//   cost(x_hat) = cost(x1) - 2 e^T g1 + e^T M e,  g1 = g - M dx.
+// Outputs cost[q], weights[q][nmax+1] (optional); keeps x1, x_hat and g1 for the gradient.
+__global__ void __launch_bounds__(256) k_finish(EvalArgs a, int final_step, double* cost,
+                                                double* weights, double* g1_out) {
+  const int64_t Q = a.sc.Q;
+  const int nm1 = a.sc.nmax + 1;
+  for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
+    const Unit u = a.units[ui];
+    const int q = u.q0 + (int)threadIdx.x;
+    if (q >= u.q1 || (a.active && !a.active[q])) continue;
+    const int n = u.N + 1;
+    if (a.sc.fail[q]) {
+      if (final_step) {
+        if (cost) cost[q] = INFINITY;
+        if (weights)
+          for (int j = 0; j < nm1; ++j) weights[(int64_t)q * nm1 + j] = 0.0;
+      }
+      continue;
+    }
+    double L[NPACK_MAX], d[NMAX1], x[NMAX1], g[NMAX1], v[NMAX1], w1[NMAX1], tmp[NMAX1];
+    const int npk = n * (n + 1) / 2;
+    for (int e = 0; e < npk; ++e) L[e] = a.sc.L[(int64_t)e * Q + q];
+    double cost0 = a.sc.rt[q];
+    for (int i = 0; i < n; ++i) {
+      const double gii = a.sc.G[(int64_t)pk(i, i) * Q + q];
+      d[i] = 1.0 / a.sc.dinv[(int64_t)i * Q + q];
+      x[i] = a.sc.x[(int64_t)i * Q + q];
+      g[i] = a.sc.rt[(int64_t)(i + 1) * Q + q] - a.lam * gii * x[i];
+      cost0 += a.lam * gii * x[i] * x[i];
+      v[i] = g[i] / d[i];
+    }
+    llt_solve(L, v, n);            // v = D dx
+    if (!final_step) {
+      for (int i = 0; i < n; ++i) a.sc.x[(int64_t)i * Q + q] = x[i] + v[i] / d[i];
+      continue;
+    }
+    lt_mul(L, v, w1, n);           // w1 = L^T D dx
+    double dg = 0.0, dmd = 0.0;
+    for (int i = 0; i < n; ++i) {
+      dg += (v[i] / d[i]) * g[i];
+      dmd += w1[i] * w1[i];
+    }
+    double c = cost0 - 2.0 * dg + dmd;
+    // The step must not raise the damped cost, whose value at x is exact: if the
+    // identity leaves [0, cost(x)] the refinement is discarded (dx = 0).
+    if (!(c >= 0.0 && c <= cost0)) {
+      c = cost0;
+      for (int i = 0; i < n; ++i) {
+        v[i] = 0.0;
+        w1[i] = 0.0;
+      }
+    }
+    l_mul(L, w1, tmp, n);          // tmp = L L^T D dx; M dx = D tmp
+    bool flipped = false;
+    double e[NMAX1];
+    for (int i = 0; i < n; ++i) {
+      const double x1 = x[i] + v[i] / d[i];
+      x[i] = x1;
+      g[i] -= d[i] * tmp[i];       // g1
+      e[i] = (i > 0 && x1 < 0.0) ? -2.0 * x1 : 0.0;
+      flipped |= (e[i] != 0.0);
+    }
+    if (flipped) {
+      for (int i = 0; i < n; ++i) tmp[i] = d[i] * e[i];
+      lt_mul(L, tmp, w1, n);
+      double eg = 0.0, eme = 0.0;
+      for (int i = 0; i < n; ++i) {
+        eg += e[i] * g[i];
+        eme += w1[i] * w1[i];
+      }
+      c = c - 2.0 * eg + eme;
+    }
+    if (!isfinite(c)) c = INFINITY;
+    if (cost) cost[q] = c;
+    for (int i = 0; i < n; ++i) {
+      a.sc.x[(int64_t)i * Q + q] = x[i];
+      a.sc.xh[(int64_t)i * Q + q] = x[i] + e[i];
+      if (g1_out) g1_out[(int64_t)i * Q + q] = g[i];
+    }
+    if (weights) {
+      for (int j = 0; j < nm1; ++j) weights[(int64_t)q * nm1 + j] = (j < n) ? x[j] + e[j] : 0.0;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ gradient
+// w = M^-1 S g_hat with g_hat = g1 - M (x_hat - x1) = h - M x_hat,
+// S = diag(1, sign x1_1, ..., sign x1_N).
+__global__ void __launch_bounds__(256) k_grad_prep(EvalArgs a, const double* g1) {
+  const int64_t Q = a.sc.Q;
+  for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
+    const Unit u = a.units[ui];
+    const int q = u.q0 + (int)threadIdx.x;
+    if (q >= u.q1 || (a.active && !a.active[q])) continue;
+    if (a.sc.fail[q]) continue;
+    const int n = u.N + 1;
+    double L[NPACK_MAX], d[NMAX1], e[NMAX1], t1[NMAX1], t2[NMAX1];
+    const int npk = n * (n + 1) / 2;
+    for (int k = 0; k < npk; ++k) L[k] = a.sc.L[(int64_t)k * Q + q];
+    for (int i = 0; i < n; ++i) {
+      d[i] = 1.0 / a.sc.dinv[(int64_t)i * Q + q];
+      const double x1 = a.sc.x[(int64_t)i * Q + q];
+      e[i] = a.sc.xh[(int64_t)i * Q + q] - x1;
+      t1[i] = d[i] * e[i];
+    }
+    lt_mul(L, t1, t2, n);
+    l_mul(L, t2, t1, n);           // M e = D t1
+    for (int i = 0; i < n; ++i) {
+      const double x1 = a.sc.x[(int64_t)i * Q + q];
+      double gh = g1[(int64_t)i * Q + q] - d[i] * t1[i];
+      if (i > 0 && x1 < 0.0) gh = -gh;
+      t2[i] = gh / d[i];
+    }
+    llt_solve(L, t2, n);
+    for (int i = 0; i < n; ++i) a.sc.w[(int64_t)i * Q + q] = t2[i] / d[i];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_grad_finish(EvalArgs a, double* grad) {
+  const int64_t Q = a.sc.Q;
+  const int nmax = a.sc.nmax;
+  for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
+    const Unit u = a.units[ui];
+    const int q = u.q0 + (int)threadIdx.x;
+    if (q >= u.q1 || (a.active && !a.active[q])) continue;
+    const int N = u.N;
+    if (a.sc.fail[q]) {
+      for (int i = 0; i < nmax; ++i) grad[(int64_t)q * nmax + i] = 0.0;
+      continue;
+    }
+    for (int i = 0; i < nmax; ++i) {
+      double gi = 0.0;
+      if (i < N) {
+        const double xh = a.sc.xh[(int64_t)(i + 1) * Q + q];
+        const double x1 = a.sc.x[(int64_t)(i + 1) * Q + q];
+        const double w = a.sc.w[(int64_t)(i + 1) * Q + q];
+        const double t_rh = a.sc.gt[(int64_t)i * Q + q];
+        const double t_aa = a.sc.gt[(int64_t)(N + i) * Q + q];
+        const double t_r = a.sc.gt[(int64_t)(2 * N + i) * Q + q];
+        const double t_aw = a.sc.gt[(int64_t)(3 * N + i) * Q + q];
+        gi = -2.0 * xh * t_rh + 2.0 * a.lam * xh * xh * t_aa - 2.0 * w * t_r +
+             4.0 * a.lam * w * x1 * t_aa + 2.0 * x1 * t_aw;
+      }
+      grad[(int64_t)q * nmax + i] = gi;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host launchers
+void launch_prep(int64_t n_samples, int64_t S, const int64_t* offsets, const double* omega,
+                 const double* er, const double* ei, const double* lo, const double* hi,
+                 float4* kf32, float4* kff, double* h0, int* status, int sms, cudaStream_t st) {
+  if (n_samples > 0) {
+    int grid = (int)std::min<int64_t>((n_samples + 255) / 256, (int64_t)sms * 16);
+    k_prep_samples<<<grid, 256, 0, st>>>(n_samples, omega, er, ei, kf32, kff, status);
+  }
+  if (S > 0) {
+    int grid = (int)std::min<int64_t>(S, (int64_t)sms * 8);
+    k_prep_spectra<<<grid, 256, 0, st>>>(S, offsets, er, lo, hi, h0, status);
+  }
+}
+
+static int grid_for(int n_units, int sms, int per_sm) {
+  return std::max(1, std::min(n_units, sms * per_sm));
+}
+
+void launch_solve(const EvalArgs& a, int block, int sms, cudaStream_t st) {
+  if (a.n_units) k_solve<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a);
+}
+void launch_finish(const EvalArgs& a, int final_step, double* cost, double* weights, double* g1,
+                   int block, int sms, cudaStream_t st) {
+  if (a.n_units) k_finish<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, final_step, cost, weights, g1);
+}
+void launch_grad_prep(const EvalArgs& a, const double* g1, int block, int sms, cudaStream_t st) {
+  if (a.n_units) k_grad_prep<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, g1);
+}
+void launch_grad_finish(const EvalArgs& a, double* grad, int block, int sms, cudaStream_t st) {
+  if (a.n_units) k_grad_finish<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, grad);
+}
+
+}  // namespace debyefit
+
+// ------------------------------------------------------------------ target synthesis (Eqs. 3-7)
+namespace debyefit {
+
+struct cplx {
+  double re, im;
+};
+__device__ __forceinline__ cplx c_add(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cplx c_scale(cplx a, double s) { return {a.re * s, a.im * s}; }
+// Principal power z^p = |z|^p exp(j p arg z).
+__device__ __forceinline__ cplx c_pow(cplx z, double p) {
+  const double m = pow(hypot(z.re, z.im), p), t = p * atan2(z.im, z.re);
+  double sn, cs;
+  sincos(t, &sn, &cs);
+  return {m * cs, m * sn};
+}
+// Debye pole eps_inf + d_eps / (1 + j x), x = omega tau (Eq. 3), as a complex number.
+__device__ __forceinline__ cplx c_debye(double ei, double de, double x) {
+  const double r = 1.0 / (1.0 + x * x);
+  return {ei + de * r, -de * x * r};
+}
+
+__global__ void k_synth(int64_t S, const int64_t* __restrict__ offsets, const double* __restrict__ omega,
+                        const int32_t* __restrict__ model, const double* __restrict__ params,
+                        const int64_t* __restrict__ pole_off, const double* __restrict__ ptau,
+                        const double* __restrict__ pdeps, const double* __restrict__ nre,
+                        const double* __restrict__ nim, double* __restrict__ er,
+                        double* __restrict__ ei, int* status) {
+  constexpr double PI = 3.141592653589793;
+  for (int64_t s = blockIdx.x; s < S; s += gridDim.x) {
+    const double* p = params + s * DEBYE_N_PARAMS;
+    const int m = model[s];
+    for (int64_t k = offsets[s] + threadIdx.x; k < offsets[s + 1]; k += blockDim.x) {
+      const double w = omega[k];
+      cplx e = {0.0, 0.0};
+      double sigma = 0.0;
+      switch (m) {
+        case DEBYE_MODEL_DEBYE:
+          e = c_debye(p[0], p[1], w * p[2]);
+          break;
+        case DEBYE_MODEL_HN:
+        case DEBYE_MODEL_CC:
+        case DEBYE_MODEL_CD: {
+          // (j w tau0)^alpha on the principal branch, then (1 + .)^beta
+          const double al = p[3], be = p[4];
+          const double mag = pow(w * p[2], al);
+          double sn, cs;
+          sincos(al * PI / 2, &sn, &cs);
+          const cplx den = c_pow(cplx{1.0 + mag * cs, mag * sn}, be);
+          const double dd = den.re * den.re + den.im * den.im;
+          e = {p[0] + p[1] * den.re / dd, -p[1] * den.im / dd};
+          break;
+        }
+        case DEBYE_MODEL_JONSCHER: {
+          const double f = p[1] * pow(w / p[2], p[3] - 1.0);
+          e = {p[0] + f, -f / tan(p[3] * PI / 2)};
+          break;
+        }
+        case DEBYE_MODEL_JONSCHER_EQ5: {
+          const double f = p[1] * pow(w / p[2], p[3]);
+          double sn, cs;
+          sincos(p[3] * PI / 2, &sn, &cs);
+          e = {p[0] + f * cs, -f * sn};
+          break;
+        }
+        case DEBYE_MODEL_CRIM: {
+          const double a = p[0];
+          const int nc = (int)p[1];
+          cplx acc = {0.0, 0.0};
+          for (int i = 0; i < nc && i < 3; ++i)
+            acc = c_add(acc, c_scale(c_pow(c_debye(p[5 + 3 * i], p[6 + 3 * i], w * p[7 + 3 * i]), a), p[2 + i]));
+          e = c_pow(acc, 1.0 / a);
+          break;
+        }
+        case DEBYE_MODEL_DEBYE_SUM: {
+          e = {p[0], 0.0};
+          for (int64_t j = pole_off[s]; j < pole_off[s + 1]; ++j) e = c_add(e, c_debye(0.0, pdeps[j], w * ptau[j]));
+          const double f = p[1] * pow(w / p[2], p[3] - 1.0);
+          e = c_add(e, cplx{f, -f / tan(p[3] * PI / 2)});
+          sigma = p[4];
+          break;
+        }
+        default:
+          set_status(status, DEBYE_EBOUNDS);
+      }
+      double vr = e.re, vi = -e.im;   // eps' and eps'' (Eq. 1)
+      if (nre && sigma != 0.0) {
+        vr *= 1.0 + sigma * nre[k];
+        vi *= 1.0 + sigma * nim[k];
+      }
+      er[k] = vr;
+      ei[k] = vi;
+    }
+  }
+}
+
+void launch_synth(int64_t S, const int64_t* offsets, const double* omega, const int32_t* model,
+                  const double* params, const int64_t* pole_off, const double* ptau,
+                  const double* pdeps, const double* nre, const double* nim, double* er, double* ei,
+                  int* status, int sms, cudaStream_t st) {
+  if (S <= 0) return;
+  int grid = (int)std::min<int64_t>(S, (int64_t)sms * 8);
+  k_synth<<<grid, 256, 0, st>>>(S, offsets, omega, model, params, pole_off, ptau, pdeps, nre, nim,
+                                er, ei, status);
+}
+
+}  // namespace debyefit

@@ -1,0 +1,30 @@
+// Per-N pass kernels for poles N = 1..4 (one translation unit per bucket so
+// the buckets compile in parallel).
+#include "eval.cuh"
+#include "launch.h"
+
+namespace debyefit {
+
+void launch_pass_b0(int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st) {
+  constexpr int LO = 1, HI = 4;
+  if (mixed) {
+    if (phase == PH_GRAM) {
+      const size_t smem = sizeof(float) * gram_smem_stride(HI) * block;
+      static bool attr_set = false;
+      if (!attr_set) {
+        cudaFuncSetAttribute(k_pass<PH_GRAM, LO, HI, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(float) * gram_smem_stride(HI) * MAX_BLOCK));
+        attr_set = true;
+      }
+      k_pass<PH_GRAM, LO, HI, true><<<grid, block, smem, st>>>(a);
+    }
+    else if (phase == PH_REFINE) k_pass<PH_REFINE, LO, HI, true><<<grid, block, 0, st>>>(a);
+    else k_pass<PH_GRAD, LO, HI, true><<<grid, block, 0, st>>>(a);
+  } else {
+    if (phase == PH_GRAM) k_pass<PH_GRAM, LO, HI, false><<<grid, block, 0, st>>>(a);
+    else if (phase == PH_REFINE) k_pass<PH_REFINE, LO, HI, false><<<grid, block, 0, st>>>(a);
+    else k_pass<PH_GRAD, LO, HI, false><<<grid, block, 0, st>>>(a);
+  }
+}
+
+}  // namespace debyefit

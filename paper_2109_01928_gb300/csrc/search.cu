@@ -1,0 +1,421 @@
+// Search kernels of libdebyefit: particle swarm (Sec. III-A, III-B), top-k
+// selection, projected L-BFGS polish, final re-solve and result assembly.
+//
+// Swarm update order matches the reference arithmetic exactly: explicit
+// __d*_rn operations (no FMA contraction) so that positions are bit-identical
+// to an FP64 implementation evaluating
+//   v = (omega v + (phi_p r1) (p - x)) + (phi_g r2) (g - x),  x = clip(x + v, lo, hi).
+#include <cmath>
+
+#include "launch.h"
+#include "search.h"
+
+namespace debyefit {
+
+__global__ void k_pso_init(SwarmArgs a) {
+  const int64_t Q = (int64_t)a.S * a.P;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = q / a.P, p = q % a.P;
+    const int N = a.n_poles[s];
+    const double lo = a.lo[s], hi = a.hi[s], span = __dsub_rn(hi, lo);
+    const uint64_t pp = rng_prefix(a.seed, TAG_INIT_POS, (uint64_t)s, 0);
+    const uint64_t pv = rng_prefix(a.seed, TAG_INIT_VEL, (uint64_t)s, 0);
+    for (int d = 0; d < a.nmax; ++d) {
+      double x = 0.0, v = 0.0;
+      if (d < N) {
+        x = __dadd_rn(lo, __dmul_rn(span, rng_uniform(pp, p, d)));
+        v = __dadd_rn(-span, __dmul_rn(__dmul_rn(2.0, span), rng_uniform(pv, p, d)));
+      }
+      a.x[q * a.nmax + d] = x;
+      a.v[q * a.nmax + d] = v;
+    }
+  }
+}
+
+__global__ void k_pso_move(SwarmArgs a) {
+  const int64_t Q = (int64_t)a.S * a.P;
+  const int gen = *a.gen;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = q / a.P, p = q % a.P;
+    const int N = a.n_poles[s];
+    const double lo = a.lo[s], hi = a.hi[s];
+    const int64_t gq = s * a.P + a.gbest[s];
+    const uint64_t p1 = rng_prefix(a.seed, TAG_R1, (uint64_t)s, (uint64_t)gen);
+    const uint64_t p2 = rng_prefix(a.seed, TAG_R2, (uint64_t)s, (uint64_t)gen);
+    for (int d = 0; d < N; ++d) {
+      const double x = a.x[q * a.nmax + d], v = a.v[q * a.nmax + d];
+      const double pb = a.pbx[q * a.nmax + d], gb = a.pbx[gq * a.nmax + d];
+      const double r1 = rng_uniform(p1, p, d), r2 = rng_uniform(p2, p, d);
+      const double t1 = __dmul_rn(a.omega, v);
+      const double t2 = __dmul_rn(__dmul_rn(a.phi_p, r1), __dsub_rn(pb, x));
+      const double t3 = __dmul_rn(__dmul_rn(a.phi_g, r2), __dsub_rn(gb, x));
+      const double vn = __dadd_rn(__dadd_rn(t1, t2), t3);
+      a.v[q * a.nmax + d] = vn;
+      a.x[q * a.nmax + d] = fmin(fmax(__dadd_rn(x, vn), lo), hi);
+    }
+  }
+}
+
+// Lexicographic (cost, index) minimum: lowest cost, lowest index on ties.
+__device__ __forceinline__ void argmin_merge(double& c, int& i, double c2, int i2) {
+  if (c2 < c || (c2 == c && i2 < i)) {
+    c = c2;
+    i = i2;
+  }
+}
+
+__device__ __forceinline__ void block_argmin(double& c, int& i) {
+  __shared__ double sc[32];
+  __shared__ int si[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    const double c2 = __shfl_down_sync(0xffffffffu, c, o);
+    const int i2 = __shfl_down_sync(0xffffffffu, i, o);
+    argmin_merge(c, i, c2, i2);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sc[wid] = c;
+    si[wid] = i;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    c = lane < nw ? sc[lane] : INFINITY;
+    i = lane < nw ? si[lane] : 0x7fffffff;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double c2 = __shfl_down_sync(0xffffffffu, c, o);
+      const int i2 = __shfl_down_sync(0xffffffffu, i, o);
+      argmin_merge(c, i, c2, i2);
+    }
+  }
+  __syncthreads();
+}
+
+// Personal bests (strictly lower cost replaces; generation 0 initialises) and
+// the global best per spectrum; one block per spectrum.
+__global__ void k_pso_best(SwarmArgs a, const double* __restrict__ cost) {
+  const int gen = *a.gen;
+  for (int64_t s = blockIdx.x; s < a.S; s += gridDim.x) {
+    const int N = a.n_poles[s];
+    double bc = INFINITY;
+    int bi = 0x7fffffff;
+    for (int p = threadIdx.x; p < a.P; p += blockDim.x) {
+      const int64_t q = s * a.P + p;
+      double c = cost[q];
+      if (!isfinite(c)) c = INFINITY;
+      double pc = a.pbc[q];
+      if (gen == 0 || c < pc) {
+        pc = c;
+        a.pbc[q] = c;
+        for (int d = 0; d < N; ++d) a.pbx[q * a.nmax + d] = a.x[q * a.nmax + d];
+      }
+      argmin_merge(bc, bi, pc, p);
+    }
+    block_argmin(bc, bi);
+    if (threadIdx.x == 0) {
+      a.gbest[s] = bi < a.P ? bi : 0;
+      if (a.trace) a.trace[s * (int64_t)(a.iters + 1) + gen] = bc;
+      if (a.evals) atomicAdd(a.evals, (double)a.P * (double)(a.offsets[s + 1] - a.offsets[s]));
+    }
+  }
+}
+
+__global__ void k_gen_advance(int* gen) { *gen += 1; }
+
+__global__ void k_add_scalar(double* dst, double v) { *dst += v; }
+
+// ------------------------------------------------------------------ top-k and polish
+// Lines l = s * T + j start from the j-th best personal best of spectrum s.
+__global__ void k_topk(SwarmArgs a, PolishArgs pa) {
+  extern __shared__ unsigned char taken_raw[];
+  unsigned char* taken = taken_raw;
+  for (int64_t s = blockIdx.x; s < a.S; s += gridDim.x) {
+    for (int p = threadIdx.x; p < a.P; p += blockDim.x) taken[p] = 0;
+    __syncthreads();
+    for (int j = 0; j < pa.T; ++j) {
+      double bc = INFINITY;
+      int bi = 0x7fffffff;
+      for (int p = threadIdx.x; p < a.P; p += blockDim.x)
+        if (!taken[p]) argmin_merge(bc, bi, a.pbc[s * a.P + p], p);
+      block_argmin(bc, bi);
+      if (threadIdx.x == 0) {
+        const int p = bi < a.P ? bi : 0;
+        taken[p] = 1;
+        const int64_t l = s * pa.T + j;
+        for (int d = 0; d < a.nmax; ++d) pa.th[l * a.nmax + d] = a.pbx[(s * a.P + p) * a.nmax + d];
+        pa.f[l] = bc;
+        pa.done[l] = 0;
+        pa.hcount[l] = 0;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Trial t of line l is candidate q = l * R + t of the polish evaluation.
+__global__ void k_polish_start(PolishArgs pa) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < pa.L;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    const int nmax = pa.nmax;
+    for (int t = 0; t < pa.R; ++t) {
+      const int64_t q = l * pa.R + t;
+      pa.active[q] = (t == 0) ? 1 : 0;
+      for (int d = 0; d < nmax; ++d) pa.tth[q * nmax + d] = pa.th[l * nmax + d];
+    }
+  }
+}
+
+// After the start evaluation: f, g of each line from trial slot 0.
+__global__ void k_polish_take0(PolishArgs pa) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < pa.L;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = l * pa.R;
+    pa.f[l] = pa.tcost[q];
+    for (int d = 0; d < pa.nmax; ++d) pa.g[l * pa.nmax + d] = pa.tgrad[q * pa.nmax + d];
+    pa.active[q] = 0;
+    if (!isfinite(pa.f[l])) pa.done[l] = 1;
+  }
+}
+
+__device__ __forceinline__ double dotn(const double* a, const double* b, int n) {
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s = fma(a[i], b[i], s);
+  return s;
+}
+
+__device__ void write_trials(const PolishArgs& pa, int64_t l, int N, double lo, double hi) {
+  const int nmax = pa.nmax;
+  const int t0 = pa.t0[l];
+  for (int t = 0; t < pa.R; ++t) {
+    const int64_t q = l * pa.R + t;
+    const int tt = t0 + t;
+    if (tt >= pa.max_trials) {
+      pa.active[q] = 0;
+      continue;
+    }
+    const double step = ldexp(1.0, -tt);
+    for (int d = 0; d < nmax; ++d) {
+      double v = 0.0;
+      if (d < N) v = fmin(fmax(pa.th[l * nmax + d] + step * pa.dir[l * nmax + d], lo), hi);
+      pa.tth[q * nmax + d] = v;
+    }
+    pa.active[q] = 1;
+  }
+}
+
+// Two-loop recursion (Nocedal and Wright, Alg. 7.4) for the direction d = -H g;
+// a non-descent direction is replaced by -g / max(1, |g|_inf) and the history cleared.
+__global__ void k_polish_dir(PolishArgs pa, const int32_t* n_poles, const double* lo_, const double* hi_) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < pa.L;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    pa.acc[l] = 0;
+    if (pa.done[l]) continue;
+    const int64_t s = l / pa.T;
+    const int N = n_poles[s];
+    const int nmax = pa.nmax, m = pa.m;
+    double q[NMAX], alpha[8];
+    const double* g = pa.g + l * nmax;
+    for (int d = 0; d < N; ++d) q[d] = g[d];
+    const int hc = pa.hcount[l];
+    // history slot of the k-th newest pair: (head - 1 - k) mod m, head = hc mod m ... stored oldest..newest
+    for (int k = hc - 1; k >= 0; --k) {
+      const double* sk = pa.hs + (l * m + k) * nmax;
+      const double* yk = pa.hy + (l * m + k) * nmax;
+      const double rho = 1.0 / dotn(yk, sk, N);
+      const double al = rho * dotn(sk, q, N);
+      for (int d = 0; d < N; ++d) q[d] -= al * yk[d];
+      alpha[k] = al;
+    }
+    double gamma;
+    if (hc > 0) {
+      const double* sn = pa.hs + (l * m + hc - 1) * nmax;
+      const double* yn = pa.hy + (l * m + hc - 1) * nmax;
+      gamma = dotn(sn, yn, N) / dotn(yn, yn, N);
+    } else {
+      double gi = 0.0;
+      for (int d = 0; d < N; ++d) gi = fmax(gi, fabs(g[d]));
+      gamma = 1.0 / fmax(1.0, gi);
+    }
+    for (int d = 0; d < N; ++d) q[d] *= gamma;
+    for (int k = 0; k < hc; ++k) {
+      const double* sk = pa.hs + (l * m + k) * nmax;
+      const double* yk = pa.hy + (l * m + k) * nmax;
+      const double rho = 1.0 / dotn(yk, sk, N);
+      const double be = rho * dotn(yk, q, N);
+      for (int d = 0; d < N; ++d) q[d] += sk[d] * (alpha[k] - be);
+    }
+    double gd = 0.0;
+    for (int d = 0; d < N; ++d) gd = fma(g[d], -q[d], gd);
+    double* dir = pa.dir + l * nmax;
+    if (!(gd < 0.0)) {
+      double gi = 0.0;
+      for (int d = 0; d < N; ++d) gi = fmax(gi, fabs(g[d]));
+      const double sc = 1.0 / fmax(1.0, gi);
+      for (int d = 0; d < N; ++d) dir[d] = -g[d] * sc;
+      pa.hcount[l] = 0;
+    } else {
+      for (int d = 0; d < N; ++d) dir[d] = -q[d];
+    }
+    pa.t0[l] = 0;
+    write_trials(pa, l, N, lo_[s], hi_[s]);
+  }
+}
+
+// Armijo test on the evaluated trials of each line, in order of decreasing step.
+__global__ void k_polish_accept(PolishArgs pa, const int32_t* n_poles, const double* lo_, const double* hi_,
+                                const int64_t* offsets) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < pa.L;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    if (pa.done[l] || pa.acc[l]) continue;
+    const int64_t s = l / pa.T;
+    const int N = n_poles[s];
+    const int nmax = pa.nmax, m = pa.m;
+    int n_active = 0;
+    int hit = -1;
+    for (int t = 0; t < pa.R; ++t) {
+      const int64_t q = l * pa.R + t;
+      if (!pa.active[q]) continue;
+      ++n_active;
+      if (hit >= 0) continue;
+      double gs = 0.0;
+      for (int d = 0; d < N; ++d)
+        gs = fma(pa.g[l * nmax + d], pa.tth[q * nmax + d] - pa.th[l * nmax + d], gs);
+      if (pa.tcost[q] <= pa.f[l] + pa.c1 * gs) hit = t;
+    }
+    if (pa.evals && n_active) atomicAdd(pa.evals, (double)n_active * (double)(offsets[s + 1] - offsets[s]));
+    for (int t = 0; t < pa.R; ++t) pa.active[l * pa.R + t] = 0;
+    if (hit >= 0) {
+      const int64_t q = l * pa.R + hit;
+      double sv[NMAX], yv[NMAX];
+      for (int d = 0; d < N; ++d) {
+        sv[d] = pa.tth[q * nmax + d] - pa.th[l * nmax + d];
+        yv[d] = pa.tgrad[q * nmax + d] - pa.g[l * nmax + d];
+      }
+      const double sy = dotn(sv, yv, N), yy = dotn(yv, yv, N);
+      if (sy > 2.220446049250313e-16 * yy) {
+        int hc = pa.hcount[l];
+        if (hc == m) {  // drop the oldest pair
+          for (int k = 1; k < m; ++k)
+            for (int d = 0; d < N; ++d) {
+              pa.hs[(l * m + k - 1) * nmax + d] = pa.hs[(l * m + k) * nmax + d];
+              pa.hy[(l * m + k - 1) * nmax + d] = pa.hy[(l * m + k) * nmax + d];
+            }
+          hc = m - 1;
+        }
+        for (int d = 0; d < N; ++d) {
+          pa.hs[(l * m + hc) * nmax + d] = sv[d];
+          pa.hy[(l * m + hc) * nmax + d] = yv[d];
+        }
+        pa.hcount[l] = hc + 1;
+      }
+      for (int d = 0; d < N; ++d) {
+        pa.th[l * nmax + d] = pa.tth[q * nmax + d];
+        pa.g[l * nmax + d] = pa.tgrad[q * nmax + d];
+      }
+      pa.f[l] = pa.tcost[q];
+      pa.acc[l] = 1;
+    } else if (n_active) {
+      pa.t0[l] += pa.R;
+      if (pa.t0[l] >= pa.max_trials) pa.done[l] = 1;
+      else write_trials(pa, l, N, lo_[s], hi_[s]);
+    }
+  }
+}
+
+// Best line per spectrum (lowest cost, lowest rank on ties), or the swarm's
+// global best when there is no polish; writes theta* of spectrum s to out[s].
+__global__ void k_pick_best(SwarmArgs a, PolishArgs pa, double* out_theta) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < a.S;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const double* src;
+    if (pa.T > 0) {
+      double bc = INFINITY;
+      int bj = 0x7fffffff;
+      for (int j = 0; j < pa.T; ++j) argmin_merge(bc, bj, pa.f[s * pa.T + j], j);
+      if (bj >= pa.T) bj = 0;
+      src = pa.th + (s * pa.T + bj) * a.nmax;
+    } else {
+      src = a.pbx + (s * a.P + a.gbest[s]) * a.nmax;
+    }
+    for (int d = 0; d < a.nmax; ++d) out_theta[s * a.nmax + d] = src[d];
+  }
+}
+
+// Poles sorted by ascending tau (stable), padded with zeros (Listing 2 layout).
+__global__ void k_assemble(int64_t S, int nmax, const int32_t* n_poles, const double* theta,
+                           const double* weights, const double* cost, double* eps_inf, double* d_eps,
+                           double* tau, double* final_cost) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int N = n_poles[s];
+    int idx[NMAX];
+    for (int i = 0; i < N; ++i) idx[i] = i;
+    for (int i = 1; i < N; ++i) {
+      const int v = idx[i];
+      int j = i - 1;
+      while (j >= 0 && theta[s * nmax + idx[j]] > theta[s * nmax + v]) {
+        idx[j + 1] = idx[j];
+        --j;
+      }
+      idx[j + 1] = v;
+    }
+    eps_inf[s] = weights[s * (nmax + 1)];
+    for (int i = 0; i < nmax; ++i) {
+      if (i < N) {
+        d_eps[s * nmax + i] = weights[s * (nmax + 1) + 1 + idx[i]];
+        tau[s * nmax + i] = exp10(theta[s * nmax + idx[i]]);
+      } else {
+        d_eps[s * nmax + i] = 0.0;
+        tau[s * nmax + i] = 0.0;
+      }
+    }
+    final_cost[s] = cost[s];
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+static int g1d(int64_t n, int sms) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8)); }
+
+void launch_pso_init(const SwarmArgs& a, int sms, cudaStream_t st) {
+  k_pso_init<<<g1d((int64_t)a.S * a.P, sms), 256, 0, st>>>(a);
+}
+void launch_pso_move(const SwarmArgs& a, int sms, cudaStream_t st) {
+  k_pso_move<<<g1d((int64_t)a.S * a.P, sms), 256, 0, st>>>(a);
+}
+void launch_pso_best(const SwarmArgs& a, const double* cost, int sms, cudaStream_t st) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.S, (int64_t)sms * 8));
+  k_pso_best<<<grid, 256, 0, st>>>(a, cost);
+}
+void launch_gen_advance(int* gen, cudaStream_t st) { k_gen_advance<<<1, 1, 0, st>>>(gen); }
+void launch_add_scalar(double* dst, double v, cudaStream_t st) { k_add_scalar<<<1, 1, 0, st>>>(dst, v); }
+void launch_topk(const SwarmArgs& a, const PolishArgs& pa, int sms, cudaStream_t st) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.S, (int64_t)sms * 8));
+  k_topk<<<grid, 256, a.P, st>>>(a, pa);
+}
+void launch_polish_start(const PolishArgs& pa, int sms, cudaStream_t st) {
+  k_polish_start<<<g1d(pa.L, sms), 256, 0, st>>>(pa);
+}
+void launch_polish_take0(const PolishArgs& pa, int sms, cudaStream_t st) {
+  k_polish_take0<<<g1d(pa.L, sms), 256, 0, st>>>(pa);
+}
+void launch_polish_dir(const PolishArgs& pa, const int32_t* n_poles, const double* lo, const double* hi,
+                       int sms, cudaStream_t st) {
+  k_polish_dir<<<g1d(pa.L, sms), 128, 0, st>>>(pa, n_poles, lo, hi);
+}
+void launch_polish_accept(const PolishArgs& pa, const int32_t* n_poles, const double* lo, const double* hi,
+                          const int64_t* offsets, int sms, cudaStream_t st) {
+  k_polish_accept<<<g1d(pa.L, sms), 128, 0, st>>>(pa, n_poles, lo, hi, offsets);
+}
+void launch_pick_best(const SwarmArgs& a, const PolishArgs& pa, double* out_theta, int sms, cudaStream_t st) {
+  k_pick_best<<<g1d(a.S, sms), 256, 0, st>>>(a, pa, out_theta);
+}
+void launch_assemble(int64_t S, int nmax, const int32_t* n_poles, const double* theta, const double* weights,
+                     const double* cost, double* eps_inf, double* d_eps, double* tau, double* final_cost,
+                     int sms, cudaStream_t st) {
+  k_assemble<<<g1d(S, sms), 256, 0, st>>>(S, nmax, n_poles, theta, weights, cost, eps_inf, d_eps, tau,
+                                           final_cost);
+}
+
+}  // namespace debyefit

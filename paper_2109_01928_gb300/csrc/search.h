@@ -1,0 +1,66 @@
+// Device-side state of the particle swarm and the L-BFGS polish.
+#pragma once
+#include "common.cuh"
+
+namespace debyefit {
+
+struct SwarmArgs {
+  int64_t S;
+  int32_t P, nmax, iters;
+  uint64_t seed;
+  double omega, phi_p, phi_g;
+  const int32_t* n_poles;
+  const double* lo;
+  const double* hi;
+  const int64_t* offsets;
+  double* x;       // [S*P][nmax] positions (log10 tau)
+  double* v;       // [S*P][nmax] velocities
+  double* pbx;     // [S*P][nmax] personal-best positions
+  double* pbc;     // [S*P]       personal-best costs
+  int32_t* gbest;  // [S]         global-best particle
+  int* gen;        // generation counter (device)
+  double* trace;   // [S][iters+1] or nullptr
+  double* evals;   // [1] or nullptr
+};
+
+struct PolishArgs {
+  int64_t L;       // lines = S * T
+  int32_t T;       // lines per spectrum
+  int32_t R;       // trial step lengths evaluated per round
+  int32_t nmax, m, max_trials;
+  double c1;
+  double* th;      // [L][nmax] current point
+  double* f;       // [L]
+  double* g;       // [L][nmax]
+  double* dir;     // [L][nmax]
+  double* hs;      // [L][m][nmax] history s (oldest first)
+  double* hy;      // [L][m][nmax] history y
+  int32_t* hcount; // [L]
+  int32_t* t0;     // [L] first trial index of the current round
+  int32_t* done;   // [L] line finished (no acceptable step or non-finite)
+  int32_t* acc;    // [L] step accepted in this iteration
+  double* tth;     // [L*R][nmax] trial points
+  double* tcost;   // [L*R]
+  double* tgrad;   // [L*R][nmax]
+  uint8_t* active; // [L*R] trial needs evaluation
+  double* evals;   // [1] or nullptr
+};
+
+void launch_pso_init(const SwarmArgs& a, int sms, cudaStream_t st);
+void launch_pso_move(const SwarmArgs& a, int sms, cudaStream_t st);
+void launch_pso_best(const SwarmArgs& a, const double* cost, int sms, cudaStream_t st);
+void launch_gen_advance(int* gen, cudaStream_t st);
+void launch_add_scalar(double* dst, double v, cudaStream_t st);
+void launch_topk(const SwarmArgs& a, const PolishArgs& pa, int sms, cudaStream_t st);
+void launch_polish_start(const PolishArgs& pa, int sms, cudaStream_t st);
+void launch_polish_take0(const PolishArgs& pa, int sms, cudaStream_t st);
+void launch_polish_dir(const PolishArgs& pa, const int32_t* n_poles, const double* lo, const double* hi,
+                       int sms, cudaStream_t st);
+void launch_polish_accept(const PolishArgs& pa, const int32_t* n_poles, const double* lo, const double* hi,
+                          const int64_t* offsets, int sms, cudaStream_t st);
+void launch_pick_best(const SwarmArgs& a, const PolishArgs& pa, double* out_theta, int sms, cudaStream_t st);
+void launch_assemble(int64_t S, int nmax, const int32_t* n_poles, const double* theta, const double* weights,
+                     const double* cost, double* eps_inf, double* d_eps, double* tau, double* final_cost,
+                     int sms, cudaStream_t st);
+
+}  // namespace debyefit

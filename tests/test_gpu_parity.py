@@ -1,0 +1,284 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: per-candidate cost relative error <= 1e-10 (FP64 path) and <= 1e-5
+(mixed path); gradients <= 1e-8 / 1e-4 relative (norm-wise per candidate);
+fitted spectra <= 1e-4 relative RMS.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import dls, fit, models, varpro
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+COST_TOL = {"fp64": 1e-10, "mixed": 1e-5}
+GRAD_TOL = {"fp64": 1e-8, "mixed": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def D():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2109_01928_gb300 import debyefit
+    debyefit.lib()   # raises if the library is not built
+    return debyefit
+
+
+def spectra_for(D, b, re, im):
+    return D.make_spectra(b.offsets, b.omega, re, im, b.n_poles, b.lo, b.hi, device="cuda")
+
+
+def oracle_costs(b, re, im, th, lam=dls.LAM_SEARCH):
+    out = np.empty(th.shape[:2])
+    wts = np.zeros(th.shape[:2] + (th.shape[2] + 1,))
+    for s in range(b.S):
+        a, c = b.offsets[s], b.offsets[s + 1]
+        N = int(b.n_poles[s])
+        out[s], w = dls.cost_population(b.omega[a:c], re[a:c], im[a:c], th[s, :, :N], lam)
+        wts[s, :, :N + 1] = w
+    return out, wts
+
+
+def ragged_batch(seed=3, S=20):
+    # every pole count 1..20 (all five kernel buckets), K from 2 to 700
+    b = W.mixed_batch(S=S, seed=seed, P=70, K_range=(2, 700), N_range=(1, 20))
+    b.n_poles[:] = np.arange(1, S + 1) % 20 + 1
+    return b
+
+
+# ------------------------------------------------------------------ target synthesis
+
+def test_synth_matches_oracle(D):
+    parts = [W.mixed_batch(S=40, seed=1), W.tabulated_batch(S=3, K=300, seed=2)]
+    j = W.mixed_batch(S=4, seed=4)
+    j.model[:] = [W.MODEL_JONSCHER_EQ5, W.MODEL_DEBYE, W.MODEL_HN, W.MODEL_CD]
+    j.params[1, :3] = [3.0, 10.0, 2e-10]
+    j.params[0, :4] = [4.0, 2.0, W.OMEGA_P, 0.5]
+    parts.append(j)
+    with D.Handle("fp64") as h:
+        for b in parts:
+            re, im = models.synthesize(b)
+            t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+            noise = (t(b.noise_re), t(b.noise_im)) if b.noise_re is not None else (None, None)
+            gr, gi = D.debye_synth_targets(h, t(b.offsets, torch.int64), t(b.omega), t(b.model, torch.int32),
+                                           t(b.params), t(b.pole_offsets, torch.int64), t(b.pole_tau),
+                                           t(b.pole_deps), *noise)
+            D.debye_sync(h)
+            np.testing.assert_allclose(gr.cpu().numpy(), re, rtol=1e-12, atol=0)
+            np.testing.assert_allclose(gi.cpu().numpy(), im, rtol=1e-11, atol=0)
+
+
+# ------------------------------------------------------------------ per-candidate cost
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_eval_population_ragged(D, prec):
+    b = ragged_batch()
+    re, im = models.synthesize(b)
+    th = W.population(b, 70, seed=9)
+    ref, wref = oracle_costs(b, re, im, th)
+    sp = spectra_for(D, b, re, im)
+    with D.Handle(prec) as h:
+        cost, w = D.debye_eval_population(h, sp, torch.as_tensor(th, device="cuda"), weights=True)
+        D.debye_sync(h)
+    cost, w = cost.cpu().numpy(), w.cpu().numpy()
+    rel = np.abs(cost - ref) / ref
+    assert rel.max() <= COST_TOL[prec], f"max relative cost error {rel.max():.3g}"
+    # weights: the cost is stationary in x, the weights are checked against their own scale
+    scale = np.abs(wref).max(axis=2, keepdims=True)
+    wtol = {"fp64": 1e-7, "mixed": 2e-3}[prec]
+    assert (np.abs(w - wref) / scale).max() <= wtol
+    # padding beyond N_s + 1 is zero
+    for s in range(b.S):
+        assert np.all(w[s, :, b.n_poles[s] + 1:] == 0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("cb", [32, 96, 128])
+def test_eval_block_sizes(D, prec, cb):
+    b = W.mixed_batch(S=5, seed=8, P=45, K_range=(40, 400), N_range=(3, 12))
+    re, im = models.synthesize(b)
+    th = W.population(b, 45, seed=2)
+    ref, _ = oracle_costs(b, re, im, th)
+    with D.Handle(prec, cands_per_block=cb) as h:
+        cost = D.debye_eval_population(h, spectra_for(D, b, re, im), torch.as_tensor(th, device="cuda"))
+    assert (np.abs(cost.cpu().numpy() - ref) / ref).max() <= COST_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_eval_full_size_sampled(D, prec):
+    # the 1024-spectrum workload at full population, checked on a seeded sample
+    b = W.workload("mixed_1024")
+    re, im = models.synthesize(b)
+    th = W.population(b, b.P, seed=0)
+    with D.Handle(prec) as h:
+        cost = D.debye_eval_population(h, spectra_for(D, b, re, im), torch.as_tensor(th, device="cuda"))
+        D.debye_sync(h)
+    cost = cost.cpu().numpy()
+    rng = np.random.default_rng(0)
+    for s, p in zip(rng.integers(0, b.S, 200), rng.integers(0, b.P, 200)):
+        a, c = b.offsets[s], b.offsets[s + 1]
+        N = int(b.n_poles[s])
+        ref = float(dls.cost(b.omega[a:c], re[a:c], im[a:c], th[s, p, :N]))
+        assert abs(cost[s, p] - ref) <= COST_TOL[prec] * ref, (s, p, cost[s, p], ref)
+
+
+def test_duplicate_tau_and_tiny_k(D):
+    b = W.mixed_batch(S=3, seed=5, P=8, K_range=(1, 3), N_range=(2, 4))
+    re, im = models.synthesize(b)
+    th = W.population(b, 8, seed=1)
+    th[:, :, 1] = th[:, :, 0]                     # two identical relaxation times
+    ref, _ = oracle_costs(b, re, im, th)
+    for prec in ("fp64", "mixed"):
+        with D.Handle(prec) as h:
+            cost = D.debye_eval_population(h, spectra_for(D, b, re, im), torch.as_tensor(th, device="cuda"))
+        assert (np.abs(cost.cpu().numpy() - ref) / ref).max() <= 10 * COST_TOL[prec]
+
+
+def test_input_errors(D):
+    b = W.mixed_batch(S=2, seed=1, P=4, K_range=(20, 30), N_range=(2, 3))
+    re, im = models.synthesize(b)
+    th = torch.as_tensor(W.population(b, 4), device="cuda")
+    with D.Handle("mixed") as h:
+        bad = re.copy()
+        bad[5] = np.nan
+        D.debye_eval_population(h, spectra_for(D, b, bad, im), th)
+        with pytest.raises(D.DebyeError) as e:
+            D.debye_sync(h)
+        assert e.value.code == D.DEBYE_ENOTFINITE
+        D.debye_sync(h)  # status was cleared
+        b2 = W.mixed_batch(S=2, seed=1, P=4, K_range=(20, 30), N_range=(2, 3))
+        b2.n_poles[0] = 0
+        with pytest.raises(D.DebyeError) as e:
+            D.debye_eval_population(h, spectra_for(D, b2, re, im), th)
+        assert e.value.code == D.DEBYE_EINVAL
+        with pytest.raises(D.DebyeError):
+            D.debye_eval_population(h, spectra_for(D, b, re, im), th, n_max=1)
+        empty = D.make_spectra(np.zeros(1, np.int64), np.zeros(0), np.zeros(0), np.zeros(0),
+                               np.zeros(0, np.int32), np.zeros(0), np.zeros(0), device="cuda")
+        c = D.debye_eval_population(h, empty, torch.zeros((0, 4, 3), dtype=torch.float64, device="cuda"))
+        assert c.shape == (0, 4)
+
+
+# ------------------------------------------------------------------ gradient
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cost_grad_matches_oracle(D, prec):
+    b = W.mixed_batch(S=6, seed=12, P=40, K_range=(60, 500), N_range=(2, 9))
+    re, im = models.synthesize(b)
+    th = W.population(b, 40, seed=3)
+    with D.Handle(prec) as h:
+        cost, grad = D.debye_cost_grad(h, spectra_for(D, b, re, im), torch.as_tensor(th, device="cuda"))
+        D.debye_sync(h)
+    cost, grad = cost.cpu().numpy(), grad.cpu().numpy()
+    checked = flipped = 0
+    for s in range(b.S):
+        a, c = b.offsets[s], b.offsets[s + 1]
+        N = int(b.n_poles[s])
+        for p in range(40):
+            x = dls.damped_solve(dls.basis(b.omega[a:c], th[s, p, :N]), dls.target(re[a:c], im[a:c]),
+                                 dls.LAM_SEARCH)
+            if np.min(np.abs(x[1:])) < 1e-6 * np.abs(x).max():
+                continue      # next to a flip kink the gradient is not defined
+            cref, gref = varpro.cost_grad(b.omega[a:c], re[a:c], im[a:c], th[s, p, :N])
+            assert abs(cost[s, p] - cref) <= COST_TOL[prec] * cref
+            err = np.linalg.norm(grad[s, p, :N] - gref) / np.linalg.norm(gref)
+            assert err <= GRAD_TOL[prec], (s, p, err)
+            assert np.all(grad[s, p, N:] == 0)
+            checked += 1
+            flipped += bool(np.any(x[1:] < 0))
+    assert checked > 150 and flipped > 20
+
+
+def test_gradient_central_differences(D):
+    b = W.mixed_batch(S=3, seed=21, P=16, K_range=(100, 300), N_range=(3, 6))
+    re, im = models.synthesize(b)
+    th = W.population(b, 16, seed=4)
+    sp = spectra_for(D, b, re, im)
+    h = 1e-6
+    with D.Handle("fp64") as hd:
+        _, g = D.debye_cost_grad(hd, sp, torch.as_tensor(th, device="cuda"))
+        g = g.cpu().numpy()
+        nm = th.shape[2]
+        fd = np.zeros_like(th)
+        for i in range(nm):
+            tp, tm = th.copy(), th.copy()
+            tp[:, :, i] += h
+            tm[:, :, i] -= h
+            cp = D.debye_eval_population(hd, sp, torch.as_tensor(tp, device="cuda")).cpu().numpy()
+            cm = D.debye_eval_population(hd, sp, torch.as_tensor(tm, device="cuda")).cpu().numpy()
+            fd[:, :, i] = (cp - cm) / (2 * h)
+    for s in range(b.S):
+        N = int(b.n_poles[s])
+        for p in range(16):
+            scale = max(1.0, np.abs(fd[s, p, :N]).max())
+            assert np.abs(g[s, p, :N] - fd[s, p, :N]).max() <= 1e-5 * scale
+
+
+def test_autograd_function(D):
+    b = W.mixed_batch(S=2, seed=2, P=8, K_range=(80, 120), N_range=(3, 4))
+    re, im = models.synthesize(b)
+    sp = spectra_for(D, b, re, im)
+    th = torch.as_tensor(W.population(b, 8, seed=6), device="cuda").requires_grad_(True)
+    with D.Handle("mixed") as h:
+        cost = D.cost_fn(th, h, sp)
+        cost.sum().backward()
+        _, g = D.debye_cost_grad(h, sp, th.detach())
+    torch.testing.assert_close(th.grad, g, rtol=0, atol=0)
+
+
+# ------------------------------------------------------------------ whole fit
+
+def fit_oracle(b, re, im, s, P, iters, topk, polish_iters, seed=0):
+    a, c = b.offsets[s], b.offsets[s + 1]
+    return fit.fit_spectrum(b.omega[a:c], re[a:c], im[a:c], int(b.n_poles[s]), float(b.lo[s]),
+                            float(b.hi[s]), P, iters, seed=seed, spectrum=s, topk=topk,
+                            polish_iters=polish_iters)
+
+
+def fitted(om, eps_inf, d_eps, tau):
+    return models.multi_debye(om, eps_inf, d_eps, tau)
+
+
+def test_fit_fp64_swarm_trace_matches_oracle(D):
+    b = W.single_hn()
+    re, im = models.synthesize(b)
+    with D.Handle("fp64") as h:
+        out = D.debye_fit_batch(h, spectra_for(D, b, re, im), P=64, iters=100, seed=0, polish_topk=0,
+                                trace=True)
+        D.debye_sync(h)
+    r = fit_oracle(b, re, im, 0, 64, 100, 0, 0)
+    tr = out["trace"].cpu().numpy()[0]
+    np.testing.assert_allclose(tr, r["trace"], rtol=1e-10, atol=0)
+    e_gpu = fitted(b.omega, out["eps_inf"].item(), out["d_eps"].cpu().numpy()[0], out["tau"].cpu().numpy()[0])
+    e_ref = fit.fitted_eps(b.omega, r)
+    assert dls.rel_rms(e_gpu, e_ref) <= 1e-8
+    assert out["evals"].item() == 64 * 101 * 50
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fit_with_polish_matches_oracle(D, prec):
+    b = W.mixed_batch(S=6, seed=31, P=32, K_range=(50, 200), N_range=(2, 5))
+    re, im = models.synthesize(b)
+    with D.Handle(prec) as h:
+        out = D.debye_fit_batch(h, spectra_for(D, b, re, im), P=32, iters=30, seed=0, polish_topk=4,
+                                polish_iters=30)
+        D.debye_sync(h)
+    ok = 0
+    for s in range(b.S):
+        a, c = b.offsets[s], b.offsets[s + 1]
+        r = fit_oracle(b, re, im, s, 32, 30, 4, 30)
+        N = int(b.n_poles[s])
+        e_gpu = fitted(b.omega[a:c], out["eps_inf"][s].item(), out["d_eps"][s, :N].cpu().numpy(),
+                       out["tau"][s, :N].cpu().numpy())
+        e_ref = fit.fitted_eps(b.omega[a:c], r)
+        rr = dls.rel_rms(e_gpu, e_ref)
+        gcost = out["final_cost"][s].item()
+        # same minimum, or a different minimum that is at least as good
+        assert rr <= 1e-4 or gcost <= r["cost_final"] * (1 + 1e-6), (s, rr, gcost, r["cost_final"])
+        ok += rr <= 1e-4
+        assert np.all(out["d_eps"][s, :N].cpu().numpy() >= 0)
+        assert np.all(np.diff(out["tau"][s, :N].cpu().numpy()) >= 0)
+    assert ok >= b.S // 2
