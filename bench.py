@@ -35,6 +35,9 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 WORKLOAD = "mixed_1024"
+# per workload: particles, swarm generations after the first, polished candidates, L-BFGS iterations
+SETTINGS = {"mixed_1024": (256, 200, 8, 50), "single_hn_k50": (64, 100, 8, 50),
+            "hn_256_k2000": (4096, 0, 32, 50), "tabulated_16384_k4096": (512, 100, 8, 50)}
 TOPK, POLISH_ITERS = 8, 50
 METRIC = "candidate cost evals x K per sec (batched mixed-precision fit)"
 UNIT = "cand*K/s"
@@ -50,11 +53,12 @@ def _oracle_chunk(job):
     sys.path.insert(0, ROOT)
     import workloads as W_
     from oracle import dls, models, pso
-    spectra, gens = job
-    full = W_.workload(WORKLOAD)
+    name, P, spectra, gens = job
+    full = W_.workload(name)
     work, secs = 0, 0.0
     for s in spectra:
         b = full.subset([s])
+        b.P = P
         re, im = models.synthesize(b)
         t0 = time.perf_counter()
         pso.pso(lambda th: dls.cost_population(b.omega, re, im, th)[0], int(b.n_poles[0]), float(b.lo[0]),
@@ -70,7 +74,7 @@ def oracle_rate(n_spectra: int, gens: int, procs: int, seed: int = 0):
     rng = np.random.default_rng(seed)
     S = W.workload(WORKLOAD).S
     picks = [int(s) for s in rng.choice(S, n_spectra, replace=False)]
-    chunks = [(picks[i::procs], gens) for i in range(procs) if picks[i::procs]]
+    chunks = [(WORKLOAD, SETTINGS[WORKLOAD][0], picks[i::procs], gens) for i in range(procs) if picks[i::procs]]
     # one BLAS thread per process, so `procs` is the number of cores used
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[v] = "1"
@@ -83,7 +87,9 @@ def oracle_rate(n_spectra: int, gens: int, procs: int, seed: int = 0):
 
 def cpu_baseline(quick: bool):
     cores = os.cpu_count() or 1
-    n1, nall = (4, max(cores, 8)) if quick else (16, max(4 * cores, 32))
+    b = W.workload(WORKLOAD)
+    heavy = float(np.mean(b.K)) * SETTINGS[WORKLOAD][0] > 3e5   # per-spectrum oracle work
+    n1, nall = (4, cores) if (quick or heavy) else (16, max(4 * cores, 32))
     r1, w1, t1 = oracle_rate(n1, 2, 1)
     ra, wa, ta = oracle_rate(nall, 2, cores)
     try:
@@ -92,7 +98,7 @@ def cpu_baseline(quick: bool):
     except Exception:
         model = ""
     return {"value": ra, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{nall} seeded spectra of {WORKLOAD}, full population P=256, 2 swarm generations "
+            "sample": f"{nall} seeded spectra of {WORKLOAD}, full population P={SETTINGS[WORKLOAD][0]}, 2 swarm generations "
                       f"(init + 1 update), numpy FP64 QR per candidate, {cores} spawned processes; "
                       f"rate = total work / slowest process's compute time",
             "single_thread": {"value": r1, "sample": f"{n1} spectra, 1 process", "seconds": t1},
@@ -170,6 +176,7 @@ def load_traffic(kind: str):
 
 
 def main():
+    global WORKLOAD, TOPK, POLISH_ITERS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -178,14 +185,24 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--iters", type=int, default=None, help="swarm generations (default: the workload's)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(SETTINGS))
+    ap.add_argument("--kernel-case", type=int, default=0, metavar="S",
+                    help="profiling case: evaluate the first S spectra of the workload at full "
+                         "population twice (debye_eval_population) and exit")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="precision of --kernel-case")
     args = ap.parse_args()
 
+    WORKLOAD = args.workload
+    P_w, iters_w, TOPK, POLISH_ITERS = SETTINGS[WORKLOAD]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.kernel_case:
+        return kernel_case(args.kernel_case, args.precision, P_w)
 
     # the oracle baseline runs first, in spawned processes, before any CUDA call
     cpu = None
@@ -221,7 +238,8 @@ def main():
         return float(t.item())
 
     b = W.workload(WORKLOAD, seed=rank)
-    iters = b.iters if args.iters is None else args.iters
+    b.P = P_w
+    iters = iters_w if args.iters is None else args.iters
     S = b.S
     nmax = b.n_max
     tt = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
@@ -229,9 +247,10 @@ def main():
     omega_d = tt(b.omega)
     # target synthesis (Eqs. 4-6) on the device, once, outside the timed region
     with D.Handle("fp64") as hs:
+        noise = (tt(b.noise_re), tt(b.noise_im)) if b.noise_re is not None else (None, None)
         eps_re_d, eps_im_d = D.debye_synth_targets(hs, offsets_d, omega_d, tt(b.model, torch.int32),
                                                     tt(b.params), tt(b.pole_offsets, torch.int64),
-                                                    tt(b.pole_tau), tt(b.pole_deps))
+                                                    tt(b.pole_tau), tt(b.pole_deps), *noise)
         D.debye_sync(hs)
     sp = D.Spectra(offsets_d, omega_d, eps_re_d, eps_im_d, tt(b.n_poles, torch.int32), tt(b.lo), tt(b.hi),
                    np.ascontiguousarray(b.offsets, np.int64), np.ascontiguousarray(b.n_poles, np.int32))
@@ -351,9 +370,11 @@ def main():
         "warmup": args.warmup, "ms_per_step": sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded HN/CC/CD/Jonscher/CRIM spectra, targets synthesised on the device)",
-        "config": {"workload": f"{WORKLOAD}: {S} spectra, K 50-1000 (sum {int(b.K.sum())}), N 2-12, "
-                               f"P={b.P}, {iters} swarm generations, top-{TOPK} x {POLISH_ITERS} L-BFGS "
-                               f"polish, mixed precision (FP32 Gram, FP64 solve, float-float residual)",
+        "config": {"workload": f"{WORKLOAD}: {S} spectra, K {int(b.K.min())}-{int(b.K.max())} "
+                               f"(sum {int(b.K.sum())}), N {int(b.n_poles.min())}-{int(b.n_poles.max())}, "
+                               f"P={b.P}, {iters} swarm generations after the first, top-{TOPK} x "
+                               f"{POLISH_ITERS} L-BFGS polish, mixed precision (FP32 Gram, FP64 solve, "
+                               f"float-float residual)",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -372,6 +393,28 @@ def main():
         dist.destroy_process_group()
 
 
+def kernel_case(S: int, precision: str, P: int):
+    """A small fixed case for kernel profilers: one workload subset, two evaluations."""
+    import torch
+    from paper_2109_01928_gb300 import debyefit as D
+    b = W.workload(WORKLOAD).subset(np.arange(S))
+    tt = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    om, offs = tt(b.omega), tt(b.offsets, torch.int64)
+    with D.Handle(precision) as h:
+        noise = (tt(b.noise_re), tt(b.noise_im)) if b.noise_re is not None else (None, None)
+        er, ei = D.debye_synth_targets(h, offs, om, tt(b.model, torch.int32), tt(b.params),
+                                       tt(b.pole_offsets, torch.int64), tt(b.pole_tau), tt(b.pole_deps), *noise)
+        sp = D.Spectra(offs, om, er, ei, tt(b.n_poles, torch.int32), tt(b.lo), tt(b.hi),
+                       np.ascontiguousarray(b.offsets), np.ascontiguousarray(b.n_poles, np.int32))
+        b.P = P
+        th = torch.as_tensor(W.population(b, P, seed=0), device="cuda")
+        for _ in range(2):
+            c = D.debye_eval_population(h, sp, th)
+        D.debye_sync(h)
+    print(json.dumps({"kernel_case": WORKLOAD, "spectra": S, "P": P, "precision": precision,
+                      "mean_cost": float(c.mean())}))
+
+
 def reference_arm(args, rank, world):
     """The FP64 oracle on the host cores, on bounded samples of the same workload."""
     if rank != 0:
@@ -385,7 +428,8 @@ def reference_arm(args, rank, world):
             work.append(w)
     value = sum(work) / sum(times)
     cpu = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"per step {max(cores, 4)} seeded spectra of {WORKLOAD}, P=256, 2 swarm generations"}
+           "sample": f"per step {max(cores, 4)} seeded spectra of {WORKLOAD}, P={SETTINGS[WORKLOAD][0]}, "
+                     f"2 swarm generations"}
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                       "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,

@@ -236,6 +236,7 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
       ab.units = a.units + g.begin[b];
       ab.n_units = n;
       const int grid = std::max(1, std::min(n, sms * 16));
+      const int pblock = cb * a.ks;
       ProfEntry pe;
       if (prof_on) {
         double fl = 0.0;
@@ -247,11 +248,11 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
         prof_begin(phase, fl, st, pe);
       }
       switch (b) {
-        case 0: launch_pass_b0(phase, mixed, ab, grid, cb, st); break;
-        case 1: launch_pass_b1(phase, mixed, ab, grid, cb, st); break;
-        case 2: launch_pass_b2(phase, mixed, ab, grid, cb, st); break;
-        case 3: launch_pass_b3(phase, mixed, ab, grid, cb, st); break;
-        default: launch_pass_b4(phase, mixed, ab, grid, cb, st); break;
+        case 0: launch_pass_b0(phase, mixed, ab, grid, pblock, st); break;
+        case 1: launch_pass_b1(phase, mixed, ab, grid, pblock, st); break;
+        case 2: launch_pass_b2(phase, mixed, ab, grid, pblock, st); break;
+        case 3: launch_pass_b3(phase, mixed, ab, grid, pblock, st); break;
+        default: launch_pass_b4(phase, mixed, ab, grid, pblock, st); break;
       }
       if (prof_on) prof_end(pe, st);
       ++launches;
@@ -268,19 +269,33 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
   int rc;
   a.n_units = (int)g.units.size();
   if (a.n_units == 0) return DEBYE_OK;
+  if (a.ks < 1 || a.ks > 32 || (a.ks & (a.ks - 1)) || cb * a.ks > MAX_BLOCK)
+    return fail(DEBYE_EINTERNAL, "bad work layout (%d candidates x %d lanes)", cb, a.ks);
+  const int gblock = warp_round(cb);
   if ((rc = per_bucket(PH_GRAM))) return rc;
-  timed(DEBYE_KERNEL_SOLVE, [&] { launch_solve(a, cb, sms, st); });
+  timed(DEBYE_KERNEL_SOLVE, [&] { launch_solve(a, gblock, sms, st); });
   if ((rc = check_launch("solve"))) return rc;
   for (int it = 0; it < steps; ++it) {
     if ((rc = per_bucket(PH_REFINE))) return rc;
     const bool last = it + 1 == steps;
-    timed(DEBYE_KERNEL_FINISH, [&] { launch_finish(a, last ? 1 : 0, cost, weights, g1, cb, sms, st); });
+    timed(DEBYE_KERNEL_FINISH, [&] { launch_finish(a, last ? 1 : 0, cost, weights, g1, gblock, sms, st); });
     if ((rc = check_launch("finish"))) return rc;
   }
   if (grad) {
-    timed(DEBYE_KERNEL_GRAD, [&] { launch_grad_prep(a, g1, cb, sms, st); });
+    // S g_hat overwrites g1 (no longer needed) for the adjoint refinement
+    timed(DEBYE_KERNEL_GRAD, [&] { launch_grad_prep(a, g1, mixed ? g1 : nullptr, gblock, sms, st); });
+    if (mixed) {
+      EvalArgs aw = a;   // residual pass on x := w against b = 0: rt = -A^T A w
+      aw.sc.x = a.sc.w;
+      aw.zero_b = 1;
+      EvalArgs saved = a;
+      a = aw;
+      if ((rc = per_bucket(PH_REFINE))) return rc;
+      a = saved;
+      timed(DEBYE_KERNEL_GRAD, [&] { launch_adjoint_refine(a, g1, gblock, sms, st); });
+    }
     if ((rc = per_bucket(PH_GRAD))) return rc;
-    timed(DEBYE_KERNEL_GRAD, [&] { launch_grad_finish(a, grad, cb, sms, st); });
+    timed(DEBYE_KERNEL_GRAD, [&] { launch_grad_finish(a, grad, gblock, sms, st); });
     if ((rc = check_launch("gradient"))) return rc;
   }
   return DEBYE_OK;
@@ -308,7 +323,8 @@ static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_
     qb[s] = (int32_t)(s * P);
     qe[s] = (int32_t)((s + 1) * P);
   }
-  const int cb = h->block_size(pl);
+  int cb, ks;
+  choose_layout(P, h->opt.cands_per_block, &cb, &ks);
   UnitGroups g;
   build_units(pl, qb, qe, cb, g);
   if ((rc = h->upload_units(g, h->ws_units, st))) return rc;
@@ -325,6 +341,7 @@ static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_
   a.eps_im = sp->eps_im;
   a.h0 = (const double*)h->ws_h0.p;
   a.active = nullptr;
+  a.ks = ks;
   a.lam = h->opt.lam_search;
   a.status = h->d_status;
   const bool mixed = h->opt.precision == DEBYE_PREC_MIXED;
@@ -340,9 +357,6 @@ int debye_ctx::eval_steps(bool with_grad) const {
   return (with_grad && mixed) ? std::max(opt.refine_steps, 2) : opt.refine_steps;
 }
 
-int debye_ctx::block_size(const Plan&) const {
-  return opt.cands_per_block > 0 ? opt.cands_per_block : 64;
-}
 
 // ------------------------------------------------------------------ C ABI
 extern "C" {

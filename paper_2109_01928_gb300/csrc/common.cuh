@@ -59,6 +59,8 @@ struct EvalArgs {
   const double* eps_im;
   const double* h0;        // [S] sum_k eps'_k
   const uint8_t* active;   // [Q] optional candidate mask (nullptr: all)
+  int32_t ks;              // lanes per candidate in the pass kernels (power of two <= 32)
+  int32_t zero_b;          // residual pass against b = 0 (t = -A^T A x), for the adjoint refinement
   double lam;
   Scratch sc;
   int* status;             // device status word
@@ -141,6 +143,13 @@ __device__ __forceinline__ void ff_add_prod(float& ah, float& al, float xh, floa
   two_sum(ah, p, s, e);
   ah = s;
   al = __fadd_rn(al, __fadd_rn(e, pe));
+}
+
+// Float-float product (ph, pl) = (ah, al) * (bh, bl) to about 2^-46 relative.
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& ph, float& pl) {
+  ph = __fmul_rn(ah, bh);
+  pl = __fmaf_rn(ah, bh, -ph);
+  pl = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, pl));
 }
 
 // (hi, lo) renormalised so that hi = fl(hi + lo) (Fast2Sum, |hi| >= |lo|).

@@ -1,6 +1,12 @@
-// Per-N passes over the frequency samples of one candidate (one thread per
-// candidate, all threads of a warp belong to the same spectrum, so every
-// per-sample load is a warp-uniform broadcast).
+// Per-N passes over the frequency samples of one candidate.
+//
+// Thread mapping: a group of `ks` consecutive lanes (ks = a.ks, a power of two
+// <= 32) evaluates one candidate; lane `slice` of the group sums the samples
+// k0 + slice, k0 + slice + ks, ... and the group then reduces its partial sums
+// with warp shuffles. All lanes of a block belong to the same spectrum. ks = 1
+// (one thread per candidate, every per-sample load a warp-wide broadcast) is
+// used for full populations; ks > 1 keeps warps full when a spectrum has only
+// a few candidates (line-search points, one re-solve per spectrum).
 //
 //   gram_unit    G = A^T A (packed, (N+1)x(N+1)) and h = A^T b of the stacked
 //                real basis of Eq. 7 (rows: eps' and eps'' of every sample).
@@ -8,9 +14,12 @@
 //   grad_unit    projections of the derivative columns needed by the
 //                variable-projection gradient.
 //
-// MIXED = true : FP32 basis and Gram (Sec. 8a rows a2/a3 on the FP32 pipe);
-//                residual in float-float, so rr carries ~2^-44 relative error.
+// MIXED = true : FP32 basis and Gram; residuals, ||r||^2 and every projection on a
+//                residual in float-float (Dot2 / TwoSum).
 // MIXED = false: everything in FP64.
+//
+// No lane returns before the group reduction: lanes without a candidate (the
+// tail of a unit, masked line-search points) contribute zeros.
 #pragma once
 #include "common.cuh"
 
@@ -31,31 +40,71 @@ __host__ __device__ constexpr int gram_smem_stride(int N) { return (2 * N + N * 
 
 extern __shared__ __align__(16) unsigned char dyn_smem[];
 
+// ------------------------------------------------------------------ group reductions
+__device__ __forceinline__ float group_sum(float v, int ks) {
+  for (int o = ks >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double group_sum(double v, int ks) {
+  for (int o = ks >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// Float-float sum over the group: leading parts by TwoSum, low parts added.
+__device__ __forceinline__ void group_sum_ff(float& h, float& l, int ks) {
+  for (int o = ks >> 1; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
+    float s, e;
+    two_sum(h, h2, s, e);
+    h = s;
+    l = __fadd_rn(__fadd_rn(l, l2), e);
+  }
+}
+
+struct Lane {
+  int q;       // candidate
+  int slice;   // sample phase within the group
+  int ks;      // lanes per candidate
+  bool act;    // this lane's candidate is evaluated
+};
+
+__device__ __forceinline__ Lane lane_of(const EvalArgs& a, const Unit& u, bool need_ok) {
+  Lane l;
+  l.ks = a.ks;
+  l.slice = (int)threadIdx.x & (a.ks - 1);
+  l.q = u.q0 + (int)threadIdx.x / a.ks;
+  l.act = l.q < u.q1;
+  if (l.act && a.active) l.act = a.active[l.q] != 0;
+  if (l.act && need_ok) l.act = a.sc.fail[l.q] == 0;
+  return l;
+}
+
 // ------------------------------------------------------------------ Gram
 template <int N, bool MIXED>
 __device__ __forceinline__ void gram_unit(const EvalArgs& a, const Unit& u) {
-  const int q = u.q0 + (int)threadIdx.x;
-  if (q >= u.q1) return;
-  if (a.active && !a.active[q]) return;
+  const Lane ln = lane_of(a, u, false);
+  const int q = ln.act ? ln.q : u.q0;
   constexpr int NP = Acc<N>::NP;
   const double* th = a.theta + (int64_t)q * a.sc.nmax;
   const int64_t Q = a.sc.Q;
+  const int64_t kbeg = u.k0 + ln.slice;
   if constexpr (MIXED) {
-    // Two-level FP32 accumulation: registers sum GRAM_BLOCK consecutive samples,
-    // then each block is added into this thread's slice of shared memory (entry e
-    // of thread t at outer[t * SA + e], SA odd and known at compile time, so every
-    // access is an immediate offset). The rounding error then grows like
-    // (GRAM_BLOCK + K / GRAM_BLOCK) instead of K.
+    // Two-level FP32 accumulation: registers sum GRAM_BLOCK of this lane's
+    // samples, then each block is added into the lane's slice of shared memory
+    // (entry e of thread t at outer[t * SA + e], SA odd and known at compile
+    // time, so every access is an immediate offset). The rounding error grows
+    // like (GRAM_BLOCK + K / GRAM_BLOCK) instead of K.
     constexpr int SA = gram_smem_stride(N);
     float* outer = reinterpret_cast<float*>(dyn_smem) + threadIdx.x * SA;
-    constexpr int bs = 1;
 #pragma unroll
     for (int e = 0; e < SA; ++e) outer[e] = 0.f;
     float tau[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) tau[i] = __double2float_rn(exp10(th[i]));
-    for (int64_t kb = u.k0; kb < u.k1; kb += GRAM_BLOCK) {
-      const int64_t ke = min(u.k1, kb + (int64_t)GRAM_BLOCK);
+    for (int i = 0; i < N; ++i) tau[i] = ln.act ? __double2float_rn(exp10(th[i])) : 0.f;
+    const int64_t kend = ln.act ? u.k1 : kbeg;
+    const int64_t step = ln.ks;
+    for (int64_t kb = kbeg; kb < kend; kb += step * GRAM_BLOCK) {
+      const int64_t ke = min(kend, kb + step * GRAM_BLOCK);
       float g0[N], hv[N], gp[NP];
 #pragma unroll
       for (int i = 0; i < N; ++i) {
@@ -64,9 +113,11 @@ __device__ __forceinline__ void gram_unit(const EvalArgs& a, const Unit& u) {
       }
 #pragma unroll
       for (int i = 0; i < NP; ++i) gp[i] = 0.f;
+      float4 vn = __ldg(&a.kf32[kb]);
 #pragma unroll 1
-      for (int64_t k = kb; k < ke; ++k) {
-        const float4 v = __ldg(&a.kf32[k]);
+      for (int64_t k = kb; k < ke; k += step) {
+        const float4 v = vn;
+        if (k + step < kend) vn = __ldg(&a.kf32[k + step]);   // next sample in flight
         float re[N], im[N];
 #pragma unroll
         for (int i = 0; i < N; ++i) {
@@ -88,37 +139,46 @@ __device__ __forceinline__ void gram_unit(const EvalArgs& a, const Unit& u) {
       }
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        outer[i * bs] += g0[i];
-        outer[(N + i) * bs] += hv[i];
+        outer[i] += g0[i];
+        outer[N + i] += hv[i];
       }
 #pragma unroll
-      for (int i = 0; i < NP; ++i) outer[(2 * N + i) * bs] += gp[i];
+      for (int i = 0; i < NP; ++i) outer[2 * N + i] += gp[i];
     }
+    const bool wr = ln.act && ln.slice == 0;
     double* G = a.sc.G;
-    G[(int64_t)pk(0, 0) * Q + q] = (double)(u.k1 - u.k0);
+    const int hb = (a.sc.nmax + 1) * (a.sc.nmax + 2) / 2;
+    if (wr) {
+      G[(int64_t)pk(0, 0) * Q + q] = (double)(u.k1 - u.k0);
+      G[(int64_t)hb * Q + q] = a.h0[u.s];
+    }
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      G[(int64_t)pk(i + 1, 0) * Q + q] = (double)outer[i * bs];
+      const float g0s = group_sum(outer[i], ln.ks);
+      const float hs = group_sum(outer[N + i], ln.ks);
+      if (wr) {
+        G[(int64_t)pk(i + 1, 0) * Q + q] = (double)g0s;
+        G[(int64_t)(hb + 1 + i) * Q + q] = (double)hs;
+      }
 #pragma unroll
-      for (int j = 0; j <= i; ++j)
-        G[(int64_t)pk(i + 1, j + 1) * Q + q] = (double)outer[(2 * N + i * (i + 1) / 2 + j) * bs];
+      for (int j = 0; j <= i; ++j) {
+        const float v = group_sum(outer[2 * N + i * (i + 1) / 2 + j], ln.ks);
+        if (wr) G[(int64_t)pk(i + 1, j + 1) * Q + q] = (double)v;
+      }
     }
-    const int hb = (a.sc.nmax + 1) * (a.sc.nmax + 2) / 2;
-    G[(int64_t)hb * Q + q] = a.h0[u.s];
-#pragma unroll
-    for (int i = 0; i < N; ++i) G[(int64_t)(hb + 1 + i) * Q + q] = (double)outer[(N + i) * bs];
   } else {
     double tau[N], g0[N], hv[N], gp[NP];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      tau[i] = exp10(th[i]);
+      tau[i] = ln.act ? exp10(th[i]) : 0.0;
       g0[i] = 0.0;
       hv[i] = 0.0;
     }
 #pragma unroll
     for (int i = 0; i < NP; ++i) gp[i] = 0.0;
+    const int64_t kend = ln.act ? u.k1 : kbeg;
 #pragma unroll 1
-    for (int64_t k = u.k0; k < u.k1; ++k) {
+    for (int64_t k = kbeg; k < kend; k += ln.ks) {
       const double w = __ldg(&a.omega[k]);
       const double br = __ldg(&a.eps_re[k]);
       const double bi = __ldg(&a.eps_im[k]);
@@ -141,18 +201,27 @@ __device__ __forceinline__ void gram_unit(const EvalArgs& a, const Unit& u) {
         for (int j = 0; j <= i; ++j)
           gp[i * (i + 1) / 2 + j] = fma(re[i], re[j], fma(im[i], im[j], gp[i * (i + 1) / 2 + j]));
     }
+    const bool wr = ln.act && ln.slice == 0;
     double* G = a.sc.G;
-    G[(int64_t)pk(0, 0) * Q + q] = (double)(u.k1 - u.k0);
+    const int hb = (a.sc.nmax + 1) * (a.sc.nmax + 2) / 2;
+    if (wr) {
+      G[(int64_t)pk(0, 0) * Q + q] = (double)(u.k1 - u.k0);
+      G[(int64_t)hb * Q + q] = a.h0[u.s];
+    }
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      G[(int64_t)pk(i + 1, 0) * Q + q] = g0[i];
+      const double g0s = group_sum(g0[i], ln.ks);
+      const double hs = group_sum(hv[i], ln.ks);
+      if (wr) {
+        G[(int64_t)pk(i + 1, 0) * Q + q] = g0s;
+        G[(int64_t)(hb + 1 + i) * Q + q] = hs;
+      }
 #pragma unroll
-      for (int j = 0; j <= i; ++j) G[(int64_t)pk(i + 1, j + 1) * Q + q] = gp[i * (i + 1) / 2 + j];
+      for (int j = 0; j <= i; ++j) {
+        const double v = group_sum(gp[i * (i + 1) / 2 + j], ln.ks);
+        if (wr) G[(int64_t)pk(i + 1, j + 1) * Q + q] = v;
+      }
     }
-    const int hb = (a.sc.nmax + 1) * (a.sc.nmax + 2) / 2;
-    G[(int64_t)hb * Q + q] = a.h0[u.s];
-#pragma unroll
-    for (int i = 0; i < N; ++i) G[(int64_t)(hb + 1 + i) * Q + q] = hv[i];
   }
 }
 
@@ -161,39 +230,54 @@ __device__ __forceinline__ void gram_unit(const EvalArgs& a, const Unit& u) {
 // rt[1 + j] = (A^T (b - A x))_j, j = 0..N.
 template <int N, bool MIXED>
 __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
-  const int q = u.q0 + (int)threadIdx.x;
-  if (q >= u.q1) return;
-  if (a.active && !a.active[q]) return;
-  if (a.sc.fail[q]) return;
+  const Lane ln = lane_of(a, u, true);
+  const int q = ln.act ? ln.q : u.q0;
   const double* th = a.theta + (int64_t)q * a.sc.nmax;
   const int64_t Q = a.sc.Q;
   const double* X = a.sc.x;
+  const int64_t kbeg = u.k0 + ln.slice;
+  const int64_t kend = ln.act ? u.k1 : kbeg;
+  const int64_t step = ln.ks;
   if constexpr (MIXED) {
     // t = A^T r is a float-float dot product (Dot2) of the float-float basis and
     // residual: the refinement step multiplies its error by M^-1, large along
     // nearly collinear poles, and a flipped cost is first-order in the weights.
-    float th_[N], tl_[N], wh[N], wl[N], th_t[N], tl_t[N];
-    float w0h, w0l;
-    split_double(X[q], w0h, w0l);
+    // It also sums G_ii = ||a_i||^2 = sum_k re_i(k) (re^2 + im^2 = re for a Debye
+    // column) in float-float: the damping lam G_ii x_i^2 then uses the exact
+    // column norms, not the FP32 Gram's diagonal.
+    float th_[N], tl_[N], wh[N], wl[N], th_t[N], tl_t[N], gdh[N], gdl[N];
+    float w0h = 0.f, w0l = 0.f;
+    if (ln.act) split_double(X[q], w0h, w0l);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      split_double(exp10(th[i]), th_[i], tl_[i]);
-      split_double(X[(int64_t)(i + 1) * Q + q], wh[i], wl[i]);
+      th_[i] = tl_[i] = wh[i] = wl[i] = 0.f;
+      if (ln.act) {
+        split_double(exp10(th[i]), th_[i], tl_[i]);
+        split_double(X[(int64_t)(i + 1) * Q + q], wh[i], wl[i]);
+      }
       th_t[i] = 0.f;
       tl_t[i] = 0.f;
+      gdh[i] = 0.f;
+      gdl[i] = 0.f;
     }
     float t0h = 0.f, t0l = 0.f, rrh = 0.f, rrl = 0.f;
+    const int64_t k0s = kbeg < u.k1 ? kbeg : u.k0;
+    float4 vhn = __ldg(&a.kf32[k0s]), vln = __ldg(&a.kff[k0s]);
 #pragma unroll 1
-    for (int64_t k = u.k0; k < u.k1; ++k) {
-      const float4 vh = __ldg(&a.kf32[k]);
-      const float4 vl = __ldg(&a.kff[k]);
+    for (int64_t k = kbeg; k < kend; k += step) {
+      const float4 vh = vhn, vl = vln;
+      if (k + step < kend) {   // next sample in flight during this one
+        vhn = __ldg(&a.kf32[k + step]);
+        vln = __ldg(&a.kff[k + step]);
+      }
       float reh[N], rel[N], imh[N], iml[N];
       // residual of the real row: eps' - eps_inf - sum x_i re_i
+      const float byh = a.zero_b ? 0.f : vh.y, byl = a.zero_b ? 0.f : vl.y;
       float arh, arl, aih, ail;
-      two_sum(vh.y, -w0h, arh, arl);
-      arl = __fadd_rn(arl, __fsub_rn(vl.y, w0l));
-      aih = vh.z;
-      ail = vl.z;
+      two_sum(byh, -w0h, arh, arl);
+      arl = __fadd_rn(arl, __fsub_rn(byl, w0l));
+      aih = a.zero_b ? 0.f : vh.z;
+      ail = a.zero_b ? 0.f : vl.z;
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         float xh;
@@ -211,28 +295,42 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
       for (int i = 0; i < N; ++i) {
         ff_add_prod(th_t[i], tl_t[i], reh[i], rel[i], arh, arl);
         ff_add_prod(th_t[i], tl_t[i], imh[i], iml[i], aih, ail);
+        ff_add(gdh[i], gdl[i], reh[i]);
+        gdl[i] = __fadd_rn(gdl[i], rel[i]);
       }
     }
-    double* R = a.sc.rt;
-    R[q] = (double)rrh + (double)rrl;
-    R[Q + q] = (double)t0h + (double)t0l;
-#pragma unroll
-    for (int i = 0; i < N; ++i) R[(int64_t)(i + 2) * Q + q] = (double)th_t[i] + (double)tl_t[i];
-  } else {
-    double tau[N], w[N], t[N];
-    const double w0 = X[q];
+    group_sum_ff(rrh, rrl, ln.ks);
+    group_sum_ff(t0h, t0l, ln.ks);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      tau[i] = exp10(th[i]);
-      w[i] = X[(int64_t)(i + 1) * Q + q];
+      group_sum_ff(th_t[i], tl_t[i], ln.ks);
+      group_sum_ff(gdh[i], gdl[i], ln.ks);
+    }
+    if (ln.act && ln.slice == 0) {
+      double* R = a.sc.rt;
+      R[q] = (double)rrh + (double)rrl;
+      R[Q + q] = (double)t0h + (double)t0l;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        R[(int64_t)(i + 2) * Q + q] = (double)th_t[i] + (double)tl_t[i];
+        a.sc.G[(int64_t)pk(i + 1, i + 1) * Q + q] = (double)gdh[i] + (double)gdl[i];
+      }
+    }
+  } else {
+    double tau[N], w[N], t[N];
+    const double w0 = ln.act ? X[q] : 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      tau[i] = ln.act ? exp10(th[i]) : 0.0;
+      w[i] = ln.act ? X[(int64_t)(i + 1) * Q + q] : 0.0;
       t[i] = 0.0;
     }
     double t0 = 0.0, rr = 0.0;
 #pragma unroll 1
-    for (int64_t k = u.k0; k < u.k1; ++k) {
+    for (int64_t k = kbeg; k < kend; k += step) {
       const double om = __ldg(&a.omega[k]);
-      double ar = __ldg(&a.eps_re[k]) - w0;
-      double ai = __ldg(&a.eps_im[k]);
+      double ar = (a.zero_b ? 0.0 : __ldg(&a.eps_re[k])) - w0;
+      double ai = a.zero_b ? 0.0 : __ldg(&a.eps_im[k]);
       double re[N], im[N];
 #pragma unroll
       for (int i = 0; i < N; ++i) {
@@ -248,11 +346,17 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
 #pragma unroll
       for (int i = 0; i < N; ++i) t[i] = fma(re[i], ar, fma(im[i], ai, t[i]));
     }
-    double* R = a.sc.rt;
-    R[q] = rr;
-    R[Q + q] = t0;
+    rr = group_sum(rr, ln.ks);
+    t0 = group_sum(t0, ln.ks);
 #pragma unroll
-    for (int i = 0; i < N; ++i) R[(int64_t)(i + 2) * Q + q] = t[i];
+    for (int i = 0; i < N; ++i) t[i] = group_sum(t[i], ln.ks);
+    if (ln.act && ln.slice == 0) {
+      double* R = a.sc.rt;
+      R[q] = rr;
+      R[Q + q] = t0;
+#pragma unroll
+      for (int i = 0; i < N; ++i) R[(int64_t)(i + 2) * Q + q] = t[i];
+    }
   }
 }
 
@@ -260,42 +364,54 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
 // With x1 (unflipped, sc.x), x_hat (flipped, sc.xh) and w = M^-1 S g_hat (sc.w):
 //   gt[i]        = a_i'^T r_hat,  r_hat = b - A x_hat
 //   gt[N + i]    = a_i^T a_i'
-//   gt[2N + i]   = a_i'^T r,      r = r_hat + A (x_hat - x1)
+//   gt[2N + i]   = a_i'^T r,      r = b - A x1
 //   gt[3N + i]   = a_i'^T (A w)
 // where a_i' = d a_i / d log10(tau_i).
 template <int N, bool MIXED>
 __device__ __forceinline__ void grad_unit(const EvalArgs& a, const Unit& u) {
-  const int q = u.q0 + (int)threadIdx.x;
-  if (q >= u.q1) return;
-  if (a.active && !a.active[q]) return;
-  if (a.sc.fail[q]) return;
+  const Lane ln = lane_of(a, u, true);
+  const int q = ln.act ? ln.q : u.q0;
   const double* th = a.theta + (int64_t)q * a.sc.nmax;
   const int64_t Q = a.sc.Q;
-  constexpr float LN10F = 2.302585092994046f;
+  const int64_t kbeg = u.k0 + ln.slice;
+  const int64_t kend = ln.act ? u.k1 : kbeg;
+  const int64_t step = ln.ks;
   constexpr double LN10 = 2.302585092994046;
+  auto ld = [&](const double* p) { return ln.act ? *p : 0.0; };
   if constexpr (MIXED) {
-    // Both residuals are float-float: r_hat = b - A x_hat and r = b - A x1 (in a
-    // flipped candidate r_hat is large and r small, so r is not formed as
-    // r_hat + A e). The projections are summed with TwoSum.
-    float th_[N], tl_[N], xhh[N], xhl[N], x1h[N], x1l[N], w[N];
-    float trh_h[N], trh_l[N], taa[N], tr_h[N], tr_l[N], taw_h[N], taw_l[N];
-    float x0h, x0l, x10h, x10l;
-    split_double(a.sc.xh[q], x0h, x0l);
-    split_double(a.sc.x[q], x10h, x10l);
-    const float w0 = __double2float_rn(a.sc.w[q]);
+    // Float-float throughout: r_hat = b - A x_hat, r = b - A x1 and A w are
+    // float-float residual sums (in a flipped candidate r_hat is large and r
+    // small, so r is not formed as r_hat + A e); the derivative columns are
+    // float-float, via im = x re:
+    //   d re / d theta = -2 ln10 im^2,   d im / d theta = ln10 im (re - x im);
+    // the projections are Dot2 / TwoSum sums (the residual of a good fit changes
+    // sign along the spectrum, so they cancel heavily).
+    constexpr float LN10H = 2.3025851249694824f;               // fl(ln 10)
+    constexpr float LN10L = -3.1975436e-08f;                    // ln 10 - fl(ln 10)
+    float th_[N], tl_[N], xhh[N], xhl[N], x1h[N], x1l[N], wh[N], wl[N];
+    float trh_h[N], trh_l[N], taa_h[N], taa_l[N], tr_h[N], tr_l[N], taw_h[N], taw_l[N];
+    float x0h, x0l, x10h, x10l, w0h, w0l;
+    split_double(ld(a.sc.xh + q), x0h, x0l);
+    split_double(ld(a.sc.x + q), x10h, x10l);
+    split_double(ld(a.sc.w + q), w0h, w0l);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      split_double(exp10(th[i]), th_[i], tl_[i]);
-      split_double(a.sc.xh[(int64_t)(i + 1) * Q + q], xhh[i], xhl[i]);
-      split_double(a.sc.x[(int64_t)(i + 1) * Q + q], x1h[i], x1l[i]);
-      w[i] = __double2float_rn(a.sc.w[(int64_t)(i + 1) * Q + q]);
-      trh_h[i] = trh_l[i] = taa[i] = tr_h[i] = tr_l[i] = taw_h[i] = taw_l[i] = 0.f;
+      split_double(ln.act ? exp10(th[i]) : 0.0, th_[i], tl_[i]);
+      split_double(ld(a.sc.xh + (int64_t)(i + 1) * Q + q), xhh[i], xhl[i]);
+      split_double(ld(a.sc.x + (int64_t)(i + 1) * Q + q), x1h[i], x1l[i]);
+      split_double(ld(a.sc.w + (int64_t)(i + 1) * Q + q), wh[i], wl[i]);
+      trh_h[i] = trh_l[i] = taa_h[i] = taa_l[i] = tr_h[i] = tr_l[i] = taw_h[i] = taw_l[i] = 0.f;
     }
+    const int64_t k0s = kbeg < u.k1 ? kbeg : u.k0;
+    float4 vhn = __ldg(&a.kf32[k0s]), vln = __ldg(&a.kff[k0s]);
 #pragma unroll 1
-    for (int64_t k = u.k0; k < u.k1; ++k) {
-      const float4 vh = __ldg(&a.kf32[k]);
-      const float4 vl = __ldg(&a.kff[k]);
-      float reh[N], imh[N], xv[N];
+    for (int64_t k = kbeg; k < kend; k += step) {
+      const float4 vh = vhn, vl = vln;
+      if (k + step < kend) {
+        vhn = __ldg(&a.kf32[k + step]);
+        vln = __ldg(&a.kff[k + step]);
+      }
+      float reh[N], rel[N], imh[N], iml[N], xv[N];
       float hrh, hrl, hih, hil, rrh, rrl, rih, ril;
       two_sum(vh.y, -x0h, hrh, hrl);
       hrl = __fadd_rn(hrl, __fsub_rn(vl.y, x0l));
@@ -305,56 +421,79 @@ __device__ __forceinline__ void grad_unit(const EvalArgs& a, const Unit& u) {
       rrl = __fadd_rn(rrl, __fsub_rn(vl.y, x10l));
       rih = vh.z;
       ril = vl.z;
-      float awr = w0, awi = 0.f;
+      float awrh = -w0h, awrl = -w0l, awih = 0.f, awil = 0.f;   // -(A w), accumulated as a residual
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        float rel, iml;
-        basis_ff(vh.x, vl.x, th_[i], tl_[i], reh[i], rel, imh[i], iml, xv[i]);
-        ff_sub_prod(hrh, hrl, xhh[i], xhl[i], reh[i], rel);
-        ff_sub_prod(hih, hil, xhh[i], xhl[i], imh[i], iml);
-        ff_sub_prod(rrh, rrl, x1h[i], x1l[i], reh[i], rel);
-        ff_sub_prod(rih, ril, x1h[i], x1l[i], imh[i], iml);
-        awr = fmaf(w[i], reh[i], awr);
-        awi = fmaf(w[i], imh[i], awi);
+        basis_ff(vh.x, vl.x, th_[i], tl_[i], reh[i], rel[i], imh[i], iml[i], xv[i]);
+        ff_sub_prod(hrh, hrl, xhh[i], xhl[i], reh[i], rel[i]);
+        ff_sub_prod(hih, hil, xhh[i], xhl[i], imh[i], iml[i]);
+        ff_sub_prod(rrh, rrl, x1h[i], x1l[i], reh[i], rel[i]);
+        ff_sub_prod(rih, ril, x1h[i], x1l[i], imh[i], iml[i]);
+        ff_sub_prod(awrh, awrl, wh[i], wl[i], reh[i], rel[i]);
+        ff_sub_prod(awih, awil, wh[i], wl[i], imh[i], iml[i]);
       }
-      const float rhr = __fadd_rn(hrh, hrl), rhi = __fadd_rn(hih, hil);
-      const float rr = __fadd_rn(rrh, rrl), ri = __fadd_rn(rih, ril);
+      ff_norm(hrh, hrl);
+      ff_norm(hih, hil);
+      ff_norm(rrh, rrl);
+      ff_norm(rih, ril);
+      ff_norm(awrh, awrl);
+      ff_norm(awih, awil);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        const float x = xv[i], re = reh[i];
-        const float re2l = re * re * LN10F;
-        const float dre = -2.0f * x * x * re2l;
-        const float dim = x * (1.0f - x * x) * re2l;
-        ff_add(trh_h[i], trh_l[i], __fmaf_rn(dim, rhi, __fmul_rn(dre, rhr)));
-        taa[i] = fmaf(re, dre, fmaf(imh[i], dim, taa[i]));
-        ff_add(tr_h[i], tr_l[i], __fmaf_rn(dim, ri, __fmul_rn(dre, rr)));
-        ff_add(taw_h[i], taw_l[i], __fmaf_rn(dim, awi, __fmul_rn(dre, awr)));
+        // x = w tau again in float-float (basis_ff returned only its leading part)
+        float xh_ = __fmul_rn(vh.x, th_[i]);
+        float xl_ = __fmaf_rn(vh.x, th_[i], -xh_);
+        xl_ = __fmaf_rn(vh.x, tl_[i], __fmaf_rn(vl.x, th_[i], xl_));
+        float sh, sl, ph, pl, dmh, dml, drh, drl, dih, dil;
+        ff_mul(imh[i], iml[i], imh[i], iml[i], sh, sl);             // im^2
+        ff_mul(sh, sl, -2.0f * LN10H, -2.0f * LN10L, drh, drl);     // d re / d theta
+        ff_mul(xh_, xl_, imh[i], iml[i], ph, pl);                   // x im
+        two_sum(reh[i], -ph, dmh, dml);                             // re - x im
+        dml = __fadd_rn(dml, __fsub_rn(rel[i], pl));
+        ff_mul(imh[i], iml[i], dmh, dml, ph, pl);
+        ff_mul(ph, pl, LN10H, LN10L, dih, dil);                     // d im / d theta
+        ff_add_prod(trh_h[i], trh_l[i], drh, drl, hrh, hrl);
+        ff_add_prod(trh_h[i], trh_l[i], dih, dil, hih, hil);
+        ff_add(taa_h[i], taa_l[i], __fmaf_rn(imh[i], dih, __fmul_rn(reh[i], drh)));
+        ff_add_prod(tr_h[i], tr_l[i], drh, drl, rrh, rrl);
+        ff_add_prod(tr_h[i], tr_l[i], dih, dil, rih, ril);
+        ff_add_prod(taw_h[i], taw_l[i], drh, drl, awrh, awrl);      // accumulates -a'^T (A w)
+        ff_add_prod(taw_h[i], taw_l[i], dih, dil, awih, awil);
       }
     }
-    double* T = a.sc.gt;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      T[(int64_t)i * Q + q] = (double)trh_h[i] + (double)trh_l[i];
-      T[(int64_t)(N + i) * Q + q] = taa[i];
-      T[(int64_t)(2 * N + i) * Q + q] = (double)tr_h[i] + (double)tr_l[i];
-      T[(int64_t)(3 * N + i) * Q + q] = (double)taw_h[i] + (double)taw_l[i];
+      group_sum_ff(trh_h[i], trh_l[i], ln.ks);
+      group_sum_ff(taa_h[i], taa_l[i], ln.ks);
+      group_sum_ff(tr_h[i], tr_l[i], ln.ks);
+      group_sum_ff(taw_h[i], taw_l[i], ln.ks);
+    }
+    if (ln.act && ln.slice == 0) {
+      double* T = a.sc.gt;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        T[(int64_t)i * Q + q] = (double)trh_h[i] + (double)trh_l[i];
+        T[(int64_t)(N + i) * Q + q] = (double)taa_h[i] + (double)taa_l[i];
+        T[(int64_t)(2 * N + i) * Q + q] = (double)tr_h[i] + (double)tr_l[i];
+        T[(int64_t)(3 * N + i) * Q + q] = -((double)taw_h[i] + (double)taw_l[i]);
+      }
     }
   } else {
     double tau[N], xh[N], e[N], w[N];
     double t_rh[N], t_aa[N], t_r[N], t_aw[N];
-    const double x0 = a.sc.xh[q];
-    const double e0 = a.sc.xh[q] - a.sc.x[q];
-    const double w0 = a.sc.w[q];
+    const double x0 = ld(a.sc.xh + q);
+    const double e0 = x0 - ld(a.sc.x + q);
+    const double w0 = ld(a.sc.w + q);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      tau[i] = exp10(th[i]);
-      xh[i] = a.sc.xh[(int64_t)(i + 1) * Q + q];
-      e[i] = xh[i] - a.sc.x[(int64_t)(i + 1) * Q + q];
-      w[i] = a.sc.w[(int64_t)(i + 1) * Q + q];
+      tau[i] = ln.act ? exp10(th[i]) : 0.0;
+      xh[i] = ld(a.sc.xh + (int64_t)(i + 1) * Q + q);
+      e[i] = xh[i] - ld(a.sc.x + (int64_t)(i + 1) * Q + q);
+      w[i] = ld(a.sc.w + (int64_t)(i + 1) * Q + q);
       t_rh[i] = t_aa[i] = t_r[i] = t_aw[i] = 0.0;
     }
 #pragma unroll 1
-    for (int64_t k = u.k0; k < u.k1; ++k) {
+    for (int64_t k = kbeg; k < kend; k += step) {
       const double om = __ldg(&a.omega[k]);
       double rhr = __ldg(&a.eps_re[k]) - x0, rhi = __ldg(&a.eps_im[k]);
       double aer = e0, aei = 0.0, awr = w0, awi = 0.0;
@@ -386,13 +525,22 @@ __device__ __forceinline__ void grad_unit(const EvalArgs& a, const Unit& u) {
         t_aw[i] = fma(dre, awr, fma(dim, awi, t_aw[i]));
       }
     }
-    double* T = a.sc.gt;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      T[(int64_t)i * Q + q] = t_rh[i];
-      T[(int64_t)(N + i) * Q + q] = t_aa[i];
-      T[(int64_t)(2 * N + i) * Q + q] = t_r[i];
-      T[(int64_t)(3 * N + i) * Q + q] = t_aw[i];
+      t_rh[i] = group_sum(t_rh[i], ln.ks);
+      t_aa[i] = group_sum(t_aa[i], ln.ks);
+      t_r[i] = group_sum(t_r[i], ln.ks);
+      t_aw[i] = group_sum(t_aw[i], ln.ks);
+    }
+    if (ln.act && ln.slice == 0) {
+      double* T = a.sc.gt;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        T[(int64_t)i * Q + q] = t_rh[i];
+        T[(int64_t)(N + i) * Q + q] = t_aa[i];
+        T[(int64_t)(2 * N + i) * Q + q] = t_r[i];
+        T[(int64_t)(3 * N + i) * Q + q] = t_aw[i];
+      }
     }
   }
 }
@@ -414,9 +562,13 @@ __device__ __forceinline__ void dispatch_n(const EvalArgs& a, const Unit& u) {
 }
 
 // One block per unit (grid-stride over the unit list); LO..HI is the pole
-// bucket compiled into this kernel.
-template <int PH, int LO, int HI, bool MIXED>
-__global__ void __launch_bounds__(256) k_pass(EvalArgs a) {
+// bucket compiled into this kernel. At most MAX_BLOCK_THREADS threads per block;
+// MINB resident blocks of that size bound the registers per thread (MINB = 3:
+// 168 registers, 12 warps per SM with 64-thread blocks).
+constexpr int MAX_BLOCK_THREADS = 128;
+
+template <int PH, int LO, int HI, bool MIXED, int MINB>
+__global__ void __launch_bounds__(MAX_BLOCK_THREADS, MINB) k_pass(EvalArgs a) {
   for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
     const Unit u = a.units[ui];
     if (u.N < LO || u.N > HI) {

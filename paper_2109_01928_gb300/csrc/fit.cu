@@ -82,7 +82,8 @@ static int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search*
   const int64_t Q = pl.S * (int64_t)P;
   if (Q > ((int64_t)1 << 31) - 1) return h->fail(DEBYE_EINVAL, "S*P exceeds 2^31-1");
   if ((rc = h->prep_spectra(sp, pl, st))) return rc;
-  const int cb = h->block_size(pl);
+  int cb, ks;
+  choose_layout(P, h->opt.cands_per_block, &cb, &ks);
   const bool mixed = h->opt.precision == DEBYE_PREC_MIXED;
   const int nmax = n_max;
 
@@ -140,6 +141,7 @@ static int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search*
   ea.eps_im = sp->eps_im;
   ea.h0 = (const double*)h->ws_h0.p;
   ea.lam = h->opt.lam_search;
+  ea.ks = ks;
   ea.status = h->d_status;
   const int steps = h->opt.refine_steps;
 
@@ -194,28 +196,51 @@ static int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search*
     pa.tth = (double*)p;
     if ((rc = h->named("pol.tcost", sizeof(double) * QT, &p))) return rc;
     pa.tcost = (double*)p;
-    if ((rc = h->named("pol.tgrad", sizeof(double) * QT * nmax, &p))) return rc;
-    pa.tgrad = (double*)p;
     if ((rc = h->named("pol.active", QT, &p))) return rc;
     pa.active = (uint8_t*)p;
+    if ((rc = h->named("pol.ath", ln, &p))) return rc;
+    pa.ath = (double*)p;
+    if ((rc = h->named("pol.acost", sizeof(double) * L, &p))) return rc;
+    pa.acost = (double*)p;
+    if ((rc = h->named("pol.agrad", ln, &p))) return rc;
+    pa.agrad = (double*)p;
+    if ((rc = h->named("pol.aactive", L, &p))) return rc;
+    pa.aactive = (uint8_t*)p;
 
-    std::vector<int32_t> pb(pl.S), pe(pl.S);
+    // trial steps: candidate l * R + t; accepted points: candidate l
+    std::vector<int32_t> pb(pl.S), pe(pl.S), ab(pl.S), ae(pl.S);
     for (int64_t s = 0; s < pl.S; ++s) {
       pb[s] = (int32_t)(s * T * pa.R);
       pe[s] = (int32_t)((s + 1) * T * pa.R);
+      ab[s] = (int32_t)(s * T);
+      ae[s] = (int32_t)((s + 1) * T);
     }
-    UnitGroups gp;
-    build_units(pl, pb, pe, cb, gp);
+    int cbp, ksp, cba, ksa;
+    choose_layout((int64_t)T * pa.R, h->opt.cands_per_block, &cbp, &ksp);
+    choose_layout(T, h->opt.cands_per_block, &cba, &ksa);
+    UnitGroups gp, ga;
+    build_units(pl, pb, pe, cbp, gp);
+    build_units(pl, ab, ae, cba, ga);
     if ((rc = h->upload_units(gp, h->named_bufs["pol.units"], st))) return rc;
+    if ((rc = h->upload_units(ga, h->named_bufs["pol.aunits"], st))) return rc;
     EvalArgs ep = ea;
     if ((rc = h->ensure_scratch(QT, nmax, h->sb_polish, ep.sc))) return rc;
     ep.units = (const Unit*)h->named_bufs["pol.units"].p;
     ep.theta = pa.tth;
     ep.active = pa.active;
+    ep.ks = ksp;
+    EvalArgs eg = ea;
+    if ((rc = h->ensure_scratch(L, nmax, h->sb_polish_acc, eg.sc))) return rc;
+    eg.units = (const Unit*)h->named_bufs["pol.aunits"].p;
+    eg.theta = pa.ath;
+    eg.active = pa.aactive;
+    eg.ks = ksa;
 
     launch_topk(sa, pa, h->sms, st); ++h->launches;
     launch_polish_start(pa, h->sms, st); ++h->launches;
-    if ((rc = h->run_eval(ep, gp, mixed, h->eval_steps(true), pa.tcost, nullptr, pa.tgrad, h->sb_polish.g1, cb, st))) return rc;
+    if ((rc = h->run_eval(eg, ga, mixed, h->eval_steps(true), pa.acost, nullptr, pa.agrad, h->sb_polish_acc.g1,
+                          cba, st)))
+      return rc;
     launch_polish_take0(pa, h->sms, st); ++h->launches;
     if (se->evals) {  // the start evaluation of every line
       double add = 0.0;
@@ -227,10 +252,17 @@ static int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search*
     rc = repeat(h, se->polish_iters, st, [&]() -> int {
       launch_polish_dir(pa, sp->n_poles, sp->lo, sp->hi, h->sms, st); ++h->launches;
       for (int r = 0; r < rounds; ++r) {
-        int e = h->run_eval(ep, gp, mixed, h->eval_steps(true), pa.tcost, nullptr, pa.tgrad, h->sb_polish.g1, cb, st);
+        // Armijo needs only costs: the trial steps are evaluated without gradients
+        int e = h->run_eval(ep, gp, mixed, h->eval_steps(false), pa.tcost, nullptr, nullptr, h->sb_polish.g1,
+                            cbp, st);
         if (e) return e;
         launch_polish_accept(pa, sp->n_poles, sp->lo, sp->hi, sp->offsets, h->sms, st); ++h->launches;
       }
+      // cost and gradient at the accepted points, then the L-BFGS update
+      int e = h->run_eval(eg, ga, mixed, h->eval_steps(true), pa.acost, nullptr, pa.agrad, h->sb_polish_acc.g1,
+                          cba, st);
+      if (e) return e;
+      launch_polish_take(pa, sp->n_poles, sp->offsets, h->sms, st); ++h->launches;
       return h->check_launch("polish iteration");
     });
     if (rc) return rc;
@@ -250,16 +282,19 @@ static int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search*
     fb[s] = (int32_t)s;
     fe[s] = (int32_t)(s + 1);
   }
+  int cbf, ksf;
+  choose_layout(1, 0, &cbf, &ksf);
   UnitGroups gf;
-  build_units(pl, fb, fe, 32, gf);
+  build_units(pl, fb, fe, cbf, gf);
   if ((rc = h->upload_units(gf, h->named_bufs["fin.units"], st))) return rc;
   EvalArgs ef = ea;
   if ((rc = h->ensure_scratch(S, nmax, h->sb_final, ef.sc))) return rc;
   ef.units = (const Unit*)h->named_bufs["fin.units"].p;
   ef.theta = th_best;
   ef.active = nullptr;
+  ef.ks = ksf;
   ef.lam = h->opt.lam_final;
-  if ((rc = h->run_eval(ef, gf, false, 2, c_best, w_best, nullptr, h->sb_final.g1, 32, st))) return rc;
+  if ((rc = h->run_eval(ef, gf, false, 2, c_best, w_best, nullptr, h->sb_final.g1, cbf, st))) return rc;
   launch_assemble(S, nmax, sp->n_poles, th_best, w_best, c_best, eps_inf, d_eps, tau, final_cost, h->sms, st);
   ++h->launches;
   return h->check_launch("assemble");

@@ -54,7 +54,7 @@ struct debye_ctx {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 
   debyefit::Buf ws_kf32, ws_kff, ws_h0, ws_units;
-  debyefit::ScratchBufs sb_eval, sb_polish, sb_final;
+  debyefit::ScratchBufs sb_eval, sb_polish, sb_polish_acc, sb_final;
   std::map<std::string, debyefit::Buf> named_bufs;  // swarm / polish / result state
 
   // kernel timing (debye_profile_*)
@@ -84,7 +84,6 @@ struct debye_ctx {
   int ensure_scratch(int64_t Q, int nmax, debyefit::ScratchBufs& sb, debyefit::Scratch& sc);
   int run_eval(debyefit::EvalArgs a, const debyefit::UnitGroups& g, bool mixed, int steps,
                double* cost, double* weights, double* grad, double* g1, int cb, cudaStream_t st);
-  int block_size(const debyefit::Plan& pl) const;
   int eval_steps(bool with_grad) const;
   int named(const char* name, size_t bytes, void** out);
 
@@ -98,7 +97,7 @@ struct debye_ctx {
     free_buf(ws_kff);
     free_buf(ws_h0);
     free_buf(ws_units);
-    for (debyefit::ScratchBufs* sb : {&sb_eval, &sb_polish, &sb_final}) {
+    for (debyefit::ScratchBufs* sb : {&sb_eval, &sb_polish, &sb_polish_acc, &sb_final}) {
       free_buf(sb->G);
       free_buf(sb->L);
       free_buf(sb->vec);

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(256) k_finish(EvalArgs a, int final_step, doub
 // ------------------------------------------------------------------ gradient
 // w = M^-1 S g_hat with g_hat = g1 - M (x_hat - x1) = h - M x_hat,
 // S = diag(1, sign x1_1, ..., sign x1_N).
-__global__ void __launch_bounds__(256) k_grad_prep(EvalArgs a, const double* g1) {
+__global__ void __launch_bounds__(256) k_grad_prep(EvalArgs a, const double* g1, double* sg_out) {
   const int64_t Q = a.sc.Q;
   for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
     const Unit u = a.units[ui];
@@ -206,10 +206,39 @@ __global__ void __launch_bounds__(256) k_grad_prep(EvalArgs a, const double* g1)
       const double x1 = a.sc.x[(int64_t)i * Q + q];
       double gh = g1[(int64_t)i * Q + q] - d[i] * t1[i];
       if (i > 0 && x1 < 0.0) gh = -gh;
+      if (sg_out) sg_out[(int64_t)i * Q + q] = gh;   // S g_hat, kept for the refinement of w
       t2[i] = gh / d[i];
     }
     llt_solve(L, t2, n);
     for (int i = 0; i < n; ++i) a.sc.w[(int64_t)i * Q + q] = t2[i] / d[i];
+  }
+}
+
+// One refinement step of the adjoint solve M w = S g_hat: with the residual pass
+// run on x := w against b = 0 (rt = -A^T A w in float-float),
+//   rho = S g_hat - (A^T A + lam diag G) w,  w <- w + M^-1 rho.
+// In a flipped candidate w is not small and enters the gradient to first order,
+// so the FP32 Gram's error in M^-1 must not reach it.
+__global__ void __launch_bounds__(256) k_adjoint_refine(EvalArgs a, const double* sg) {
+  const int64_t Q = a.sc.Q;
+  for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
+    const Unit u = a.units[ui];
+    const int q = u.q0 + (int)threadIdx.x;
+    if (q >= u.q1 || (a.active && !a.active[q])) continue;
+    if (a.sc.fail[q]) continue;
+    const int n = u.N + 1;
+    double L[NPACK_MAX], d[NMAX1], v[NMAX1], w[NMAX1];
+    const int npk = n * (n + 1) / 2;
+    for (int k = 0; k < npk; ++k) L[k] = a.sc.L[(int64_t)k * Q + q];
+    for (int i = 0; i < n; ++i) {
+      d[i] = 1.0 / a.sc.dinv[(int64_t)i * Q + q];
+      w[i] = a.sc.w[(int64_t)i * Q + q];
+      const double gii = a.sc.G[(int64_t)pk(i, i) * Q + q];
+      const double rho = sg[(int64_t)i * Q + q] + a.sc.rt[(int64_t)(i + 1) * Q + q] - a.lam * gii * w[i];
+      v[i] = rho / d[i];
+    }
+    llt_solve(L, v, n);
+    for (int i = 0; i < n; ++i) a.sc.w[(int64_t)i * Q + q] = w[i] + v[i] / d[i];
   }
 }
 
@@ -268,8 +297,11 @@ void launch_finish(const EvalArgs& a, int final_step, double* cost, double* weig
                    int block, int sms, cudaStream_t st) {
   if (a.n_units) k_finish<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, final_step, cost, weights, g1);
 }
-void launch_grad_prep(const EvalArgs& a, const double* g1, int block, int sms, cudaStream_t st) {
-  if (a.n_units) k_grad_prep<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, g1);
+void launch_grad_prep(const EvalArgs& a, const double* g1, double* sg_out, int block, int sms, cudaStream_t st) {
+  if (a.n_units) k_grad_prep<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, g1, sg_out);
+}
+void launch_adjoint_refine(const EvalArgs& a, const double* sg, int block, int sms, cudaStream_t st) {
+  if (a.n_units) k_adjoint_refine<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, sg);
 }
 void launch_grad_finish(const EvalArgs& a, double* grad, int block, int sms, cudaStream_t st) {
   if (a.n_units) k_grad_finish<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, grad);

@@ -7,23 +7,26 @@ namespace debyefit {
 
 void launch_pass_b2(int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st) {
   constexpr int LO = 9, HI = 12;
+  // mixed-precision passes up to 12 poles fit in 168 registers without spills:
+  // cap them for 3 resident 128-thread blocks; larger N keeps the full register file
+  constexpr int MB_MIXED = HI <= 12 ? 3 : 1;
   if (mixed) {
     if (phase == PH_GRAM) {
       const size_t smem = sizeof(float) * gram_smem_stride(HI) * block;
       static bool attr_set = false;
       if (!attr_set) {
-        cudaFuncSetAttribute(k_pass<PH_GRAM, LO, HI, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_pass<PH_GRAM, LO, HI, true, MB_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(float) * gram_smem_stride(HI) * MAX_BLOCK));
         attr_set = true;
       }
-      k_pass<PH_GRAM, LO, HI, true><<<grid, block, smem, st>>>(a);
+      k_pass<PH_GRAM, LO, HI, true, MB_MIXED><<<grid, block, smem, st>>>(a);
     }
-    else if (phase == PH_REFINE) k_pass<PH_REFINE, LO, HI, true><<<grid, block, 0, st>>>(a);
-    else k_pass<PH_GRAD, LO, HI, true><<<grid, block, 0, st>>>(a);
+    else if (phase == PH_REFINE) k_pass<PH_REFINE, LO, HI, true, MB_MIXED><<<grid, block, 0, st>>>(a);
+    else k_pass<PH_GRAD, LO, HI, true, 1><<<grid, block, 0, st>>>(a);
   } else {
-    if (phase == PH_GRAM) k_pass<PH_GRAM, LO, HI, false><<<grid, block, 0, st>>>(a);
-    else if (phase == PH_REFINE) k_pass<PH_REFINE, LO, HI, false><<<grid, block, 0, st>>>(a);
-    else k_pass<PH_GRAD, LO, HI, false><<<grid, block, 0, st>>>(a);
+    if (phase == PH_GRAM) k_pass<PH_GRAM, LO, HI, false, 1><<<grid, block, 0, st>>>(a);
+    else if (phase == PH_REFINE) k_pass<PH_REFINE, LO, HI, false, 1><<<grid, block, 0, st>>>(a);
+    else k_pass<PH_GRAD, LO, HI, false, 1><<<grid, block, 0, st>>>(a);
   }
 }
 

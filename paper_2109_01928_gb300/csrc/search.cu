@@ -154,27 +154,24 @@ __global__ void k_topk(SwarmArgs a, PolishArgs pa) {
   }
 }
 
-// Trial t of line l is candidate q = l * R + t of the polish evaluation.
+// The start point of each line is evaluated, with its gradient, in the
+// accepted-point slot (candidate l of the gradient evaluation).
 __global__ void k_polish_start(PolishArgs pa) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < pa.L;
        l += (int64_t)gridDim.x * blockDim.x) {
-    const int nmax = pa.nmax;
-    for (int t = 0; t < pa.R; ++t) {
-      const int64_t q = l * pa.R + t;
-      pa.active[q] = (t == 0) ? 1 : 0;
-      for (int d = 0; d < nmax; ++d) pa.tth[q * nmax + d] = pa.th[l * nmax + d];
-    }
+    for (int d = 0; d < pa.nmax; ++d) pa.ath[l * pa.nmax + d] = pa.th[l * pa.nmax + d];
+    pa.aactive[l] = 1;
+    for (int t = 0; t < pa.R; ++t) pa.active[l * pa.R + t] = 0;
   }
 }
 
-// After the start evaluation: f, g of each line from trial slot 0.
+// After the start evaluation: f, g of each line.
 __global__ void k_polish_take0(PolishArgs pa) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < pa.L;
        l += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t q = l * pa.R;
-    pa.f[l] = pa.tcost[q];
-    for (int d = 0; d < pa.nmax; ++d) pa.g[l * pa.nmax + d] = pa.tgrad[q * pa.nmax + d];
-    pa.active[q] = 0;
+    pa.f[l] = pa.acost[l];
+    for (int d = 0; d < pa.nmax; ++d) pa.g[l * pa.nmax + d] = pa.agrad[l * pa.nmax + d];
+    pa.aactive[l] = 0;
     if (!isfinite(pa.f[l])) pa.done[l] = 1;
   }
 }
@@ -271,7 +268,7 @@ __global__ void k_polish_accept(PolishArgs pa, const int32_t* n_poles, const dou
     if (pa.done[l] || pa.acc[l]) continue;
     const int64_t s = l / pa.T;
     const int N = n_poles[s];
-    const int nmax = pa.nmax, m = pa.m;
+    const int nmax = pa.nmax;
     int n_active = 0;
     int hit = -1;
     for (int t = 0; t < pa.R; ++t) {
@@ -288,39 +285,56 @@ __global__ void k_polish_accept(PolishArgs pa, const int32_t* n_poles, const dou
     for (int t = 0; t < pa.R; ++t) pa.active[l * pa.R + t] = 0;
     if (hit >= 0) {
       const int64_t q = l * pa.R + hit;
-      double sv[NMAX], yv[NMAX];
-      for (int d = 0; d < N; ++d) {
-        sv[d] = pa.tth[q * nmax + d] - pa.th[l * nmax + d];
-        yv[d] = pa.tgrad[q * nmax + d] - pa.g[l * nmax + d];
-      }
-      const double sy = dotn(sv, yv, N), yy = dotn(yv, yv, N);
-      if (sy > 2.220446049250313e-16 * yy) {
-        int hc = pa.hcount[l];
-        if (hc == m) {  // drop the oldest pair
-          for (int k = 1; k < m; ++k)
-            for (int d = 0; d < N; ++d) {
-              pa.hs[(l * m + k - 1) * nmax + d] = pa.hs[(l * m + k) * nmax + d];
-              pa.hy[(l * m + k - 1) * nmax + d] = pa.hy[(l * m + k) * nmax + d];
-            }
-          hc = m - 1;
-        }
-        for (int d = 0; d < N; ++d) {
-          pa.hs[(l * m + hc) * nmax + d] = sv[d];
-          pa.hy[(l * m + hc) * nmax + d] = yv[d];
-        }
-        pa.hcount[l] = hc + 1;
-      }
-      for (int d = 0; d < N; ++d) {
-        pa.th[l * nmax + d] = pa.tth[q * nmax + d];
-        pa.g[l * nmax + d] = pa.tgrad[q * nmax + d];
-      }
-      pa.f[l] = pa.tcost[q];
+      for (int d = 0; d < nmax; ++d) pa.ath[l * nmax + d] = pa.tth[q * nmax + d];
+      pa.aactive[l] = 1;
       pa.acc[l] = 1;
     } else if (n_active) {
       pa.t0[l] += pa.R;
       if (pa.t0[l] >= pa.max_trials) pa.done[l] = 1;
       else write_trials(pa, l, N, lo_[s], hi_[s]);
     }
+  }
+}
+
+// L-BFGS update with the accepted point's cost and gradient: history pair
+// (s, y) kept only when s^T y > eps y^T y (oldest pair dropped when full).
+__global__ void k_polish_take(PolishArgs pa, const int32_t* n_poles, const int64_t* offsets) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < pa.L;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    if (!pa.aactive[l]) continue;
+    pa.aactive[l] = 0;
+    const int64_t s = l / pa.T;
+    const int N = n_poles[s];
+    const int nmax = pa.nmax, m = pa.m;
+    if (pa.evals) atomicAdd(pa.evals, (double)(offsets[s + 1] - offsets[s]));
+    double sv[NMAX], yv[NMAX];
+    for (int d = 0; d < N; ++d) {
+      sv[d] = pa.ath[l * nmax + d] - pa.th[l * nmax + d];
+      yv[d] = pa.agrad[l * nmax + d] - pa.g[l * nmax + d];
+    }
+    const double sy = dotn(sv, yv, N), yy = dotn(yv, yv, N);
+    if (sy > 2.220446049250313e-16 * yy) {
+      int hc = pa.hcount[l];
+      if (hc == m) {
+        for (int k = 1; k < m; ++k)
+          for (int d = 0; d < N; ++d) {
+            pa.hs[(l * m + k - 1) * nmax + d] = pa.hs[(l * m + k) * nmax + d];
+            pa.hy[(l * m + k - 1) * nmax + d] = pa.hy[(l * m + k) * nmax + d];
+          }
+        hc = m - 1;
+      }
+      for (int d = 0; d < N; ++d) {
+        pa.hs[(l * m + hc) * nmax + d] = sv[d];
+        pa.hy[(l * m + hc) * nmax + d] = yv[d];
+      }
+      pa.hcount[l] = hc + 1;
+    }
+    for (int d = 0; d < N; ++d) {
+      pa.th[l * nmax + d] = pa.ath[l * nmax + d];
+      pa.g[l * nmax + d] = pa.agrad[l * nmax + d];
+    }
+    pa.f[l] = pa.acost[l];
+    if (!isfinite(pa.f[l])) pa.done[l] = 1;
   }
 }
 
@@ -407,6 +421,10 @@ void launch_polish_dir(const PolishArgs& pa, const int32_t* n_poles, const doubl
 void launch_polish_accept(const PolishArgs& pa, const int32_t* n_poles, const double* lo, const double* hi,
                           const int64_t* offsets, int sms, cudaStream_t st) {
   k_polish_accept<<<g1d(pa.L, sms), 128, 0, st>>>(pa, n_poles, lo, hi, offsets);
+}
+void launch_polish_take(const PolishArgs& pa, const int32_t* n_poles, const int64_t* offsets, int sms,
+                        cudaStream_t st) {
+  k_polish_take<<<g1d(pa.L, sms), 128, 0, st>>>(pa, n_poles, offsets);
 }
 void launch_pick_best(const SwarmArgs& a, const PolishArgs& pa, double* out_theta, int sms, cudaStream_t st) {
   k_pick_best<<<g1d(a.S, sms), 256, 0, st>>>(a, pa, out_theta);

@@ -41,8 +41,12 @@ struct PolishArgs {
   int32_t* acc;    // [L] step accepted in this iteration
   double* tth;     // [L*R][nmax] trial points
   double* tcost;   // [L*R]
-  double* tgrad;   // [L*R][nmax]
   uint8_t* active; // [L*R] trial needs evaluation
+  // the accepted point of each line, evaluated with its gradient
+  double* ath;     // [L][nmax] accepted point
+  double* acost;   // [L]
+  double* agrad;   // [L][nmax]
+  uint8_t* aactive;// [L] line has an accepted point to take
   double* evals;   // [1] or nullptr
 };
 
@@ -58,6 +62,8 @@ void launch_polish_dir(const PolishArgs& pa, const int32_t* n_poles, const doubl
                        int sms, cudaStream_t st);
 void launch_polish_accept(const PolishArgs& pa, const int32_t* n_poles, const double* lo, const double* hi,
                           const int64_t* offsets, int sms, cudaStream_t st);
+void launch_polish_take(const PolishArgs& pa, const int32_t* n_poles, const int64_t* offsets, int sms,
+                        cudaStream_t st);
 void launch_pick_best(const SwarmArgs& a, const PolishArgs& pa, double* out_theta, int sms, cudaStream_t st);
 void launch_assemble(int64_t S, int nmax, const int32_t* n_poles, const double* theta, const double* weights,
                      const double* cost, double* eps_inf, double* d_eps, double* tau, double* final_cost,
