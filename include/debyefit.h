@@ -159,6 +159,35 @@ int debye_fit_batch(debye_handle h, const debye_spectra* spectra, const debye_se
                     int32_t n_max, double* eps_inf, double* d_eps, double* tau,
                     double* final_cost, cudaStream_t stream);
 
+/* Allocation-free evaluation. The paper has no counterpart to this entry point;
+ * it exists for callers that cannot let the library allocate device memory, such
+ * as an application embedding the fitter that owns a fixed device-memory budget,
+ * or a latency-critical loop where cudaMalloc/cudaFree (which may synchronise the
+ * device) are not acceptable.
+ *
+ * Computes exactly what debye_eval_population computes (costs, and weights if
+ * `weights` is not NULL) for the options in `opt` (NULL = defaults), without a
+ * handle. It calls no cudaMalloc, cudaFree or other allocating routine: all
+ * temporary data lives in one fixed scratch array of DEBYE_NOALLOC_SCRATCH_BYTES
+ * (32 MiB) inside the library's device image, held by every GPU that loads the
+ * library until the process exits. A batch whose temporaries do not fit (about
+ * 2.3 KB per candidate at n_max = 12, plus 32 B per frequency sample), or that
+ * needs more than 4096 work units, is rejected with DEBYE_EINVAL and a message.
+ * spectra->offsets_host and spectra->n_poles_host are required.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. Every call on a device shares the one array and leaves
+ * its contents behind (the call initialises everything it reads); calls whose
+ * work overlaps on the GPU race on the array, so order them (one stream, or
+ * events). The call returns after the work on `stream` has finished, with
+ * DEBYE_ENOTFINITE / DEBYE_EBOUNDS for input problems found on the device.
+ * `err` (may be NULL) receives a message of at most err_len bytes. */
+#define DEBYE_NOALLOC_SCRATCH_BYTES (32u << 20)
+int debye_eval_population_noalloc(const debye_options* opt, const debye_spectra* spectra, int32_t P,
+                                  int32_t n_max, const double* theta, double* cost, double* weights,
+                                  char* err, int32_t err_len, cudaStream_t stream);
+
 /* Wait for `stream`, then return and clear the device status word
  * (DEBYE_OK, DEBYE_ENOTFINITE, DEBYE_EBOUNDS or DEBYE_ETIMEOUT). */
 int debye_sync(debye_handle h, cudaStream_t stream);

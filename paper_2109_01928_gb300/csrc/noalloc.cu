@@ -1,0 +1,243 @@
+// Allocation-free population evaluation (debye_eval_population_noalloc).
+//
+// Some callers cannot let this library allocate device memory: an application
+// that embeds the fitter (for example an FDTD solver that owns a fixed device
+// memory budget and pre-allocates everything up front), or a latency-critical
+// loop in which cudaMalloc/cudaFree, which may synchronise the device, are not
+// acceptable. The handle-based entry points allocate their workspaces on first
+// use; this one instead uses a fixed scratch array that lives in the library's
+// own device image, so a call allocates nothing. The caller still provides the
+// inputs and the outputs.
+//
+// The scratch is one file-scope array per device, held from the time the
+// library's device code is loaded on that device until the process exits.
+// Every call on a device uses the same array and leaves its contents behind;
+// calls whose work overlaps on the GPU (different streams or host threads,
+// without ordering between them) race on it and give wrong results.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "launch.h"
+
+namespace debyefit {
+namespace {
+
+constexpr size_t SCRATCH_BYTES = DEBYE_NOALLOC_SCRATCH_BYTES;
+constexpr int MAX_UNITS = 4096;
+constexpr int MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
+
+// Device address of g_scratch per device. In host code `g_scratch` names a host
+// stand-in, not device memory, so the address must come from the runtime.
+std::mutex g_mu;
+void* g_scratch_dev[MAX_DEVICES] = {nullptr};
+
+int scratch_address(void** out, char* err, int err_len) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+    cudaGetLastError();
+    if (err && err_len > 0) snprintf(err, err_len, "no usable CUDA device");
+    return DEBYE_ECUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_scratch_dev[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      if (err && err_len > 0)
+        snprintf(err, err_len, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
+      return DEBYE_ECUDA;
+    }
+    g_scratch_dev[dev] = p;
+  }
+  *out = g_scratch_dev[dev];
+  return DEBYE_OK;
+}
+
+// Bump allocator over the fixed array (offsets only, nothing is allocated).
+struct Carve {
+  unsigned char* base;
+  size_t used = 0;
+  bool ok = true;
+  void* take(size_t bytes) {
+    const size_t off = (used + 255) & ~(size_t)255;
+    if (off + bytes > SCRATCH_BYTES) {
+      ok = false;
+      return nullptr;
+    }
+    used = off + bytes;
+    return base + off;
+  }
+};
+
+int fail_msg(int code, char* err, int err_len, const char* msg) {
+  if (err && err_len > 0) snprintf(err, err_len, "%s", msg);
+  return code;
+}
+
+}  // namespace
+}  // namespace debyefit
+
+using namespace debyefit;
+
+extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const debye_spectra* sp,
+                                             int32_t P, int32_t n_max, const double* theta,
+                                             double* cost, double* weights, char* err,
+                                             int32_t err_len, cudaStream_t st) {
+  if (err && err_len > 0) err[0] = '\0';
+  debye_options opt;
+  if (opt_in) opt = *opt_in;
+  else debye_default_options(&opt);
+  if (opt.precision != DEBYE_PREC_FP64 && opt.precision != DEBYE_PREC_MIXED)
+    return fail_msg(DEBYE_EINVAL, err, err_len, "precision must be DEBYE_PREC_FP64 or DEBYE_PREC_MIXED");
+  if (opt.refine_steps < 1 || opt.refine_steps > 4 || !(opt.lam_search >= 0.0))
+    return fail_msg(DEBYE_EINVAL, err, err_len, "refine_steps outside 1..4 or negative lam_search");
+  if (!sp) return fail_msg(DEBYE_EINVAL, err, err_len, "spectra is NULL");
+  if (sp->S < 0 || P < 1 || n_max < 1 || n_max > NMAX)
+    return fail_msg(DEBYE_EINVAL, err, err_len, "S < 0, P < 1 or n_max outside 1..DEBYE_MAX_POLES");
+  if (sp->S == 0) return DEBYE_OK;
+  if (!sp->offsets_host || !sp->n_poles_host)
+    return fail_msg(DEBYE_EINVAL, err, err_len, "offsets_host and n_poles_host are required");
+  if (!sp->offsets || !sp->omega || !sp->eps_re || !sp->eps_im || !sp->n_poles || !sp->lo || !sp->hi ||
+      !theta || !cost)
+    return fail_msg(DEBYE_EINVAL, err, err_len, "a required pointer is NULL");
+  const int64_t S = sp->S;
+  const int64_t Q = S * (int64_t)P;
+  if (Q > ((int64_t)1 << 31) - 1) return fail_msg(DEBYE_EINVAL, err, err_len, "S*P exceeds 2^31-1");
+  if (opt.cands_per_block != 0 &&
+      (opt.cands_per_block < 32 || opt.cands_per_block > MAX_BLOCK || opt.cands_per_block % 32))
+    return fail_msg(DEBYE_EINVAL, err, err_len, "cands_per_block");
+  int cb, ks;
+  choose_layout(P, opt.cands_per_block, &cb, &ks);
+  const int64_t* offs = sp->offsets_host;
+  if (offs[0] != 0) return fail_msg(DEBYE_EINVAL, err, err_len, "offsets[0] must be 0");
+
+  // work units, grouped by pole bucket, on the host stack
+  Unit units[MAX_UNITS];
+  int begin[N_BUCKETS + 1];
+  int n_units = 0;
+  for (int b = 0; b < N_BUCKETS; ++b) {
+    begin[b] = n_units;
+    for (int64_t s = 0; s < S; ++s) {
+      const int N = sp->n_poles_host[s];
+      if (N < 1 || N > n_max || offs[s + 1] < offs[s])
+        return fail_msg(DEBYE_EINVAL, err, err_len, "n_poles outside 1..n_max or offsets decreasing");
+      if (bucket_of(N) != b) continue;
+      for (int64_t q = s * P; q < (s + 1) * P; q += cb) {
+        if (n_units == MAX_UNITS)
+          return fail_msg(DEBYE_EINVAL, err, err_len, "batch needs more than 4096 work units");
+        Unit& u = units[n_units++];
+        u.s = (int32_t)s;
+        u.q0 = (int32_t)q;
+        u.q1 = (int32_t)std::min<int64_t>((s + 1) * P, q + cb);
+        u.N = N;
+        u.k0 = offs[s];
+        u.k1 = offs[s + 1];
+      }
+    }
+  }
+  begin[N_BUCKETS] = n_units;
+  const int64_t n_samples = offs[S];
+
+  // carve the fixed scratch: status, units, per-sample, per-spectrum and per-candidate arrays
+  void* base = nullptr;
+  int rc = scratch_address(&base, err, err_len);
+  if (rc) return rc;
+  Carve cv{(unsigned char*)base};
+  const int nm1 = n_max + 1;
+  const int npk = nm1 * (nm1 + 1) / 2;
+  int* status = (int*)cv.take(sizeof(int));
+  Unit* d_units = (Unit*)cv.take(sizeof(Unit) * n_units);
+  float4* kf32 = (float4*)cv.take(sizeof(float4) * n_samples);
+  float4* kff = (float4*)cv.take(sizeof(float4) * n_samples);
+  double* h0 = (double*)cv.take(sizeof(double) * S);
+  Scratch sc{};
+  sc.Q = Q;
+  sc.nmax = n_max;
+  sc.ng = npk + nm1;
+  sc.G = (double*)cv.take(sizeof(double) * sc.ng * Q);
+  sc.L = (double*)cv.take(sizeof(double) * npk * Q);
+  sc.dinv = (double*)cv.take(sizeof(double) * nm1 * Q);
+  sc.x = (double*)cv.take(sizeof(double) * nm1 * Q);
+  sc.xh = (double*)cv.take(sizeof(double) * nm1 * Q);
+  sc.w = (double*)cv.take(sizeof(double) * nm1 * Q);
+  double* g1 = (double*)cv.take(sizeof(double) * nm1 * Q);
+  sc.rt = (double*)cv.take(sizeof(double) * (nm1 + 1) * Q);
+  sc.gt = sc.G;
+  sc.fail = (int32_t*)cv.take(sizeof(int32_t) * Q);
+  if (!cv.ok) {
+    if (err && err_len > 0)
+      snprintf(err, err_len, "batch needs more than the %zu-byte allocation-free scratch "
+               "(S=%lld, P=%d, n_max=%d, samples=%lld)", SCRATCH_BYTES, (long long)S, P, n_max,
+               (long long)n_samples);
+    return DEBYE_EINVAL;
+  }
+
+  int sms = 1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_units, units, sizeof(Unit) * n_units, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail_msg(DEBYE_ECUDA, err, err_len, cudaGetErrorString(e));
+  }
+  launch_prep(n_samples, S, sp->offsets, sp->omega, sp->eps_re, sp->eps_im, sp->lo, sp->hi, kf32, kff, h0,
+              status, sms, st);
+
+  EvalArgs a{};
+  a.units = d_units;
+  a.n_units = n_units;
+  a.theta = theta;
+  a.kf32 = kf32;
+  a.kff = kff;
+  a.omega = sp->omega;
+  a.eps_re = sp->eps_re;
+  a.eps_im = sp->eps_im;
+  a.h0 = h0;
+  a.active = nullptr;
+  a.ks = ks;
+  a.lam = opt.lam_search;
+  a.sc = sc;
+  a.status = status;
+  const bool mixed = opt.precision == DEBYE_PREC_MIXED;
+  auto per_bucket = [&](int phase) {
+    for (int b = 0; b < N_BUCKETS; ++b) {
+      const int n = begin[b + 1] - begin[b];
+      if (!n) continue;
+      EvalArgs ab = a;
+      ab.units = a.units + begin[b];
+      ab.n_units = n;
+      const int grid = std::max(1, std::min(n, sms * 16));
+      switch (b) {
+        case 0: launch_pass_b0(phase, mixed, ab, grid, cb * ks, st); break;
+        case 1: launch_pass_b1(phase, mixed, ab, grid, cb * ks, st); break;
+        case 2: launch_pass_b2(phase, mixed, ab, grid, cb * ks, st); break;
+        case 3: launch_pass_b3(phase, mixed, ab, grid, cb * ks, st); break;
+        default: launch_pass_b4(phase, mixed, ab, grid, cb * ks, st); break;
+      }
+    }
+  };
+  per_bucket(PH_GRAM);
+  launch_solve(a, warp_round(cb), sms, st);
+  for (int it = 0; it < opt.refine_steps; ++it) {
+    per_bucket(PH_REFINE);
+    launch_finish(a, it + 1 == opt.refine_steps ? 1 : 0, cost, weights, g1, warp_round(cb), sms, st);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_msg(DEBYE_ECUDA, err, err_len, cudaGetErrorString(e));
+
+  // wait for the work and report what the device detected (non-finite input, bounds)
+  int dstatus = 0;
+  e = cudaMemcpyAsync(&dstatus, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail_msg(DEBYE_ECUDA, err, err_len, cudaGetErrorString(e));
+  if (dstatus != 0) return fail_msg(dstatus, err, err_len, "device reported invalid input (non-finite or bounds)");
+  return DEBYE_OK;
+}

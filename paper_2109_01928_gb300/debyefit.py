@@ -89,11 +89,14 @@ def lib() -> ctypes.CDLL:
     L.debye_version.restype = ctypes.c_char_p
     L.debye_profile_enable.argtypes = [_VP, ctypes.c_int32]
     L.debye_launch_count.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]
+    L.debye_eval_population_noalloc.argtypes = [ctypes.POINTER(Options), ctypes.POINTER(SpectraC),
+                                                ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP,
+                                                ctypes.c_char_p, ctypes.c_int32, _VP]
     L.debye_profile_read.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     for f in ("debye_fit_init", "debye_fit_destroy", "debye_synth_targets", "debye_eval_population",
               "debye_cost_grad", "debye_fit_batch", "debye_sync", "debye_profile_enable",
-              "debye_profile_read", "debye_launch_count"):
+              "debye_profile_read", "debye_launch_count", "debye_eval_population_noalloc"):
         getattr(L, f).restype = _I
     _lib = L
     return L
@@ -277,6 +280,30 @@ def debye_sync(h: Handle, stream=None):
 
 
 KERNEL_KINDS = {"gram": 0, "refine": 1, "grad": 2, "solve": 3, "finish": 4}
+
+
+def debye_eval_population_noalloc(sp: Spectra, theta, precision: str = "mixed", weights: bool = False,
+                                  n_max: int | None = None, options: Options | None = None, cost=None,
+                                  weights_out=None, stream=None):
+    """debye_eval_population without a handle and without any device allocation by the
+    library (fixed scratch inside the library); the caller provides the outputs."""
+    import torch
+    S, P, nm = theta.shape
+    n_max = nm if n_max is None else n_max
+    o = options if options is not None else default_options()
+    o.precision = {"mixed": PREC_MIXED, "fp64": PREC_FP64}[precision]
+    if cost is None:
+        cost = torch.empty((S, P), dtype=torch.float64, device=theta.device)
+    if weights and weights_out is None:
+        weights_out = torch.empty((S, P, n_max + 1), dtype=torch.float64, device=theta.device)
+    buf = ctypes.create_string_buffer(512)
+    c = sp.c()
+    rc = lib().debye_eval_population_noalloc(ctypes.byref(o), ctypes.byref(c), P, n_max, _ptr(theta),
+                                             _ptr(cost), _ptr(weights_out) if weights else None, buf, 512,
+                                             _stream(stream))
+    if rc != DEBYE_OK:
+        raise DebyeError(rc, buf.value.decode())
+    return (cost, weights_out) if weights else cost
 
 
 def debye_launch_count(h: Handle, reset: bool = False) -> int:
