@@ -14,6 +14,7 @@ Modules
   varpro  analytic gradient of that cost w.r.t. log10(tau)
   rng     SplitMix64 counter-based random numbers
   pso     particle-swarm search over log10(tau) (Sec. III-A, Kennedy-Eberhart)
+  de      differential evolution over log10(tau) (Sec. III-B, Storn-Price)
   lbfgs   projected L-BFGS polish
   fit     the whole fit of one spectrum and the reported result (Listing 2)
 

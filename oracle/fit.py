@@ -1,7 +1,7 @@
 """Whole fit of one spectrum and the reported result (oracle).
 
-Sequence (Sec. III-B, IV): particle swarm over log10(tau) with DLS weights per
-particle (damping LAM_SEARCH), projected L-BFGS polish of the best `topk`
+Sequence (Sec. III-B, IV): particle swarm (or differential evolution) over
+log10(tau) with DLS weights per candidate (damping LAM_SEARCH), projected L-BFGS polish of the best `topk`
 personal bests (lowest cost first, lowest particle index on ties), the best
 polished candidate (lowest cost, lowest rank on ties) re-solved with damping
 LAM_FINAL (by default the search damping: the reported weights are the DLS
@@ -13,16 +13,25 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import dls, lbfgs, pso, varpro
+from . import de, dls, lbfgs, pso, varpro
 
 
 def fit_spectrum(omega, eps_re, eps_im, N: int, lo: float, hi: float, P: int, iters: int,
                  seed: int = 0, spectrum: int = 0, topk: int = 8, polish_iters: int = 50,
-                 lam_search: float = dls.LAM_SEARCH, lam_final: float = dls.LAM_FINAL):
+                 lam_search: float = dls.LAM_SEARCH, lam_final: float = dls.LAM_FINAL,
+                 method: str = "pso", de_opts: dict | None = None):
+    """method "pso" (particle swarm) or "de" (differential evolution, keyword
+    arguments of de.de in de_opts); the polish starts from the best personal
+    bests (swarm) or population members (evolution)."""
     def cost_fn(th):
         return dls.cost_population(omega, eps_re, eps_im, th, lam_search)[0]
 
-    pbx, pbc, gi, trace = pso.pso(cost_fn, N, lo, hi, P, iters, seed, spectrum)
+    if method == "pso":
+        pbx, pbc, gi, trace = pso.pso(cost_fn, N, lo, hi, P, iters, seed, spectrum)
+    elif method == "de":
+        pbx, pbc, gi, trace = de.de(cost_fn, N, lo, hi, P, iters, seed, spectrum, **(de_opts or {}))
+    else:
+        raise ValueError("method must be 'pso' or 'de'")
     order = np.argsort(pbc, kind="stable")
     best_th, best_c = pbx[gi].copy(), float(pbc[gi])
     n_evals = P * (iters + 1)

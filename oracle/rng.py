@@ -14,7 +14,10 @@ number generators", OOPSLA 2014), used as a mixing function:
 all modulo 2^64. The key is absorbed one field at a time,
     h = mix(seed); h = mix(h ^ tag); h = mix(h ^ spectrum);
     h = mix(h ^ generation); h = mix(h ^ particle); h = mix(h ^ dim),
-and the uniform double is (h >> 11) * 2^-53 in [0, 1).
+and the uniform double is (h >> 11) * 2^-53 in [0, 1). An integer below m
+(m < 2^32) is ((h >> 32) * m) >> 32, the multiply-shift map of the key's upper
+32 bits (Lemire, "Fast random integer generation in an interval", 2019,
+without the rejection step; the bias is below m / 2^32).
 """
 from __future__ import annotations
 
@@ -24,6 +27,11 @@ TAG_INIT_POS = 1
 TAG_INIT_VEL = 2
 TAG_R1 = 3
 TAG_R2 = 4
+TAG_DE_IDX = 5     # differential evolution: donor indices
+TAG_DE_J = 6       # the coordinate always taken from the mutant
+TAG_DE_CR = 7      # binomial crossover draws
+TAG_DE_BOUND = 8   # re-draw of a mutant coordinate outside the bounds
+TAG_DE_F = 9       # per-generation scale factor (dither)
 
 
 def mix(z: int) -> int:
@@ -48,6 +56,11 @@ def uniform(seed: int, tag: int, spectrum: int, generation: int, particle: int, 
     return (key(seed, tag, spectrum, generation, particle, dim) >> 11) * (1.0 / (1 << 53))
 
 
+def below(z: int, m: int) -> int:
+    """Integer in [0, m) from the key z (multiply-shift of the upper 32 bits)."""
+    return ((z >> 32) * m) >> 32
+
+
 def mix_array(z):
     """`mix` over a numpy uint64 array (wrap-around arithmetic mod 2^64)."""
     import numpy as np
@@ -59,13 +72,19 @@ def mix_array(z):
     return z ^ (z >> np.uint64(31))
 
 
-def uniform_array(seed: int, tag: int, spectrum: int, generation: int, P: int, N: int):
-    """uniform(seed, tag, spectrum, generation, p, d) for all p < P, d < N, as (P, N)."""
+def key_array(seed: int, tag: int, spectrum: int, generation: int, P: int, N: int):
+    """key(seed, tag, spectrum, generation, p, d) for all p < P, d < N, as uint64 (P, N)."""
     import numpy as np
     h = mix(seed & MASK)
     h = mix(h ^ tag)
     h = mix(h ^ (spectrum & MASK))
     h = mix(h ^ (generation & MASK))
     hp = mix_array(np.uint64(h) ^ np.arange(P, dtype=np.uint64))
-    hd = mix_array(hp[:, None] ^ np.arange(N, dtype=np.uint64)[None, :])
+    return mix_array(hp[:, None] ^ np.arange(N, dtype=np.uint64)[None, :])
+
+
+def uniform_array(seed: int, tag: int, spectrum: int, generation: int, P: int, N: int):
+    """uniform(seed, tag, spectrum, generation, p, d) for all p < P, d < N, as (P, N)."""
+    import numpy as np
+    hd = key_array(seed, tag, spectrum, generation, P, N)
     return (hd >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))

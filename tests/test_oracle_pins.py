@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle import dls, fit, lbfgs, models, pso, rng, varpro
+from oracle import de, dls, fit, lbfgs, models, pso, rng, varpro
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -256,7 +256,82 @@ def test_uniform_array_matches_scalar():
     assert 0.0 <= big.min() and big.max() < 1.0 and abs(big.mean() - 0.5) < 0.01
 
 
+def test_below_bounds_and_uniformity():
+    # multiply-shift of the upper 32 bits: the extreme keys map to the ends of [0, m)
+    assert rng.below(0, 7) == 0 and rng.below(rng.MASK, 7) == 6
+    assert rng.below((1 << 63), 2) == 1 and rng.below((1 << 63) - 1, 2) == 0
+    z = rng.key_array(3, rng.TAG_DE_IDX, 0, 0, 20000, 1)[:, 0]
+    r = ((z >> np.uint64(32)) * np.uint64(7)) >> np.uint64(32)
+    counts = np.bincount(r.astype(np.int64), minlength=7)
+    chi2 = float(np.sum((counts - 20000 / 7) ** 2 / (20000 / 7)))
+    assert counts.size == 7 and chi2 < 22.5   # 99.9 % quantile of chi-square with 6 dof
+
+
 # ---------------------------------------------------------------- search
+
+def test_de_donors_are_distinct_uniform_and_rank_mapped():
+    for P in (4, 5, 17, 64):
+        for g in range(1, 6):
+            d = de.donors(11, 2, g, P, 3)
+            assert d.min() >= 0 and d.max() < P
+            for p in range(P):
+                assert len({p, *d[p]}) == 4
+    # brute force on a tiny population: slot j takes the r-th free index in ascending order
+    P = 6
+    z = rng.key_array(5, rng.TAG_DE_IDX, 1, 3, P, 3)
+    d = de.donors(5, 1, 3, P, 3)
+    for p in range(P):
+        taken = [p]
+        for j in range(3):
+            free = [i for i in range(P) if i not in taken]
+            r = rng.below(int(z[p, j]), P - 1 - j)
+            assert d[p, j] == free[r]
+            taken.append(free[r])
+    # each other member is an equally likely first donor
+    counts = np.zeros(8)
+    for g in range(1, 801):
+        counts += np.bincount(de.donors(0, 0, g, 8, 3)[:, 0], minlength=8)
+    expected = 800 * 8 / 8
+    assert float(np.sum((counts - expected) ** 2 / expected)) < 24.3   # 99.9 % of chi-square, 7 dof
+
+
+def test_de_trial_structure():
+    rs = np.random.default_rng(4)
+    x = rs.uniform(-12, -6, size=(5, 3))
+    # F = 0, CR = 1: every trial is another member of the population (the first donor)
+    u = de.trials(x, 0, 0, 0, 1, -13.0, -5.0, f_lo=0.0, f_hi=0.0, cr=1.0)
+    for p in range(5):
+        assert any(np.array_equal(u[p], x[i]) for i in range(5) if i != p)
+    # F = 1, CR = 1, inside the box: trial = one member plus the difference of two others
+    u = de.trials(x, 0, 0, 0, 2, -40.0, 30.0, f_lo=1.0, f_hi=1.0, cr=1.0)
+    for p in range(5):
+        found = [(a, b, c) for a in range(5) for b in range(5) for c in range(5)
+                 if len({p, a, b, c}) == 4 and np.allclose(u[p], x[a] + (x[b] - x[c]), rtol=0, atol=1e-12)]
+        assert found, p
+    # best/1: trial = best member plus the difference of two members other than the target
+    u = de.trials(x, 3, 0, 0, 2, -40.0, 30.0, f_lo=1.0, f_hi=1.0, cr=1.0, strategy=de.BEST1)
+    for p in range(5):
+        assert any(len({p, b, c}) == 3 and np.allclose(u[p], x[3] + (x[b] - x[c]), rtol=0, atol=1e-12)
+                   for b in range(5) for c in range(5))
+    # CR = 0: exactly one coordinate comes from the mutant
+    x = rs.uniform(-12, -6, size=(64, 6))
+    u = de.trials(x, 0, 0, 0, 1, -13.0, -5.0, cr=0.0)
+    assert np.all(np.sum(u != x, axis=1) == 1)
+    # large F: every coordinate stays in the box (mutants outside are re-drawn)
+    u = de.trials(x, 0, 0, 0, 1, -13.0, -5.0, f_lo=8.0, f_hi=8.0, cr=1.0)
+    assert u.min() >= -13.0 and u.max() <= -5.0
+
+
+@pytest.mark.parametrize("strategy", [de.RAND1, de.BEST1])
+def test_de_finds_quadratic_minimum(strategy):
+    target = np.array([-9.3, -7.7, -11.1])
+    def f(th):
+        return np.sum((th - target) ** 2, axis=1)
+    x, c, gi, trace = de.de(f, 3, -13, -5, 32, 300, seed=1, strategy=strategy)
+    assert np.all(np.diff(trace) <= 0)
+    np.testing.assert_allclose(x[gi], target, atol=1e-4)
+    assert np.all(c >= c[gi]) and np.all(c == f(x))
+
 
 def test_pso_finds_quadratic_minimum():
     target = np.array([-9.3, -7.7])
@@ -307,13 +382,14 @@ def _brute_force_n2(om, re, im, lam, n=301):
     return best
 
 
+@pytest.mark.parametrize("method", ["pso", "de"])
 @pytest.mark.parametrize("N", [1, 2])
-def test_search_reaches_brute_force_minimum(N):
+def test_search_reaches_brute_force_minimum(N, method):
     b = W.single_hn(K=50, N=N)
     re, im = models.synthesize(b)
     lam = dls.LAM_SEARCH
     bf = _brute_force_n1(b.omega, re, im, lam) if N == 1 else _brute_force_n2(b.omega, re, im, lam)
-    r = fit.fit_spectrum(b.omega, re, im, N, -13.0, -6.0, 64, 100, topk=8)
+    r = fit.fit_spectrum(b.omega, re, im, N, -13.0, -6.0, 64, 100, topk=8, method=method)
     assert r["cost_search"] <= (1 + 1e-6) * bf
 
 
