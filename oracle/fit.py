@@ -69,3 +69,25 @@ def fitted_eps(omega, result) -> np.ndarray:
     """Complex permittivity of a fit result (Eq. 7)."""
     return dls.model_eps(omega, np.concatenate([[result["eps_inf"]], result["d_eps"]]),
                          np.log10(result["tau"]))
+
+
+AUTO_THRESHOLD = 5.0   # percent
+AUTO_N_MAX = 20
+
+
+def fit_auto(omega, eps_re, eps_im, lo: float, hi: float, P: int, iters: int, seed: int = 0,
+             spectrum: int = 0, topk: int = 8, polish_iters: int = 50, n_hi: int = AUTO_N_MAX,
+             threshold: float = AUTO_THRESHOLD, **kw):
+    """Automatic number of poles (Sec. III-B, N = -1): fit with N = 1, 2, ... poles
+    and stop at the first N whose average fractional error (Sec. IV metric, in
+    percent: mean relative error of eps' plus that of eps'') is below `threshold`,
+    or at N = n_hi (the paper's cap is 20 poles and 5 %). Every N is a complete
+    fit of its own with the same seed and spectrum index. Returns that fit's
+    record with "N" added."""
+    for N in range(1, n_hi + 1):
+        r = fit_spectrum(omega, eps_re, eps_im, N, lo, hi, P, iters, seed=seed, spectrum=spectrum,
+                         topk=topk, polish_iters=polish_iters, **kw)
+        if r["avg_frac_err"] < threshold:
+            break
+    r["N"] = N
+    return r

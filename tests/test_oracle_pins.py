@@ -393,6 +393,31 @@ def test_search_reaches_brute_force_minimum(N, method):
     assert r["cost_search"] <= (1 + 1e-6) * bf
 
 
+def _debye_target(om, eps_inf, d_eps, tau):
+    e = models.multi_debye(om, eps_inf, np.asarray(d_eps, float), np.asarray(tau, float))
+    return e.real.copy(), -e.imag.copy()
+
+
+def test_auto_pole_count_on_exact_debye_sums():
+    # a single Debye pole is recovered with N = 1; the Marquardt damping (1e-3)
+    # biases the weights by well under 1 %, far below the 5 % threshold
+    om = W.log_grid(1e6, 1e11, 120)
+    re, im = _debye_target(om, 3.0, [20.0], [1e-9])
+    r = fit.fit_auto(om, re, im, -13.0, -5.0, 32, 30, topk=4, polish_iters=30, n_hi=6)
+    assert r["N"] == 1 and r["avg_frac_err"] < 1.0
+    # two poles four decades apart: one pole cannot follow both loss peaks (its
+    # error is far above 5 %); two poles recover the sum up to the damping bias
+    re, im = _debye_target(om, 3.0, [20.0, 20.0], [1e-11, 1e-7])
+    one = fit.fit_spectrum(om, re, im, 1, -13.0, -5.0, 32, 30, topk=4, polish_iters=30)
+    assert one["avg_frac_err"] > 20.0
+    r = fit.fit_auto(om, re, im, -13.0, -5.0, 32, 40, topk=4, polish_iters=40, n_hi=6)
+    assert r["N"] == 2 and r["avg_frac_err"] < 1.0
+    np.testing.assert_allclose(r["tau"], [1e-11, 1e-7], rtol=2e-2)
+    # a threshold nothing reaches runs up to the cap
+    r = fit.fit_auto(om, re, im, -13.0, -5.0, 16, 5, topk=0, polish_iters=0, n_hi=3, threshold=0.0)
+    assert r["N"] == 3
+
+
 def test_fit_is_passive_and_sorted():
     b = W.single_hn()
     re, im = models.synthesize(b)
