@@ -308,6 +308,10 @@ def main():
         return times, evals, out, h2d, d2h
 
     hm = D.Handle("mixed")
+    # pick the work layout on this batch before timing (project autotuner)
+    th_tune = torch.as_tensor(W.population(b, b.P, seed=2), device=dev)
+    tuned = D.debye_autotune(hm, sp, th_tune)
+    del th_tune
     with ClockSampler(local) as clk:
         times, evals, out_mixed, _, _ = timed_steps(hm, args.steps, args.warmup)
     clocks = clk.summary()
@@ -335,10 +339,50 @@ def main():
     fN = float(np.sum(b.K * b.P * (4 * b.n_poles + 2 * (b.n_poles + 2.0) ** 2)) / np.sum(b.K * b.P))
     step_fp32 = value / world * fN / 1e12
 
+    # one batched evaluation of the whole population vs one launch sequence per spectrum
+    batching = None
+    if not args.no_fp64 and world == 1:
+        th_pop = torch.as_tensor(W.population(b, b.P, seed=1), device=dev)
+        per_spec = []
+        for s in range(S):
+            a_, c_ = int(b.offsets[s]), int(b.offsets[s + 1])
+            per_spec.append((D.Spectra(tt(np.array([0, c_ - a_]), torch.int64), omega_d[a_:c_], eps_re_d[a_:c_],
+                                       eps_im_d[a_:c_], tt(b.n_poles[s:s + 1], torch.int32), tt(b.lo[s:s + 1]),
+                                       tt(b.hi[s:s + 1]), np.array([0, c_ - a_], np.int64),
+                                       np.ascontiguousarray(b.n_poles[s:s + 1], np.int32)),
+                             th_pop[s:s + 1].contiguous()))
+        batching = {}
+        for prec in ("mixed", "fp64"):
+            with D.Handle(prec) as hb:
+                D.debye_eval_population(hb, sp, th_pop)        # warm-up (workspaces)
+                for spx, thx in per_spec[:4]:
+                    D.debye_eval_population(hb, spx, thx)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                D.debye_eval_population(hb, sp, th_pop)
+                e1.record()
+                torch.cuda.synchronize()
+                t_batched = e0.elapsed_time(e1)
+                t0 = time.perf_counter()
+                e0.record()
+                for spx, thx in per_spec:
+                    D.debye_eval_population(hb, spx, thx)
+                e1.record()
+                torch.cuda.synchronize()
+                t_each = e0.elapsed_time(e1)
+            candk = float(b.P * b.K.sum())
+            batching[prec] = {"batched_ms": t_batched, "per_spectrum_ms": t_each,
+                              "batched_candK_per_s": candk / (t_batched * 1e-3),
+                              "per_spectrum_candK_per_s": candk / (t_each * 1e-3)}
+
     # the plain FP64 GPU evaluator on the same workload, and agreement of the fitted spectra
     fp64 = None
     if not args.no_fp64:
         hd = D.Handle("fp64")
+        th_tune = torch.as_tensor(W.population(b, b.P, seed=2), device=dev)
+        D.debye_autotune(hd, sp, th_tune)
+        del th_tune
         d_times, d_evals, out_fp64, _, _ = timed_steps(hd, 1, 1)
         d_value = sum_over_ranks(sum(d_evals)) / max_over_ranks(sum(d_times) * 1e-3)
         from oracle import models as om
@@ -379,6 +423,7 @@ def main():
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "autotune": {"cands_per_block": tuned},
         "roofline": {"bound": "alu", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "traffic": traffic,
                      "launches": n_l, "ms_per_launch": ms_l / max(n_l, 1),
@@ -387,6 +432,7 @@ def main():
                      "per_kind_ms": {k: v[1] for k, v in prof.items()}},
         "cpu_baseline": cpu,
         "fp64_plain": fp64,
+        "eval_batching": batching,
     }
     print(json.dumps(line))
     if world > 1:

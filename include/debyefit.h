@@ -9,7 +9,8 @@
  *     Cole-Davidson, Jonscher, CRIM: Eqs. 3-6) or by tabulated values (Sec. III-A);
  *   - is approximated by the multi-pole Debye expansion
  *     eps_inf + sum_n d_eps_n / (1 + j w tau_n)                             (Eq. 7);
- *   - a global optimiser (particle swarm) searches the relaxation times, and for
+ *   - a global optimiser (particle swarm or differential evolution) searches the
+ *     relaxation times, and for
  *     each candidate the weights (eps_inf, d_eps_n) come from damped least squares
  *     over the real and imaginary parts, with negative weights sign-flipped as a
  *     penalty (Sec. III-A, III-B);
@@ -70,6 +71,12 @@ extern "C" {
 #define DEBYE_MODEL_DEBYE_SUM    7  /* Eq. 7 source poles + Jonscher tail + noise */
 #define DEBYE_N_PARAMS          16  /* float64 parameter record per spectrum */
 
+/* ------------------------------------------------------------------ search methods */
+#define DEBYE_SEARCH_PSO 0    /* particle swarm (Sec. III-B; Kennedy and Eberhart) */
+#define DEBYE_SEARCH_DE  1    /* differential evolution (Sec. III-B; Storn and Price) */
+#define DEBYE_DE_RAND1   0    /* mutant x_r1 + F (x_r2 - x_r3), needs P >= 4 */
+#define DEBYE_DE_BEST1   1    /* mutant x_best + F (x_r1 - x_r2), needs P >= 3 */
+
 typedef struct debye_ctx* debye_handle;
 
 /* Solver options. debye_default_options() fills the documented defaults. */
@@ -86,6 +93,10 @@ typedef struct {
   double  lbfgs_c1;       /* Armijo constant (default 1e-4) */
   int32_t cands_per_block;/* candidates per thread block, 32..128, multiple of 32; 0 = autotune */
   int32_t use_graphs;     /* capture the generation and polish loops in CUDA graphs (default 1) */
+  double  de_f_lo;        /* differential evolution: scale factor F ~ U[de_f_lo, de_f_hi) drawn */
+  double  de_f_hi;        /*   once per generation; 0 <= lo <= hi <= 2 (default 0.5, 1.0) */
+  double  de_cr;          /* binomial crossover rate, 0..1 (default 0.7) */
+  int32_t de_strategy;    /* DEBYE_DE_RAND1 (default) or DEBYE_DE_BEST1 */
 } debye_options;
 
 /* A ragged batch of S spectra, CSR over frequency (all device memory unless _host). */
@@ -104,13 +115,14 @@ typedef struct {
 
 /* Search settings of debye_fit_batch. */
 typedef struct {
-  int32_t  P;             /* particles per spectrum, 1..32768 */
-  int32_t  iters;         /* swarm generations after the initial one, >= 0 */
+  int32_t  P;             /* particles (population members) per spectrum, 1..32768 */
+  int32_t  iters;         /* generations after the initial one, >= 0 */
   uint64_t seed;          /* seed of the counter-based generator */
   int32_t  polish_topk;   /* personal bests polished per spectrum, 0..min(P,64) */
   int32_t  polish_iters;  /* L-BFGS iterations per polished candidate, >= 0 */
   double*  trace;         /* optional [S][iters+1] device: global-best cost per generation */
   double*  evals;         /* optional [1] device: candidate evaluations x K performed */
+  int32_t  method;        /* DEBYE_SEARCH_PSO (0) or DEBYE_SEARCH_DE */
 } debye_search;
 
 /* Fill *opt with the defaults listed above. */
@@ -150,14 +162,34 @@ int debye_eval_population(debye_handle h, const debye_spectra* spectra, int32_t 
 int debye_cost_grad(debye_handle h, const debye_spectra* spectra, int32_t P, int32_t n_max,
                     const double* theta, double* cost, double* grad, cudaStream_t stream);
 
-/* Whole fit (Sec. III-B, IV): seeded particle swarm over log10(tau) with DLS
- * weights, projected L-BFGS polish of the best polish_topk personal bests, the
+/* Whole fit (Sec. III-B, IV): seeded particle swarm or differential evolution
+ * over log10(tau) with DLS weights, projected L-BFGS polish of the best
+ * polish_topk personal bests (swarm) or population members (evolution), the
  * best result re-solved in FP64 at damping lam_final with the sign flip, poles
  * sorted by ascending tau. Outputs eps_inf [S], d_eps [S][n_max], tau [S][n_max]
  * (seconds; entries beyond N_s are 0) and final_cost [S] (cost at lam_final). */
 int debye_fit_batch(debye_handle h, const debye_spectra* spectra, const debye_search* search,
                     int32_t n_max, double* eps_inf, double* d_eps, double* tau,
                     double* final_cost, cudaStream_t stream);
+
+/* Automatic number of poles (Sec. III-B: the pole count set to -1). For every
+ * spectrum, complete fits as debye_fit_batch makes them (same search settings)
+ * with N = 1, 2, ... poles; the result is the fit with the first N whose average
+ * fractional error is below `threshold` (percent; the paper uses 5), or with
+ * N = n_poles[s] if none is (n_poles is the per-spectrum cap here; the paper's
+ * is 20). The error is the mean over the spectrum's samples of
+ * |eps'_fit - eps'| / |eps'| plus the same mean for eps'' (Sec. IV), times 100.
+ * Every fit of spectrum s draws its random numbers with s as the spectrum key,
+ * whatever N, so the result equals that of the sequential N = 1, 2, ... loop.
+ * The fits run in waves of `wave` (1..20) consecutive pole counts, each wave one
+ * ragged batch; spectra that found their N leave before the next wave (the call
+ * synchronises its work stream once per wave). Outputs as debye_fit_batch
+ * (d_eps, tau [S][n_max], zero beyond the chosen N) plus frac_err [S] (percent)
+ * and n_chosen [S]. search->trace must be NULL. */
+int debye_fit_auto(debye_handle h, const debye_spectra* spectra, const debye_search* search,
+                   int32_t n_max, double threshold, int32_t wave, double* eps_inf, double* d_eps,
+                   double* tau, double* final_cost, double* frac_err, int32_t* n_chosen,
+                   cudaStream_t stream);
 
 /* Allocation-free evaluation. The paper has no counterpart to this entry point;
  * it exists for callers that cannot let the library allocate device memory, such
@@ -188,6 +220,18 @@ int debye_eval_population_noalloc(const debye_options* opt, const debye_spectra*
                                   int32_t n_max, const double* theta, double* cost, double* weights,
                                   char* err, int32_t err_len, cudaStream_t stream);
 
+/* Work-layout autotuner. Times debye_eval_population on the caller's batch
+ * (theta as for that call, cost [S][P] is overwritten) for every candidates-
+ * per-block choice (32, 64, 96, 128) and keeps the fastest for this handle; it
+ * is used by later calls whose options leave cands_per_block at 0 (auto).
+ * cache_path (may be NULL) is a text file of "key | choice" lines keyed by the
+ * device's SM count, precision, S, P, n_max and sample count: a cached choice
+ * is reused without timing, a new one is appended. *chosen (may be NULL)
+ * receives the choice. Synchronises `stream`. */
+int debye_autotune(debye_handle h, const debye_spectra* spectra, int32_t P, int32_t n_max,
+                   const double* theta, double* cost, const char* cache_path, int32_t* chosen,
+                   cudaStream_t stream);
+
 /* Wait for `stream`, then return and clear the device status word
  * (DEBYE_OK, DEBYE_ENOTFINITE, DEBYE_EBOUNDS or DEBYE_ETIMEOUT). */
 int debye_sync(debye_handle h, cudaStream_t stream);
@@ -199,7 +243,7 @@ int debye_sync(debye_handle h, cudaStream_t stream);
  * capture is switched off. Per kernel kind the library accumulates the number of
  * launches, the summed event time (ms) and the algorithmic FLOPs of the launched
  * work: per candidate and frequency sample, 4N + 2(N+2)^2 for the Gram pass (basis
- * build plus the unique Gram/right-hand-side products) and 67N + 25 for the
+ * build plus the unique Gram/right-hand-side products) and 98N + 38 for the
  * float-float residual pass (FMA counted as 2). Launches restricted by an
  * activity mask (the polish line search) count their time but no FLOPs. */
 #define DEBYE_KERNEL_GRAM   0

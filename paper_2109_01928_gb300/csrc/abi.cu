@@ -92,10 +92,15 @@ int debye_ctx::prof_collect() {
   return rc;
 }
 
-// Algorithmic FLOPs per candidate and sample of the Gram and residual passes.
+// Algorithmic FLOPs (FMA = 2) per candidate and sample of the Gram and residual passes.
+// Gram: basis (x, 1 + x^2, reciprocal, x re) and the unique Gram / right-hand-side
+// products, 4N + 2(N+2)^2. Residual (float-float): per pole 33 for the float-float
+// basis value, 30 for the two Dot2 residual updates, 30 for the two Dot2 updates
+// of A^T r and 5 for the exact column norm; per sample 38 (target split,
+// renormalisation, ||r||^2 and the eps_inf column).
 static double flops_per_cand_k(int kind, int N) {
   if (kind == DEBYE_KERNEL_GRAM) return 4.0 * N + 2.0 * (N + 2) * (N + 2);
-  if (kind == DEBYE_KERNEL_REFINE) return 67.0 * N + 25.0;
+  if (kind == DEBYE_KERNEL_REFINE) return 98.0 * N + 38.0;
   return 0.0;
 }
 
@@ -228,15 +233,35 @@ int debye_ctx::ensure_scratch(int64_t Q, int nmax, ScratchBufs& sb, Scratch& sc)
 // the gradient. Units must already be on the device (a.units).
 int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, double* cost,
                         double* weights, double* grad, double* g1, int cb, cudaStream_t st) {
+  // The buckets' launches of one pass are independent (disjoint candidates): all but
+  // the first non-empty one go to side streams forked from st and joined back, so
+  // that one bucket's tail overlaps the others' work. Kernel timing runs them in
+  // order on st instead, so that each launch's duration is its own.
   auto per_bucket = [&](int phase) -> int {
+    int first = -1, n_nonempty = 0;
+    for (int b = 0; b < N_BUCKETS; ++b)
+      if (g.begin[b + 1] > g.begin[b]) {
+        if (first < 0) first = b;
+        ++n_nonempty;
+      }
+    const bool fork = n_nonempty > 1 && !prof_on;
+    if (fork) cudaEventRecord(ev_fork, st);
     for (int b = 0; b < N_BUCKETS; ++b) {
       const int n = g.begin[b + 1] - g.begin[b];
       if (!n) continue;
+      cudaStream_t bs = st;
+      if (fork && b != first) {
+        bs = side[b];
+        cudaStreamWaitEvent(bs, ev_fork, 0);
+      }
       EvalArgs ab = a;
       ab.units = a.units + g.begin[b];
       ab.n_units = n;
       const int grid = std::max(1, std::min(n, sms * 16));
-      const int pblock = cb * a.ks;
+      // Gram rows of N >= 13 split over two warps (fewer live accumulators) when each
+      // candidate has one lane
+      ab.gs = (phase == PH_GRAM && mixed && b >= 3 && a.ks == 1 && cb % 32 == 0) ? 2 : 1;
+      const int pblock = cb * a.ks * ab.gs;
       ProfEntry pe;
       if (prof_on) {
         double fl = 0.0;
@@ -248,14 +273,18 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
         prof_begin(phase, fl, st, pe);
       }
       switch (b) {
-        case 0: launch_pass_b0(phase, mixed, ab, grid, pblock, st); break;
-        case 1: launch_pass_b1(phase, mixed, ab, grid, pblock, st); break;
-        case 2: launch_pass_b2(phase, mixed, ab, grid, pblock, st); break;
-        case 3: launch_pass_b3(phase, mixed, ab, grid, pblock, st); break;
-        default: launch_pass_b4(phase, mixed, ab, grid, pblock, st); break;
+        case 0: launch_pass_b0(phase, mixed, ab, grid, pblock, bs); break;
+        case 1: launch_pass_b1(phase, mixed, ab, grid, pblock, bs); break;
+        case 2: launch_pass_b2(phase, mixed, ab, grid, pblock, bs); break;
+        case 3: launch_pass_b3(phase, mixed, ab, grid, pblock, bs); break;
+        default: launch_pass_b4(phase, mixed, ab, grid, pblock, bs); break;
       }
       if (prof_on) prof_end(pe, st);
       ++launches;
+      if (bs != st) {
+        cudaEventRecord(ev_join[b], bs);
+        cudaStreamWaitEvent(st, ev_join[b], 0);
+      }
     }
     return check_launch("pass");
   };
@@ -324,7 +353,7 @@ static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_
     qe[s] = (int32_t)((s + 1) * P);
   }
   int cb, ks;
-  choose_layout(P, h->opt.cands_per_block, &cb, &ks);
+  choose_layout(P, h->cb_option(), &cb, &ks);
   UnitGroups g;
   build_units(pl, qb, qe, cb, g);
   if ((rc = h->upload_units(g, h->ws_units, st))) return rc;
@@ -358,6 +387,14 @@ int debye_ctx::eval_steps(bool with_grad) const {
 }
 
 
+static bool create_side_streams(debye_ctx* h) {
+  for (int b = 0; b < N_BUCKETS; ++b)
+    if (cudaStreamCreateWithFlags(&h->side[b], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join[b], cudaEventDisableTiming) != cudaSuccess)
+      return false;
+  return true;
+}
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 
@@ -376,6 +413,10 @@ void debye_default_options(debye_options* o) {
   o->lbfgs_c1 = 1e-4;
   o->cands_per_block = 0;
   o->use_graphs = 1;
+  o->de_f_lo = 0.5;
+  o->de_f_hi = 1.0;
+  o->de_cr = 0.7;
+  o->de_strategy = DEBYE_DE_RAND1;
 }
 
 int debye_fit_init(debye_handle* out, const debye_options* opt) {
@@ -392,6 +433,9 @@ int debye_fit_init(debye_handle* out, const debye_options* opt) {
   if (o.cands_per_block != 0 &&
       (o.cands_per_block < 32 || o.cands_per_block > MAX_BLOCK || o.cands_per_block % 32))
     return DEBYE_EINVAL;
+  if (!(o.de_f_lo >= 0.0) || !(o.de_f_hi >= o.de_f_lo) || !(o.de_f_hi <= 2.0)) return DEBYE_EINVAL;
+  if (!(o.de_cr >= 0.0) || !(o.de_cr <= 1.0)) return DEBYE_EINVAL;
+  if (o.de_strategy != DEBYE_DE_RAND1 && o.de_strategy != DEBYE_DE_BEST1) return DEBYE_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -406,7 +450,9 @@ int debye_fit_init(debye_handle* out, const debye_options* opt) {
       cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->work_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      !create_side_streams(h)) {
     cudaGetLastError();
     h->release();
     delete h;
@@ -467,6 +513,81 @@ int debye_sync(debye_handle h, cudaStream_t st) {
 }
 
 const char* debye_last_error(debye_handle h) { return h ? h->err.c_str() : "invalid handle"; }
+
+int debye_autotune(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n_max, const double* theta,
+                   double* cost, const char* cache_path, int32_t* chosen, cudaStream_t st) {
+  if (!h) return DEBYE_EINVAL;
+  h->err.clear();
+  if (!sp || !theta || !cost) return h->fail(DEBYE_EINVAL, "spectra, theta or cost is NULL");
+  char key[160];
+  int64_t nsamp = 0;
+  if (sp->offsets_host && sp->S > 0) nsamp = sp->offsets_host[sp->S];
+  snprintf(key, sizeof(key), "sms=%d prec=%d S=%lld P=%d nmax=%d samples=%lld", h->sms, h->opt.precision,
+           (long long)sp->S, P, n_max, (long long)nsamp);
+  if (cache_path) {  // "key | cb" lines
+    if (FILE* f = fopen(cache_path, "r")) {
+      char line[256];
+      while (fgets(line, sizeof(line), f)) {
+        char* bar = strchr(line, '|');
+        if (!bar) continue;
+        *bar = '\0';
+        std::string k(line);
+        while (!k.empty() && k.back() == ' ') k.pop_back();
+        if (k == key) {
+          const int cb = atoi(bar + 1);
+          if (cb >= 32 && cb <= MAX_BLOCK && cb % 32 == 0) {
+            h->tuned_cb = cb;
+            if (chosen) *chosen = cb;
+            fclose(f);
+            return DEBYE_OK;
+          }
+        }
+      }
+      fclose(f);
+    }
+  }
+  const int saved = h->opt.cands_per_block;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return h->fail(DEBYE_ECUDA, "event creation failed");
+  }
+  int best = 0;
+  float best_ms = 0.f;
+  int rc = DEBYE_OK;
+  for (int cb = 32; cb <= MAX_BLOCK && rc == DEBYE_OK; cb += 32) {
+    h->opt.cands_per_block = cb;
+    rc = debye_eval_population(h, sp, P, n_max, theta, cost, nullptr, st);   // warm-up
+    if (rc) break;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && rc == DEBYE_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      rc = debye_eval_population(h, sp, P, n_max, theta, cost, nullptr, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      ms += t;
+    }
+    if (rc == DEBYE_OK && (best == 0 || ms < best_ms)) {
+      best = cb;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->opt.cands_per_block = saved;
+  if (rc) return rc;
+  h->tuned_cb = best;
+  if (chosen) *chosen = best;
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "a")) {
+      fprintf(f, "%s | %d\n", key, best);
+      fclose(f);
+    }
+  }
+  return DEBYE_OK;
+}
 
 int debye_launch_count(debye_handle h, int64_t* count, int32_t reset) {
   if (!h) return DEBYE_EINVAL;

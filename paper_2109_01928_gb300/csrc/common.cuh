@@ -61,6 +61,7 @@ struct EvalArgs {
   const uint8_t* active;   // [Q] optional candidate mask (nullptr: all)
   int32_t ks;              // lanes per candidate in the pass kernels (power of two <= 32)
   int32_t zero_b;          // residual pass against b = 0 (t = -A^T A x), for the adjoint refinement
+  int32_t gs;              // Gram pass: 2 = each candidate's Gram rows split over two warps
   double lam;
   Scratch sc;
   int* status;             // device status word
@@ -186,12 +187,24 @@ __host__ __device__ __forceinline__ uint64_t rng_prefix(uint64_t seed, uint64_t 
   return splitmix64(h ^ g);
 }
 
-// Uniform double in [0, 1) for (prefix, particle, dim).
+// Full 64-bit key for (prefix, particle, dim).
+__host__ __device__ __forceinline__ uint64_t rng_key(uint64_t prefix, uint64_t p, uint64_t d) {
+  return splitmix64(splitmix64(prefix ^ p) ^ d);
+}
+
+// Uniform double in [0, 1) for (prefix, particle, dim): the key's upper 53 bits.
 __host__ __device__ __forceinline__ double rng_uniform(uint64_t prefix, uint64_t p, uint64_t d) {
-  uint64_t h = splitmix64(splitmix64(prefix ^ p) ^ d);
-  return (double)(h >> 11) * (1.0 / 9007199254740992.0);
+  return (double)(rng_key(prefix, p, d) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// Integer in [0, m), m < 2^32: multiply-shift of the key's upper 32 bits (Lemire 2019,
+// without rejection).
+__host__ __device__ __forceinline__ uint32_t rng_below(uint64_t key, uint32_t m) {
+  return (uint32_t)(((key >> 32) * (uint64_t)m) >> 32);
 }
 
 constexpr uint64_t TAG_INIT_POS = 1, TAG_INIT_VEL = 2, TAG_R1 = 3, TAG_R2 = 4;
+// differential evolution: donor indices, forced coordinate, crossover, bound re-draw, F
+constexpr uint64_t TAG_DE_IDX = 5, TAG_DE_J = 6, TAG_DE_CR = 7, TAG_DE_BOUND = 8, TAG_DE_F = 9;
 
 }  // namespace debyefit

@@ -79,9 +79,108 @@ __device__ __forceinline__ Lane lane_of(const EvalArgs& a, const Unit& u, bool n
   return l;
 }
 
+// ------------------------------------------------------------------ Gram, rows split over two warps
+// For large N one thread cannot hold the whole Gram: with a.gs = 2 the block has
+// 2 * cb threads, threads [0, cb) accumulate rows [0, R) of the pair triangle and
+// G_0j, threads [cb, 2 cb) rows [R, N) and h_j, both computing every basis
+// value (R balances the pair counts). ks = 1.
+__host__ __device__ constexpr int split_row(int N) {
+  int r = 0;
+  while (r * (r + 1) < N * (N + 1) / 2) ++r;
+  return r;
+}
+__host__ __device__ constexpr int split_part_floats(int N) {
+  return (N + split_row(N) * (split_row(N) + 1) / 2 > N + N * (N + 1) / 2 - split_row(N) * (split_row(N) + 1) / 2
+              ? N + split_row(N) * (split_row(N) + 1) / 2
+              : N + N * (N + 1) / 2 - split_row(N) * (split_row(N) + 1) / 2) | 1;
+}
+
+template <int N, int R0, int R1, bool FIRST>
+__device__ __forceinline__ void gram_rows(const EvalArgs& a, const Unit& u, int q, bool act) {
+  constexpr int P0 = R0 * (R0 + 1) / 2;
+  constexpr int NPR = R1 * (R1 + 1) / 2 - P0;
+  constexpr int SA = split_part_floats(N);
+  const double* th = a.theta + (int64_t)q * a.sc.nmax;
+  const int64_t Q = a.sc.Q;
+  float* outer = reinterpret_cast<float*>(dyn_smem) + threadIdx.x * SA;
+#pragma unroll
+  for (int e = 0; e < N + NPR; ++e) outer[e] = 0.f;
+  float tau[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) tau[i] = act ? __double2float_rn(exp10(th[i])) : 0.f;
+  const int64_t kend = act ? u.k1 : u.k0;
+  for (int64_t kb = u.k0; kb < kend; kb += GRAM_BLOCK) {
+    const int64_t ke = min(kend, kb + (int64_t)GRAM_BLOCK);
+    float gv[N], gp[NPR];   // gv: G_0j (first part) or h_j (second part)
+#pragma unroll
+    for (int i = 0; i < N; ++i) gv[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < NPR; ++i) gp[i] = 0.f;
+    float4 vn = __ldg(&a.kf32[kb]);
+#pragma unroll 1
+    for (int64_t k = kb; k < ke; ++k) {
+      const float4 v = vn;
+      if (k + 1 < kend) vn = __ldg(&a.kf32[k + 1]);
+      float re[N], im[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const float x = v.x * tau[i];
+        const float r = rcp_approx(fmaf(x, x, 1.0f));
+        re[i] = r;
+        im[i] = x * r;
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        if constexpr (FIRST) gv[i] += re[i];
+        else gv[i] = fmaf(re[i], v.y, fmaf(im[i], v.z, gv[i]));
+      }
+#pragma unroll
+      for (int i = R0; i < R1; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j)
+          gp[i * (i + 1) / 2 + j - P0] = fmaf(re[i], re[j], fmaf(im[i], im[j], gp[i * (i + 1) / 2 + j - P0]));
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) outer[i] += gv[i];
+#pragma unroll
+    for (int i = 0; i < NPR; ++i) outer[N + i] += gp[i];
+  }
+  if (!act) return;
+  double* G = a.sc.G;
+  const int hb = (a.sc.nmax + 1) * (a.sc.nmax + 2) / 2;
+  if constexpr (FIRST) {
+    G[(int64_t)pk(0, 0) * Q + q] = (double)(u.k1 - u.k0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) G[(int64_t)pk(i + 1, 0) * Q + q] = (double)outer[i];
+  } else {
+    G[(int64_t)hb * Q + q] = a.h0[u.s];
+#pragma unroll
+    for (int i = 0; i < N; ++i) G[(int64_t)(hb + 1 + i) * Q + q] = (double)outer[i];
+  }
+#pragma unroll
+  for (int i = R0; i < R1; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j)
+      G[(int64_t)pk(i + 1, j + 1) * Q + q] = (double)outer[N + i * (i + 1) / 2 + j - P0];
+}
+
 // ------------------------------------------------------------------ Gram
 template <int N, bool MIXED>
 __device__ __forceinline__ void gram_unit(const EvalArgs& a, const Unit& u) {
+  if constexpr (MIXED && N >= 13) {
+    if (a.gs == 2) {
+      const int cbg = (int)blockDim.x / 2;
+      const int part = (int)threadIdx.x / cbg;          // warp-uniform (cbg is a multiple of 32)
+      const int q0 = u.q0 + (int)threadIdx.x % cbg;
+      bool act = q0 < u.q1;
+      if (act && a.active) act = a.active[q0] != 0;
+      const int q = act ? q0 : u.q0;
+      constexpr int R = split_row(N);
+      if (part == 0) gram_rows<N, 0, R, true>(a, u, q, act);
+      else gram_rows<N, R, N, false>(a, u, q, act);
+      return;
+    }
+  }
   const Lane ln = lane_of(a, u, false);
   const int q = ln.act ? ln.q : u.q0;
   constexpr int NP = Acc<N>::NP;
@@ -244,7 +343,9 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
     // nearly collinear poles, and a flipped cost is first-order in the weights.
     // It also sums G_ii = ||a_i||^2 = sum_k re_i(k) (re^2 + im^2 = re for a Debye
     // column) in float-float: the damping lam G_ii x_i^2 then uses the exact
-    // column norms, not the FP32 Gram's diagonal.
+    // column norms, not the FP32 Gram's diagonal. The sum starts at 1 so that it
+    // always dominates the next term (re <= 1) and Fast2Sum (Dekker) is exact;
+    // the bias is removed in FP64 at the end.
     float th_[N], tl_[N], wh[N], wl[N], th_t[N], tl_t[N], gdh[N], gdl[N];
     float w0h = 0.f, w0l = 0.f;
     if (ln.act) split_double(X[q], w0h, w0l);
@@ -257,7 +358,7 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
       }
       th_t[i] = 0.f;
       tl_t[i] = 0.f;
-      gdh[i] = 0.f;
+      gdh[i] = 1.f;
       gdl[i] = 0.f;
     }
     float t0h = 0.f, t0l = 0.f, rrh = 0.f, rrl = 0.f;
@@ -271,9 +372,11 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
         vln = __ldg(&a.kff[k + step]);
       }
       float reh[N], rel[N], imh[N], iml[N];
-      // residual of the real row: eps' - eps_inf - sum x_i re_i
+      // residual of the real row: eps' - eps_inf - sum x_i re_i; each row is summed
+      // in two independent float-float chains (even / odd poles) merged at the end,
+      // halving the serial TwoSum dependency per sample
       const float byh = a.zero_b ? 0.f : vh.y, byl = a.zero_b ? 0.f : vl.y;
-      float arh, arl, aih, ail;
+      float arh, arl, aih, ail, brh = 0.f, brl = 0.f, bih = 0.f, bil = 0.f;
       two_sum(byh, -w0h, arh, arl);
       arl = __fadd_rn(arl, __fsub_rn(byl, w0l));
       aih = a.zero_b ? 0.f : vh.z;
@@ -282,8 +385,22 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
       for (int i = 0; i < N; ++i) {
         float xh;
         basis_ff(vh.x, vl.x, th_[i], tl_[i], reh[i], rel[i], imh[i], iml[i], xh);
-        ff_sub_prod(arh, arl, wh[i], wl[i], reh[i], rel[i]);
-        ff_sub_prod(aih, ail, wh[i], wl[i], imh[i], iml[i]);
+        if (i & 1) {
+          ff_sub_prod(brh, brl, wh[i], wl[i], reh[i], rel[i]);
+          ff_sub_prod(bih, bil, wh[i], wl[i], imh[i], iml[i]);
+        } else {
+          ff_sub_prod(arh, arl, wh[i], wl[i], reh[i], rel[i]);
+          ff_sub_prod(aih, ail, wh[i], wl[i], imh[i], iml[i]);
+        }
+      }
+      if (N > 1) {
+        float s, e;
+        two_sum(arh, brh, s, e);
+        arh = s;
+        arl = __fadd_rn(arl, __fadd_rn(brl, e));
+        two_sum(aih, bih, s, e);
+        aih = s;
+        ail = __fadd_rn(ail, __fadd_rn(bil, e));
       }
       ff_norm(arh, arl);
       ff_norm(aih, ail);
@@ -295,8 +412,9 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
       for (int i = 0; i < N; ++i) {
         ff_add_prod(th_t[i], tl_t[i], reh[i], rel[i], arh, arl);
         ff_add_prod(th_t[i], tl_t[i], imh[i], iml[i], aih, ail);
-        ff_add(gdh[i], gdl[i], reh[i]);
-        gdl[i] = __fadd_rn(gdl[i], rel[i]);
+        const float gs = __fadd_rn(gdh[i], reh[i]);                 // Fast2Sum, gdh >= 1 >= reh
+        gdl[i] = __fadd_rn(gdl[i], __fadd_rn(__fsub_rn(reh[i], __fsub_rn(gs, gdh[i])), rel[i]));
+        gdh[i] = gs;
       }
     }
     group_sum_ff(rrh, rrl, ln.ks);
@@ -313,7 +431,7 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         R[(int64_t)(i + 2) * Q + q] = (double)th_t[i] + (double)tl_t[i];
-        a.sc.G[(int64_t)pk(i + 1, i + 1) * Q + q] = (double)gdh[i] + (double)gdl[i];
+        a.sc.G[(int64_t)pk(i + 1, i + 1) * Q + q] = ((double)gdh[i] - (double)ln.ks) + (double)gdl[i];
       }
     }
   } else {
@@ -562,13 +680,11 @@ __device__ __forceinline__ void dispatch_n(const EvalArgs& a, const Unit& u) {
 }
 
 // One block per unit (grid-stride over the unit list); LO..HI is the pole
-// bucket compiled into this kernel. At most MAX_BLOCK_THREADS threads per block;
-// MINB resident blocks of that size bound the registers per thread (MINB = 3:
-// 168 registers, 12 warps per SM with 64-thread blocks).
-constexpr int MAX_BLOCK_THREADS = 128;
-
-template <int PH, int LO, int HI, bool MIXED, int MINB>
-__global__ void __launch_bounds__(MAX_BLOCK_THREADS, MINB) k_pass(EvalArgs a) {
+// bucket compiled into this kernel. At most MAXT threads per block; MINB
+// resident blocks of that size bound the registers per thread (128 x 3: 168
+// registers, 12 warps per SM with 64-thread blocks).
+template <int PH, int LO, int HI, bool MIXED, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_pass(EvalArgs a) {
   for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
     const Unit u = a.units[ui];
     if (u.N < LO || u.N > HI) {

@@ -1,4 +1,5 @@
-// debye_fit_batch: seeded swarm + polish + final re-solve (host orchestration).
+// debye_fit_batch: seeded swarm or differential evolution + polish + final
+// re-solve (host orchestration).
 //
 // The work runs on the handle's own non-blocking stream, joined to the
 // caller's stream by events, so that the generation loop and the polish loop can
@@ -71,8 +72,9 @@ static int repeat(debye_ctx* h, int times, cudaStream_t st, F body) {
   return DEBYE_OK;
 }
 
-static int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, int32_t n_max,
-                    double* eps_inf, double* d_eps, double* tau, double* final_cost, cudaStream_t st) {
+int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, int32_t n_max,
+             double* eps_inf, double* d_eps, double* tau, double* final_cost, cudaStream_t st,
+             const int64_t* rng_id, bool reset_evals) {
   int rc;
   Plan pl;
   if ((rc = h->load_plan(sp, pl, st))) return rc;
@@ -83,7 +85,7 @@ static int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search*
   if (Q > ((int64_t)1 << 31) - 1) return h->fail(DEBYE_EINVAL, "S*P exceeds 2^31-1");
   if ((rc = h->prep_spectra(sp, pl, st))) return rc;
   int cb, ks;
-  choose_layout(P, h->opt.cands_per_block, &cb, &ks);
+  choose_layout(P, h->cb_option(), &cb, &ks);
   const bool mixed = h->opt.precision == DEBYE_PREC_MIXED;
   const int nmax = n_max;
 
@@ -108,10 +110,16 @@ static int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search*
   sa.omega = h->opt.pso_omega;
   sa.phi_p = h->opt.pso_phi_p;
   sa.phi_g = h->opt.pso_phi_g;
+  sa.de_f_lo = h->opt.de_f_lo;
+  sa.de_f_hi = h->opt.de_f_hi;
+  sa.de_cr = h->opt.de_cr;
+  sa.de_strategy = h->opt.de_strategy;
+  const bool evolve = se->method == DEBYE_SEARCH_DE;
   sa.n_poles = sp->n_poles;
   sa.lo = sp->lo;
   sa.hi = sp->hi;
   sa.offsets = sp->offsets;
+  sa.rng_id = rng_id;
   const size_t qn = sizeof(double) * (size_t)Q * nmax;
   if ((rc = h->named("swarm.x", qn, &p))) return rc;
   sa.x = (double*)p;
@@ -129,7 +137,7 @@ static int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search*
   sa.gen = (int*)p;
   sa.trace = se->trace;
   sa.evals = se->evals;
-  if (se->evals) cudaMemsetAsync(se->evals, 0, sizeof(double), st);
+  if (se->evals && reset_evals) cudaMemsetAsync(se->evals, 0, sizeof(double), st);
   cudaMemsetAsync(sa.gen, 0, sizeof(int), st);
 
   ea.units = (const Unit*)h->ws_units.p;
@@ -145,14 +153,16 @@ static int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search*
   ea.status = h->d_status;
   const int steps = h->opt.refine_steps;
 
-  // generation 0: initial positions, evaluation, bests
+  // generation 0: initial positions (the same for both methods), evaluation, bests
   launch_pso_init(sa, h->sms, st); ++h->launches;
   if ((rc = h->run_eval(ea, g, mixed, steps, cost, nullptr, nullptr, h->sb_eval.g1, cb, st))) return rc;
   launch_pso_best(sa, cost, h->sms, st); ++h->launches;
   launch_gen_advance(sa.gen, st); ++h->launches;
   if ((rc = h->check_launch("swarm start"))) return rc;
   rc = repeat(h, se->iters, st, [&]() -> int {
-    launch_pso_move(sa, h->sms, st); ++h->launches;
+    if (evolve) launch_de_trial(sa, h->sms, st);
+    else launch_pso_move(sa, h->sms, st);
+    ++h->launches;
     int r = h->run_eval(ea, g, mixed, steps, cost, nullptr, nullptr, h->sb_eval.g1, cb, st);
     if (r) return r;
     launch_pso_best(sa, cost, h->sms, st); ++h->launches;
@@ -216,8 +226,8 @@ static int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search*
       ae[s] = (int32_t)((s + 1) * T);
     }
     int cbp, ksp, cba, ksa;
-    choose_layout((int64_t)T * pa.R, h->opt.cands_per_block, &cbp, &ksp);
-    choose_layout(T, h->opt.cands_per_block, &cba, &ksa);
+    choose_layout((int64_t)T * pa.R, h->cb_option(), &cbp, &ksp);
+    choose_layout(T, h->cb_option(), &cba, &ksa);
     UnitGroups gp, ga;
     build_units(pl, pb, pe, cbp, gp);
     build_units(pl, ab, ae, cba, ga);
@@ -308,6 +318,12 @@ extern "C" int debye_fit_batch(debye_handle h, const debye_spectra* sp, const de
   if (!sp || !se) return h->fail(DEBYE_EINVAL, "spectra or search is NULL");
   if (se->P < 1 || se->P > 32768) return h->fail(DEBYE_EINVAL, "P = %d outside 1..32768", se->P);
   if (se->iters < 0) return h->fail(DEBYE_EINVAL, "iters < 0");
+  if (se->method != DEBYE_SEARCH_PSO && se->method != DEBYE_SEARCH_DE)
+    return h->fail(DEBYE_EINVAL, "method must be DEBYE_SEARCH_PSO or DEBYE_SEARCH_DE");
+  if (se->method == DEBYE_SEARCH_DE && se->iters > 0 &&
+      se->P < (h->opt.de_strategy == DEBYE_DE_RAND1 ? 4 : 3))
+    return h->fail(DEBYE_EINVAL, "differential evolution needs P >= %d",
+                   h->opt.de_strategy == DEBYE_DE_RAND1 ? 4 : 3);
   if (se->polish_topk < 0 || se->polish_topk > 64) return h->fail(DEBYE_EINVAL, "polish_topk outside 0..64");
   if (se->polish_iters < 0) return h->fail(DEBYE_EINVAL, "polish_iters < 0");
   if (n_max < 1 || n_max > NMAX) return h->fail(DEBYE_EINVAL, "n_max = %d outside 1..%d", n_max, NMAX);
@@ -315,7 +331,7 @@ extern "C" int debye_fit_batch(debye_handle h, const debye_spectra* sp, const de
   cudaStream_t ws = h->work_stream;
   cudaEventRecord(h->ev_in, st);
   cudaStreamWaitEvent(ws, h->ev_in, 0);
-  int rc = fit_impl(h, sp, se, n_max, eps_inf, d_eps, tau, final_cost, ws);
+  int rc = fit_impl(h, sp, se, n_max, eps_inf, d_eps, tau, final_cost, ws, nullptr, true);
   cudaEventRecord(h->ev_out, ws);
   cudaStreamWaitEvent(st, h->ev_out, 0);
   return rc;

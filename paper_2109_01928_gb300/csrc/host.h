@@ -40,6 +40,17 @@ void build_units(const Plan& pl, const std::vector<int32_t>& qb, const std::vect
 
 }  // namespace debyefit
 
+// Whole fit of a batch on stream st (the body of debye_fit_batch). rng_id [S]
+// (device, or nullptr) replaces the batch index in the generator's keys;
+// reset_evals zeroes se->evals first.
+int fit_impl(struct debye_ctx* h, const debye_spectra* sp, const debye_search* se, int32_t n_max,
+             double* eps_inf, double* d_eps, double* tau, double* final_cost, cudaStream_t st,
+             const int64_t* rng_id, bool reset_evals);
+
+namespace debyefit {
+
+}  // namespace debyefit
+
 struct debye_ctx {
   debye_options opt{};
   int device = 0;
@@ -52,6 +63,10 @@ struct debye_ctx {
 
   cudaStream_t work_stream = nullptr;  // non-blocking stream of debye_fit_batch
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // Pole buckets of one pass run concurrently: bucket b > first on side[b], forked
+  // from and joined back to the launching stream (so their tails overlap).
+  cudaStream_t side[debyefit::N_BUCKETS] = {nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[debyefit::N_BUCKETS] = {nullptr};
 
   debyefit::Buf ws_kf32, ws_kff, ws_h0, ws_units;
   debyefit::ScratchBufs sb_eval, sb_polish, sb_polish_acc, sb_final;
@@ -64,6 +79,7 @@ struct debye_ctx {
     cudaEvent_t a, b;
   };
   int64_t launches = 0;  // kernel launches enqueued (graph replays count every node)
+  int tuned_cb = 0;      // candidates per block chosen by debye_autotune (0: not tuned)
   bool prof_on = false;
   std::vector<ProfEntry> prof_pending;
   std::vector<cudaEvent_t> prof_pool;
@@ -85,6 +101,7 @@ struct debye_ctx {
   int run_eval(debyefit::EvalArgs a, const debyefit::UnitGroups& g, bool mixed, int steps,
                double* cost, double* weights, double* grad, double* g1, int cb, cudaStream_t st);
   int eval_steps(bool with_grad) const;
+  int cb_option() const { return opt.cands_per_block > 0 ? opt.cands_per_block : tuned_cb; }
   int named(const char* name, size_t bytes, void** out);
 
   void free_buf(debyefit::Buf& b) {
@@ -113,6 +130,14 @@ struct debye_ctx {
     prof_pool.clear();
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    ev_fork = nullptr;
+    for (int b = 0; b < debyefit::N_BUCKETS; ++b) {
+      if (ev_join[b]) cudaEventDestroy(ev_join[b]);
+      if (side[b]) cudaStreamDestroy(side[b]);
+      ev_join[b] = nullptr;
+      side[b] = nullptr;
+    }
     if (work_stream) cudaStreamDestroy(work_stream);
     ev_in = ev_out = nullptr;
     work_stream = nullptr;

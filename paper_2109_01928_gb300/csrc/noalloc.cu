@@ -215,6 +215,7 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
       ab.units = a.units + begin[b];
       ab.n_units = n;
       const int grid = std::max(1, std::min(n, sms * 16));
+      ab.gs = 1;
       switch (b) {
         case 0: launch_pass_b0(phase, mixed, ab, grid, cb * ks, st); break;
         case 1: launch_pass_b1(phase, mixed, ab, grid, cb * ks, st); break;

@@ -1,5 +1,6 @@
-// Search kernels of libdebyefit: particle swarm (Sec. III-A, III-B), top-k
-// selection, projected L-BFGS polish, final re-solve and result assembly.
+// Search kernels of libdebyefit: particle swarm and differential evolution
+// (Sec. III-B), top-k selection, projected L-BFGS polish, final re-solve and
+// result assembly.
 //
 // Swarm update order matches the reference arithmetic exactly: explicit
 // __d*_rn operations (no FMA contraction) so that positions are bit-identical
@@ -12,6 +13,11 @@
 
 namespace debyefit {
 
+// Spectrum field of the generator's key: the caller's index map, else the batch index.
+__device__ __forceinline__ uint64_t key_id(const SwarmArgs& a, int64_t s) {
+  return a.rng_id ? (uint64_t)a.rng_id[s] : (uint64_t)s;
+}
+
 __global__ void k_pso_init(SwarmArgs a) {
   const int64_t Q = (int64_t)a.S * a.P;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q;
@@ -19,8 +25,8 @@ __global__ void k_pso_init(SwarmArgs a) {
     const int64_t s = q / a.P, p = q % a.P;
     const int N = a.n_poles[s];
     const double lo = a.lo[s], hi = a.hi[s], span = __dsub_rn(hi, lo);
-    const uint64_t pp = rng_prefix(a.seed, TAG_INIT_POS, (uint64_t)s, 0);
-    const uint64_t pv = rng_prefix(a.seed, TAG_INIT_VEL, (uint64_t)s, 0);
+    const uint64_t pp = rng_prefix(a.seed, TAG_INIT_POS, key_id(a, s), 0);
+    const uint64_t pv = rng_prefix(a.seed, TAG_INIT_VEL, key_id(a, s), 0);
     for (int d = 0; d < a.nmax; ++d) {
       double x = 0.0, v = 0.0;
       if (d < N) {
@@ -42,8 +48,8 @@ __global__ void k_pso_move(SwarmArgs a) {
     const int N = a.n_poles[s];
     const double lo = a.lo[s], hi = a.hi[s];
     const int64_t gq = s * a.P + a.gbest[s];
-    const uint64_t p1 = rng_prefix(a.seed, TAG_R1, (uint64_t)s, (uint64_t)gen);
-    const uint64_t p2 = rng_prefix(a.seed, TAG_R2, (uint64_t)s, (uint64_t)gen);
+    const uint64_t p1 = rng_prefix(a.seed, TAG_R1, key_id(a, s), (uint64_t)gen);
+    const uint64_t p2 = rng_prefix(a.seed, TAG_R2, key_id(a, s), (uint64_t)gen);
     for (int d = 0; d < N; ++d) {
       const double x = a.x[q * a.nmax + d], v = a.v[q * a.nmax + d];
       const double pb = a.pbx[q * a.nmax + d], gb = a.pbx[gq * a.nmax + d];
@@ -54,6 +60,62 @@ __global__ void k_pso_move(SwarmArgs a) {
       const double vn = __dadd_rn(__dadd_rn(t1, t2), t3);
       a.v[q * a.nmax + d] = vn;
       a.x[q * a.nmax + d] = fmin(fmax(__dadd_rn(x, vn), lo), hi);
+    }
+  }
+}
+
+// Differential evolution (Storn and Price): one trial vector per population member.
+// The population lives in pbx/pbc (k_pso_best's strictly-lower replacement is
+// the evolution's selection), the trials are written to x for evaluation.
+//   donors: slot j draws r below P-1-j and takes the r-th free index (ascending),
+//           free = not the target and not an earlier slot;
+//   mutant: rand/1  x_r0 + F (x_r1 - x_r2)   best/1  x_best + F (x_r0 - x_r1),
+//           F = f_lo + (f_hi - f_lo) u once per generation;
+//   a mutant coordinate outside [lo, hi] is re-drawn uniformly in the box;
+//   binomial crossover: coordinate d from the mutant if u_d < CR or d = j_rand.
+// Explicit __d*_rn operations keep the trials bit-identical to an FP64
+// implementation evaluating the same expressions.
+__global__ void k_de_trial(SwarmArgs a) {
+  const int64_t Q = (int64_t)a.S * a.P;
+  const int gen = *a.gen;
+  const int k = a.de_strategy == DEBYE_DE_RAND1 ? 3 : 2;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = q / a.P;
+    const int p = (int)(q % a.P);
+    const int N = a.n_poles[s];
+    const double lo = a.lo[s], hi = a.hi[s], span = __dsub_rn(hi, lo);
+    const uint64_t pidx = rng_prefix(a.seed, TAG_DE_IDX, key_id(a, s), (uint64_t)gen);
+    const uint64_t pj = rng_prefix(a.seed, TAG_DE_J, key_id(a, s), (uint64_t)gen);
+    const uint64_t pcr = rng_prefix(a.seed, TAG_DE_CR, key_id(a, s), (uint64_t)gen);
+    const uint64_t pb = rng_prefix(a.seed, TAG_DE_BOUND, key_id(a, s), (uint64_t)gen);
+    const double uf = rng_uniform(rng_prefix(a.seed, TAG_DE_F, key_id(a, s), (uint64_t)gen), 0, 0);
+    const double F = __dadd_rn(a.de_f_lo, __dmul_rn(__dsub_rn(a.de_f_hi, a.de_f_lo), uf));
+    int taken[4];  // sorted ascending
+    int r[3] = {0, 0, 0};
+    taken[0] = p;
+    int nt = 1;
+    for (int j = 0; j < k; ++j) {
+      int v = (int)rng_below(rng_key(pidx, (uint64_t)p, (uint64_t)j), (uint32_t)(a.P - 1 - j));
+      for (int t = 0; t < nt; ++t) v += (v >= taken[t]) ? 1 : 0;
+      r[j] = v;
+      int t = nt++;
+      while (t > 0 && taken[t - 1] > v) {
+        taken[t] = taken[t - 1];
+        --t;
+      }
+      taken[t] = v;
+    }
+    const int64_t base = s * a.P + (k == 3 ? r[0] : a.gbest[s]);
+    const int64_t d1 = s * a.P + (k == 3 ? r[1] : r[0]);
+    const int64_t d2 = s * a.P + (k == 3 ? r[2] : r[1]);
+    const int jr = (int)rng_below(rng_key(pj, (uint64_t)p, 0), (uint32_t)N);
+    for (int d = 0; d < N; ++d) {
+      double v = __dadd_rn(a.pbx[base * a.nmax + d],
+                           __dmul_rn(F, __dsub_rn(a.pbx[d1 * a.nmax + d], a.pbx[d2 * a.nmax + d])));
+      if (v < lo || v > hi) v = __dadd_rn(lo, __dmul_rn(span, rng_uniform(pb, (uint64_t)p, (uint64_t)d)));
+      const bool take = rng_uniform(pcr, (uint64_t)p, (uint64_t)d) < a.de_cr || d == jr;
+      a.x[q * a.nmax + d] = take ? v : a.pbx[q * a.nmax + d];
     }
   }
 }
@@ -397,6 +459,9 @@ void launch_pso_init(const SwarmArgs& a, int sms, cudaStream_t st) {
 }
 void launch_pso_move(const SwarmArgs& a, int sms, cudaStream_t st) {
   k_pso_move<<<g1d((int64_t)a.S * a.P, sms), 256, 0, st>>>(a);
+}
+void launch_de_trial(const SwarmArgs& a, int sms, cudaStream_t st) {
+  k_de_trial<<<g1d((int64_t)a.S * a.P, sms), 256, 0, st>>>(a);
 }
 void launch_pso_best(const SwarmArgs& a, const double* cost, int sms, cudaStream_t st) {
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.S, (int64_t)sms * 8));

@@ -9,14 +9,17 @@ struct SwarmArgs {
   int32_t P, nmax, iters;
   uint64_t seed;
   double omega, phi_p, phi_g;
+  double de_f_lo, de_f_hi, de_cr;  // differential evolution coefficients
+  int32_t de_strategy;             // DEBYE_DE_RAND1 or DEBYE_DE_BEST1
   const int32_t* n_poles;
   const double* lo;
   const double* hi;
   const int64_t* offsets;
-  double* x;       // [S*P][nmax] positions (log10 tau)
-  double* v;       // [S*P][nmax] velocities
-  double* pbx;     // [S*P][nmax] personal-best positions
-  double* pbc;     // [S*P]       personal-best costs
+  const int64_t* rng_id;  // [S] spectrum index used in the generator's keys, or nullptr (= s)
+  double* x;       // [S*P][nmax] positions (log10 tau); differential evolution: trial vectors
+  double* v;       // [S*P][nmax] velocities (swarm only)
+  double* pbx;     // [S*P][nmax] personal-best positions; differential evolution: the population
+  double* pbc;     // [S*P]       personal-best costs; differential evolution: population costs
   int32_t* gbest;  // [S]         global-best particle
   int* gen;        // generation counter (device)
   double* trace;   // [S][iters+1] or nullptr
@@ -52,6 +55,7 @@ struct PolishArgs {
 
 void launch_pso_init(const SwarmArgs& a, int sms, cudaStream_t st);
 void launch_pso_move(const SwarmArgs& a, int sms, cudaStream_t st);
+void launch_de_trial(const SwarmArgs& a, int sms, cudaStream_t st);
 void launch_pso_best(const SwarmArgs& a, const double* cost, int sms, cudaStream_t st);
 void launch_gen_advance(int* gen, cudaStream_t st);
 void launch_add_scalar(double* dst, double v, cudaStream_t st);

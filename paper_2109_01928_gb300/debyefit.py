@@ -27,6 +27,10 @@ DEBYE_ENOTFINITE = -6
 DEBYE_EBOUNDS = -7
 PREC_FP64 = 0
 PREC_MIXED = 1
+SEARCH_PSO = 0
+SEARCH_DE = 1
+DE_RAND1 = 0
+DE_BEST1 = 1
 MAX_POLES = 20
 N_PARAMS = 16
 
@@ -43,7 +47,9 @@ class Options(ctypes.Structure):
                 ("pso_omega", ctypes.c_double), ("pso_phi_p", ctypes.c_double),
                 ("pso_phi_g", ctypes.c_double), ("lbfgs_m", ctypes.c_int32),
                 ("lbfgs_max_trials", ctypes.c_int32), ("lbfgs_c1", ctypes.c_double),
-                ("cands_per_block", ctypes.c_int32), ("use_graphs", ctypes.c_int32)]
+                ("cands_per_block", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
+                ("de_f_lo", ctypes.c_double), ("de_f_hi", ctypes.c_double), ("de_cr", ctypes.c_double),
+                ("de_strategy", ctypes.c_int32)]
 
 
 class SpectraC(ctypes.Structure):
@@ -56,7 +62,7 @@ class SpectraC(ctypes.Structure):
 class SearchC(ctypes.Structure):
     _fields_ = [("P", ctypes.c_int32), ("iters", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("polish_topk", ctypes.c_int32), ("polish_iters", ctypes.c_int32),
-                ("trace", ctypes.c_void_p), ("evals", ctypes.c_void_p)]
+                ("trace", ctypes.c_void_p), ("evals", ctypes.c_void_p), ("method", ctypes.c_int32)]
 
 
 _lib = None
@@ -83,12 +89,16 @@ def lib() -> ctypes.CDLL:
                                   _VP, _VP, _VP, _VP]
     L.debye_fit_batch.argtypes = [_VP, ctypes.POINTER(SpectraC), ctypes.POINTER(SearchC), ctypes.c_int32,
                                   _VP, _VP, _VP, _VP, _VP]
+    L.debye_fit_auto.argtypes = [_VP, ctypes.POINTER(SpectraC), ctypes.POINTER(SearchC), ctypes.c_int32,
+                                 ctypes.c_double, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP]
     L.debye_sync.argtypes = [_VP, _VP]
     L.debye_last_error.argtypes = [_VP]
     L.debye_last_error.restype = ctypes.c_char_p
     L.debye_version.restype = ctypes.c_char_p
     L.debye_profile_enable.argtypes = [_VP, ctypes.c_int32]
     L.debye_launch_count.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]
+    L.debye_autotune.argtypes = [_VP, ctypes.POINTER(SpectraC), ctypes.c_int32, ctypes.c_int32, _VP, _VP,
+                                 ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32), _VP]
     L.debye_eval_population_noalloc.argtypes = [ctypes.POINTER(Options), ctypes.POINTER(SpectraC),
                                                 ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP,
                                                 ctypes.c_char_p, ctypes.c_int32, _VP]
@@ -96,7 +106,7 @@ def lib() -> ctypes.CDLL:
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     for f in ("debye_fit_init", "debye_fit_destroy", "debye_synth_targets", "debye_eval_population",
               "debye_cost_grad", "debye_fit_batch", "debye_sync", "debye_profile_enable",
-              "debye_profile_read", "debye_launch_count", "debye_eval_population_noalloc"):
+              "debye_profile_read", "debye_launch_count", "debye_autotune", "debye_eval_population_noalloc"):
         getattr(L, f).restype = _I
     _lib = L
     return L
@@ -252,9 +262,10 @@ def debye_cost_grad(h: Handle, sp: Spectra, theta, cost=None, grad=None, stream=
 
 def debye_fit_batch(h: Handle, sp: Spectra, P: int, iters: int, seed: int = 0, polish_topk: int = 8,
                     polish_iters: int = 50, n_max: int | None = None, trace: bool = False, stream=None,
-                    out=None):
+                    out=None, method: str = "pso"):
     """Whole fit of every spectrum: dict of eps_inf [S], d_eps [S, n_max], tau [S, n_max],
-    final_cost [S], evals (candidate evaluations x K) and optionally trace [S, iters+1]."""
+    final_cost [S], evals (candidate evaluations x K) and optionally trace [S, iters+1].
+    method: "pso" (particle swarm) or "de" (differential evolution)."""
     import torch
     dev = sp.omega.device
     n_max = sp.n_max if n_max is None else n_max
@@ -267,11 +278,36 @@ def debye_fit_batch(h: Handle, sp: Spectra, P: int, iters: int, seed: int = 0, p
                "evals": torch.zeros(1, dtype=torch.float64, device=dev)}
         if trace:
             out["trace"] = torch.empty((S, iters + 1), dtype=torch.float64, device=dev)
-    srch = SearchC(P, iters, seed, polish_topk, polish_iters, _ptr(out.get("trace")), _ptr(out["evals"]))
+    srch = SearchC(P, iters, seed, polish_topk, polish_iters, _ptr(out.get("trace")), _ptr(out["evals"]),
+                   {"pso": SEARCH_PSO, "de": SEARCH_DE}[method])
     c = sp.c()
     h.check(lib().debye_fit_batch(h.ptr, ctypes.byref(c), ctypes.byref(srch), n_max, _ptr(out["eps_inf"]),
                                   _ptr(out["d_eps"]), _ptr(out["tau"]), _ptr(out["final_cost"]),
                                   _stream(stream)))
+    return out
+
+
+def debye_fit_auto(h: Handle, sp: Spectra, P: int, iters: int, seed: int = 0, polish_topk: int = 8,
+                   polish_iters: int = 50, n_max: int | None = None, threshold: float = 5.0, wave: int = 4,
+                   method: str = "pso", stream=None):
+    """Automatic pole count: sp.n_poles is each spectrum's cap; returns the dict of
+    debye_fit_batch plus frac_err [S] (percent) and n_chosen [S] (int32)."""
+    import torch
+    dev = sp.omega.device
+    n_max = sp.n_max if n_max is None else n_max
+    S = sp.S
+    f64 = dict(dtype=torch.float64, device=dev)
+    out = {"eps_inf": torch.empty(S, **f64), "d_eps": torch.empty((S, n_max), **f64),
+           "tau": torch.empty((S, n_max), **f64), "final_cost": torch.empty(S, **f64),
+           "frac_err": torch.empty(S, **f64), "n_chosen": torch.empty(S, dtype=torch.int32, device=dev),
+           "evals": torch.zeros(1, **f64)}
+    srch = SearchC(P, iters, seed, polish_topk, polish_iters, None, _ptr(out["evals"]),
+                   {"pso": SEARCH_PSO, "de": SEARCH_DE}[method])
+    c = sp.c()
+    h.check(lib().debye_fit_auto(h.ptr, ctypes.byref(c), ctypes.byref(srch), n_max, float(threshold), wave,
+                                 _ptr(out["eps_inf"]), _ptr(out["d_eps"]), _ptr(out["tau"]),
+                                 _ptr(out["final_cost"]), _ptr(out["frac_err"]), _ptr(out["n_chosen"]),
+                                 _stream(stream)))
     return out
 
 
@@ -304,6 +340,19 @@ def debye_eval_population_noalloc(sp: Spectra, theta, precision: str = "mixed", 
     if rc != DEBYE_OK:
         raise DebyeError(rc, buf.value.decode())
     return (cost, weights_out) if weights else cost
+
+
+def debye_autotune(h: Handle, sp: Spectra, theta, cache_path: str | None = None, stream=None) -> int:
+    """Time the candidates-per-block choices on this batch and keep the fastest for h."""
+    import torch
+    S, P, nm = theta.shape
+    cost = torch.empty((S, P), dtype=torch.float64, device=theta.device)
+    chosen = ctypes.c_int32(0)
+    c = sp.c()
+    h.check(lib().debye_autotune(h.ptr, ctypes.byref(c), P, nm, _ptr(theta), _ptr(cost),
+                                 cache_path.encode() if cache_path else None, ctypes.byref(chosen),
+                                 _stream(stream)))
+    return chosen.value
 
 
 def debye_launch_count(h: Handle, reset: bool = False) -> int:

@@ -34,6 +34,7 @@ def test_default_options(lib):
     assert o.lam_search == 1e-3 and o.lam_final == 1e-3
     assert (o.pso_omega, o.pso_phi_p, o.pso_phi_g) == (0.5, 0.5, 0.5)
     assert o.lbfgs_m == 8 and o.lbfgs_max_trials == 20 and o.lbfgs_c1 == 1e-4
+    assert (o.de_f_lo, o.de_f_hi, o.de_cr, o.de_strategy) == (0.5, 1.0, 0.7, D.DE_RAND1)
 
 
 def test_init_rejects_bad_options(lib):
@@ -44,6 +45,10 @@ def test_init_rejects_bad_options(lib):
     o = D.default_options()
     o.cands_per_block = 48
     assert lib.debye_fit_init(ctypes.byref(h), ctypes.byref(o)) == D.DEBYE_EINVAL
+    for field, bad in (("de_cr", 1.5), ("de_f_lo", -0.1), ("de_f_hi", 0.25), ("de_strategy", 2)):
+        o = D.default_options()
+        setattr(o, field, bad)
+        assert lib.debye_fit_init(ctypes.byref(h), ctypes.byref(o)) == D.DEBYE_EINVAL
     assert not h.value
 
 
@@ -66,6 +71,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(debye_options, lam_search), offsetof(debye_options, lbfgs_c1),
          offsetof(debye_options, use_graphs), offsetof(debye_search, trace));
   printf("%zu\n", offsetof(debye_spectra, n_poles_host));
+  printf("%zu %zu %zu\n", offsetof(debye_options, de_f_lo), offsetof(debye_options, de_strategy),
+         offsetof(debye_search, method));
   return 0;
 }
 ''')
@@ -85,3 +92,6 @@ int main(void) {
     assert vals[5] == D.Options.use_graphs.offset
     assert vals[6] == D.SearchC.trace.offset
     assert vals[7] == D.SpectraC.n_poles_host.offset
+    assert vals[8] == D.Options.de_f_lo.offset
+    assert vals[9] == D.Options.de_strategy.offset
+    assert vals[10] == D.SearchC.method.offset
