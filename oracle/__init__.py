@@ -15,6 +15,8 @@ Modules
   rng     SplitMix64 counter-based random numbers
   pso     particle-swarm search over log10(tau) (Sec. III-A, Kennedy-Eberhart)
   de      differential evolution over log10(tau) (Sec. III-B, Storn-Price)
+  da      dual annealing over log10(tau) (Sec. III-B, Tsallis-Stariolo)
+  dmath   log, exp and normal deviates as fixed sequences of IEEE operations
   lbfgs   projected L-BFGS polish
   fit     the whole fit of one spectrum and the reported result (Listing 2)
 

@@ -13,16 +13,17 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import de, dls, lbfgs, pso, varpro
+from . import da, de, dls, lbfgs, pso, varpro
 
 
 def fit_spectrum(omega, eps_re, eps_im, N: int, lo: float, hi: float, P: int, iters: int,
                  seed: int = 0, spectrum: int = 0, topk: int = 8, polish_iters: int = 50,
                  lam_search: float = dls.LAM_SEARCH, lam_final: float = dls.LAM_FINAL,
                  method: str = "pso", de_opts: dict | None = None):
-    """method "pso" (particle swarm) or "de" (differential evolution, keyword
-    arguments of de.de in de_opts); the polish starts from the best personal
-    bests (swarm) or population members (evolution)."""
+    """method "pso" (particle swarm), "de" (differential evolution) or "da" (dual
+    annealing); keyword arguments of de.de / da.da in de_opts; the polish starts
+    from the best personal bests (swarm), population members (evolution) or chain
+    states (annealing)."""
     def cost_fn(th):
         return dls.cost_population(omega, eps_re, eps_im, th, lam_search)[0]
 
@@ -30,11 +31,13 @@ def fit_spectrum(omega, eps_re, eps_im, N: int, lo: float, hi: float, P: int, it
         pbx, pbc, gi, trace = pso.pso(cost_fn, N, lo, hi, P, iters, seed, spectrum)
     elif method == "de":
         pbx, pbc, gi, trace = de.de(cost_fn, N, lo, hi, P, iters, seed, spectrum, **(de_opts or {}))
+    elif method == "da":
+        pbx, pbc, gi, trace = da.da(cost_fn, N, lo, hi, P, iters, seed, spectrum, **(de_opts or {}))
     else:
-        raise ValueError("method must be 'pso' or 'de'")
+        raise ValueError("method must be 'pso', 'de' or 'da'")
     order = np.argsort(pbc, kind="stable")
     best_th, best_c = pbx[gi].copy(), float(pbc[gi])
-    n_evals = P * (iters + 1)
+    n_evals = P * (iters * 2 * N + 1) if method == "da" else P * (iters + 1)
     polished = []
     for rank in range(min(topk, P)):
         th0 = pbx[order[rank]]

@@ -32,6 +32,8 @@ TAG_DE_J = 6       # the coordinate always taken from the mutant
 TAG_DE_CR = 7      # binomial crossover draws
 TAG_DE_BOUND = 8   # re-draw of a mutant coordinate outside the bounds
 TAG_DE_F = 9       # per-generation scale factor (dither)
+TAG_DA_VISIT = 10  # dual annealing: uniforms of the visiting deviates
+TAG_DA_ACCEPT = 11 # dual annealing: acceptance draws
 
 
 def mix(z: int) -> int:
@@ -81,6 +83,18 @@ def key_array(seed: int, tag: int, spectrum: int, generation: int, P: int, N: in
     h = mix(h ^ (generation & MASK))
     hp = mix_array(np.uint64(h) ^ np.arange(P, dtype=np.uint64))
     return mix_array(hp[:, None] ^ np.arange(N, dtype=np.uint64)[None, :])
+
+
+def uniform_cols(seed: int, tag: int, spectrum: int, generation: int, P: int, cols):
+    """uniform(seed, tag, spectrum, generation, p, c) for all p < P and c in cols, as (P, len(cols))."""
+    import numpy as np
+    h = mix(seed & MASK)
+    h = mix(h ^ tag)
+    h = mix(h ^ (spectrum & MASK))
+    h = mix(h ^ (generation & MASK))
+    hp = mix_array(np.uint64(h) ^ np.arange(P, dtype=np.uint64))
+    hd = mix_array(hp[:, None] ^ np.asarray(cols, dtype=np.uint64)[None, :])
+    return (hd >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
 
 
 def uniform_array(seed: int, tag: int, spectrum: int, generation: int, P: int, N: int):

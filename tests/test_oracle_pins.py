@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle import de, dls, fit, lbfgs, models, pso, rng, varpro
+from oracle import da, de, dls, dmath, fit, lbfgs, models, pso, rng, varpro
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -333,6 +333,104 @@ def test_de_finds_quadratic_minimum(strategy):
     assert np.all(c >= c[gi]) and np.all(c == f(x))
 
 
+# ---------------------------------------------------------------- fixed-operation elementary functions
+
+def test_dmath_log_exp_against_libm():
+    rs = np.random.default_rng(0)
+    x = np.concatenate([np.exp(rs.uniform(-700, 700, 20000)), rs.uniform(0.5, 2.0, 20000),
+                        [1.0, 2.0, 0.5, 1e-300, 1.7e308]])
+    ref = np.array([math.log(v) for v in x])
+    got = dmath.log(x)
+    assert np.max(np.abs(got - ref) / np.spacing(np.maximum(np.abs(ref), 1e-300))) <= 3.0
+    assert dmath.log(1.0) == 0.0
+    y = np.concatenate([rs.uniform(-700, 700, 20000), rs.uniform(-1, 1, 20000), [0.0, 1.0, -1.0]])
+    ref = np.array([math.exp(v) for v in y])
+    got = dmath.exp(y)
+    assert np.max(np.abs(got - ref) / np.spacing(ref)) <= 2.0
+    assert dmath.exp(0.0) == 1.0 and dmath.exp(800.0) == math.inf and dmath.exp(-800.0) == 0.0
+
+
+def test_dmath_polar_gaussian():
+    us = [rng.uniform_array(1, 99, 0, t, 50000, 1)[:, 0] for t in range(dmath.POLAR_TRIES)]
+    vs = [rng.uniform_array(2, 99, 0, t, 50000, 1)[:, 0] for t in range(dmath.POLAR_TRIES)]
+    z1, z2 = dmath.gauss_pair(us, vs)
+    for z in (z1, z2):
+        assert abs(z.mean()) < 0.02 and abs(z.var() - 1.0) < 0.02
+        assert abs(np.mean(z ** 4) - 3.0) < 0.1            # normal kurtosis
+    assert abs(np.corrcoef(z1, z2)[0, 1]) < 0.02
+    # the pair comes from the first accepted try: u^2 + v^2 = s and z1^2 + z2^2 = -2 log s
+    u, v = 2 * us[0] - 1, 2 * vs[0] - 1
+    s = u * u + v * v
+    ok = (s > 0) & (s < 1)
+    np.testing.assert_allclose((z1 ** 2 + z2 ** 2)[ok], -2 * np.log(s[ok]), rtol=1e-12)
+
+
+# ---------------------------------------------------------------- dual annealing
+
+def test_da_temperature_schedule():
+    assert da.visiting_temperature(1) == da.T0
+    ts = [da.visiting_temperature(t) for t in range(1, 1001)]
+    assert all(a > b for a, b in zip(ts, ts[1:]))
+    for t in (2, 10, 500, 1000):
+        ref = da.T0 * (2 ** (da.QV - 1) - 1) / ((1 + t) ** (da.QV - 1) - 1)
+        assert abs(da.visiting_temperature(t) / ref - 1) < 1e-13
+    # no chain reaches the re-annealing threshold within the iteration cap
+    assert ts[-1] > 2e-5 * da.T0
+
+
+def test_da_visiting_scale_against_its_factors():
+    qv = da.QV
+    for T in (0.37, 5.0, 5230.0):
+        f1 = T ** (1 / (qv - 1))
+        f2 = (qv - 1) ** (4 - qv)
+        f3 = 2 ** ((2 - qv) / (qv - 1))
+        f4 = math.sqrt(math.pi) * f1 * f2 / (f3 * (3 - qv))
+        a = 1 / (qv - 1) - 0.5
+        f6 = math.pi * (1 - a) / math.sin(math.pi * (1 - a)) / math.gamma(2 - a)
+        ref = (f6 / f4) ** (-(qv - 1) / (3 - qv))
+        assert abs(da.sigma(T) / ref - 1) < 1e-12
+
+
+def test_da_visiting_deviates_follow_the_ratio_distribution():
+    # dx = sigma z1 / |z2|^a: P(dx <= v) = E_z2[Phi(v |z2|^a / sigma)], integrated numerically
+    from scipy import integrate, stats
+    T = 3.0
+    sig = da.sigma(T)
+    a = (da.QV - 1) / (3 - da.QV)
+    z1, z2 = da.gauss_pairs(7, 0, 1, 20000, 0, [0, 1, 2])
+    dx = da.visit(z1, z2, sig).ravel()
+    for q in (0.05, 0.25, 0.5, 0.75, 0.95):
+        v = float(np.quantile(dx, q))
+        ref = integrate.quad(lambda y: stats.norm.cdf(v * abs(y) ** a / sig) * stats.norm.pdf(y),
+                             -np.inf, np.inf)[0]
+        assert abs(ref - q) < 0.01, (q, v, ref)
+
+
+def test_da_wrap_and_acceptance():
+    x = np.array([-13.0, -9.0, -5.0, -4.0, -14.5, 3.0])
+    w = da.wrap(x, -13.0, -5.0)
+    np.testing.assert_array_equal(w[:3], x[:3])
+    assert np.all((w >= -13.0) & (w <= -5.0))
+    np.testing.assert_allclose(w[3:], [-12.0, -6.5, -13.0], atol=1e-12)
+    # generalized Metropolis: (1 - (1-qa) dE/T)^(1/(1-qa)), zero once the bracket is not positive
+    T = 2.0
+    for de_ in (0.0, 0.01, 0.1, 0.3):
+        ref = (1 - (1 - da.QA) * de_ / T) ** (1 / (1 - da.QA))
+        assert abs(float(da.accept_probability(np.array([de_]), T)[0]) - ref) < 1e-14
+    assert float(da.accept_probability(np.array([T / (1 - da.QA)]), T)[0]) == 0.0
+    assert float(da.accept_probability(np.array([1.0]), T)[0]) == 0.0
+
+
+def test_da_finds_quadratic_minimum():
+    target = np.array([-9.3, -7.7])
+    def f(th):
+        return np.sum((th - target) ** 2, axis=1)
+    x, c, gi, trace = da.da(f, 2, -13, -5, 32, 200, seed=1)
+    assert np.all(np.diff(trace) <= 0)
+    np.testing.assert_allclose(x[gi], target, atol=2e-2)
+    assert np.all(c == f(x))
+
+
 def test_pso_finds_quadratic_minimum():
     target = np.array([-9.3, -7.7])
     def f(th):
@@ -382,14 +480,15 @@ def _brute_force_n2(om, re, im, lam, n=301):
     return best
 
 
-@pytest.mark.parametrize("method", ["pso", "de"])
+@pytest.mark.parametrize("method", ["pso", "de", "da"])
 @pytest.mark.parametrize("N", [1, 2])
 def test_search_reaches_brute_force_minimum(N, method):
     b = W.single_hn(K=50, N=N)
     re, im = models.synthesize(b)
     lam = dls.LAM_SEARCH
     bf = _brute_force_n1(b.omega, re, im, lam) if N == 1 else _brute_force_n2(b.omega, re, im, lam)
-    r = fit.fit_spectrum(b.omega, re, im, N, -13.0, -6.0, 64, 100, topk=8, method=method)
+    iters = 30 if method == "da" else 100
+    r = fit.fit_spectrum(b.omega, re, im, N, -13.0, -6.0, 64, iters, topk=8, method=method)
     assert r["cost_search"] <= (1 + 1e-6) * bf
 
 
