@@ -191,6 +191,8 @@ def main():
                          "population twice (debye_eval_population) and exit")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="precision of --kernel-case")
+    ap.add_argument("--kernel-n", type=int, default=0, metavar="N",
+                    help="--kernel-case: fit every spectrum with N poles (one pass kernel fills the GPU)")
     args = ap.parse_args()
 
     WORKLOAD = args.workload
@@ -202,7 +204,7 @@ def main():
     if args.impl == "reference":
         return reference_arm(args, rank, world)
     if args.kernel_case:
-        return kernel_case(args.kernel_case, args.precision, P_w)
+        return kernel_case(args.kernel_case, args.precision, P_w, args.kernel_n)
 
     # the oracle baseline runs first, in spawned processes, before any CUDA call
     cpu = None
@@ -426,7 +428,11 @@ def main():
         "autotune": {"cands_per_block": tuned},
         "roofline": {"bound": "alu", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "traffic": traffic,
-                     "launches": n_l, "ms_per_launch": ms_l / max(n_l, 1),
+                     "passes": n_l, "ms_per_pass": ms_l / max(n_l, 1),
+                     "pass_note": "one pass = the concurrent launches of the pass kernel for every "
+                                  "pole count (one kernel per N on forked streams), timed fork to join; "
+                                  "full-population passes only (the line search's masked passes are "
+                                  "timed under *_masked)",
                      "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz",
                      "step_fp32_tflops": step_fp32, "step_fp32_frac": step_fp32 / peak,
                      "per_kind_ms": {k: v[1] for k, v in prof.items()}},
@@ -439,11 +445,13 @@ def main():
         dist.destroy_process_group()
 
 
-def kernel_case(S: int, precision: str, P: int):
+def kernel_case(S: int, precision: str, P: int, n_poles: int = 0):
     """A small fixed case for kernel profilers: one workload subset, two evaluations."""
     import torch
     from paper_2109_01928_gb300 import debyefit as D
     b = W.workload(WORKLOAD).subset(np.arange(S))
+    if n_poles:
+        b.n_poles = np.full(b.S, n_poles, dtype=np.int32)
     tt = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
     om, offs = tt(b.omega), tt(b.offsets, torch.int64)
     with D.Handle(precision) as h:
@@ -457,7 +465,7 @@ def kernel_case(S: int, precision: str, P: int):
         for _ in range(2):
             c = D.debye_eval_population(h, sp, th)
         D.debye_sync(h)
-    print(json.dumps({"kernel_case": WORKLOAD, "spectra": S, "P": P, "precision": precision,
+    print(json.dumps({"kernel_case": WORKLOAD, "spectra": S, "P": P, "n_poles": n_poles, "precision": precision,
                       "mean_cost": float(c.mean())}))
 
 

@@ -237,21 +237,26 @@ int debye_autotune(debye_handle h, const debye_spectra* spectra, int32_t P, int3
 int debye_sync(debye_handle h, cudaStream_t stream);
 
 /* ------------------------------------------------------------------ kernel timing
- * For measurement tools. While enabled, every kernel launch of the evaluation
- * (Gram pass, residual/refinement pass, gradient pass, FP64 solve and finish) is
- * bracketed by CUDA events recorded on the stream it is launched on, and CUDA-graph
- * capture is switched off. Per kernel kind the library accumulates the number of
- * launches, the summed event time (ms) and the algorithmic FLOPs of the launched
- * work: per candidate and frequency sample, 4N + 2(N+2)^2 for the Gram pass (basis
- * build plus the unique Gram/right-hand-side products) and 98N + 38 for the
- * float-float residual pass (FMA counted as 2). Launches restricted by an
- * activity mask (the polish line search) count their time but no FLOPs. */
-#define DEBYE_KERNEL_GRAM   0
-#define DEBYE_KERNEL_REFINE 1
-#define DEBYE_KERNEL_GRAD   2
-#define DEBYE_KERNEL_SOLVE  3
-#define DEBYE_KERNEL_FINISH 4
-#define DEBYE_KERNEL_KINDS  5
+ * For measurement tools. While enabled, CUDA-graph capture is switched off and
+ * every pass of the evaluation is bracketed by CUDA events recorded on the
+ * launching stream: a Gram, residual/refinement or gradient pass is one kernel
+ * per pole count, launched concurrently on forked streams, and its interval runs
+ * from the fork to the join; the FP64 solve and the finish are single launches.
+ * Per kind the library accumulates the number of passes, the summed event time
+ * (ms) and the algorithmic FLOPs of the work: per candidate and frequency sample,
+ * 4N + 2(N+2)^2 for the Gram pass (basis build plus the unique Gram/right-hand-side
+ * products) and 98N + 38 for the float-float residual pass (FMA counted as 2).
+ * Passes restricted by an activity mask (the polish line search and its accepted
+ * points) are accumulated under their own *_MASKED kinds, with time but no FLOPs. */
+#define DEBYE_KERNEL_GRAM          0
+#define DEBYE_KERNEL_REFINE        1
+#define DEBYE_KERNEL_GRAD          2
+#define DEBYE_KERNEL_SOLVE         3
+#define DEBYE_KERNEL_FINISH        4
+#define DEBYE_KERNEL_GRAM_MASKED   5
+#define DEBYE_KERNEL_REFINE_MASKED 6
+#define DEBYE_KERNEL_GRAD_MASKED   7
+#define DEBYE_KERNEL_KINDS         8
 
 /* Number of kernel launches the handle has enqueued (a CUDA-graph replay counts
  * each of its kernel nodes); reset != 0 sets the counter to zero afterwards. */
@@ -260,8 +265,8 @@ int debye_launch_count(debye_handle h, int64_t* count, int32_t reset);
 /* Enable (1) or disable (0) kernel timing; enabling clears the totals. */
 int debye_profile_enable(debye_handle h, int32_t enable);
 
-/* Totals of kernel kind `kind` since timing was enabled (waits for the recorded
- * events). Any output pointer may be NULL. */
+/* Totals of kind `kind` since timing was enabled: passes (or launches), summed
+ * milliseconds, FLOPs (waits for the recorded events). Any output may be NULL. */
 int debye_profile_read(debye_handle h, int32_t kind, int64_t* launches, double* ms, double* flops);
 
 /* Message of the last failed call on h (never NULL; "" if none). */

@@ -235,8 +235,9 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
                         double* weights, double* grad, double* g1, int cb, cudaStream_t st) {
   // The buckets' launches of one pass are independent (disjoint candidates): all but
   // the first non-empty one go to side streams forked from st and joined back, so
-  // that one bucket's tail overlaps the others' work. Kernel timing runs them in
-  // order on st instead, so that each launch's duration is its own.
+  // that the pole counts' launches run concurrently and fill the GPU together.
+  // Kernel timing brackets the whole pass (fork to join) with events on st: its
+  // duration is that of the pass as it runs, and its FLOPs those of every bucket.
   auto per_bucket = [&](int phase) -> int {
     int first = -1, n_nonempty = 0;
     for (int b = 0; b < N_BUCKETS; ++b)
@@ -244,7 +245,16 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
         if (first < 0) first = b;
         ++n_nonempty;
       }
-    const bool fork = n_nonempty > 1 && !prof_on;
+    if (!n_nonempty) return DEBYE_OK;
+    ProfEntry pe;
+    if (prof_on) {
+      double fl = 0.0;
+      if (!a.active)
+        for (const Unit& x : g.units)
+          fl += (double)(x.q1 - x.q0) * (double)(x.k1 - x.k0) * flops_per_cand_k(phase, x.N);
+      prof_begin(a.active ? DEBYE_KERNEL_GRAM_MASKED + phase : phase, fl, st, pe);
+    }
+    const bool fork = n_nonempty > 1;
     if (fork) cudaEventRecord(ev_fork, st);
     for (int b = 0; b < N_BUCKETS; ++b) {
       const int n = g.begin[b + 1] - g.begin[b];
@@ -260,32 +270,16 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
       const int grid = std::max(1, std::min(n, sms * 16));
       // Gram rows of N >= 13 split over two warps (fewer live accumulators) when each
       // candidate has one lane
-      ab.gs = (phase == PH_GRAM && mixed && b >= 3 && a.ks == 1 && cb % 32 == 0) ? 2 : 1;
+      ab.gs = (phase == PH_GRAM && mixed && b + 1 >= 13 && a.ks == 1 && cb % 32 == 0) ? 2 : 1;
       const int pblock = cb * a.ks * ab.gs;
-      ProfEntry pe;
-      if (prof_on) {
-        double fl = 0.0;
-        if (!a.active)
-          for (int u = g.begin[b]; u < g.begin[b + 1]; ++u) {
-            const Unit& x = g.units[u];
-            fl += (double)(x.q1 - x.q0) * (double)(x.k1 - x.k0) * flops_per_cand_k(phase, x.N);
-          }
-        prof_begin(phase, fl, st, pe);
-      }
-      switch (b) {
-        case 0: launch_pass_b0(phase, mixed, ab, grid, pblock, bs); break;
-        case 1: launch_pass_b1(phase, mixed, ab, grid, pblock, bs); break;
-        case 2: launch_pass_b2(phase, mixed, ab, grid, pblock, bs); break;
-        case 3: launch_pass_b3(phase, mixed, ab, grid, pblock, bs); break;
-        default: launch_pass_b4(phase, mixed, ab, grid, pblock, bs); break;
-      }
-      if (prof_on) prof_end(pe, st);
+      launch_pass(b + 1, phase, mixed, ab, grid, pblock, bs);
       ++launches;
       if (bs != st) {
         cudaEventRecord(ev_join[b], bs);
         cudaStreamWaitEvent(st, ev_join[b], 0);
       }
     }
+    if (prof_on) prof_end(pe, st);
     return check_launch("pass");
   };
   auto timed = [&](int kind, auto launch) {

@@ -679,8 +679,8 @@ __device__ __forceinline__ void dispatch_n(const EvalArgs& a, const Unit& u) {
   }
 }
 
-// One block per unit (grid-stride over the unit list); LO..HI is the pole
-// bucket compiled into this kernel. At most MAXT threads per block; MINB
+// One block per unit (grid-stride over the unit list); LO..HI is the range of
+// pole counts compiled into this kernel (the library launches one N per kernel). At most MAXT threads per block; MINB
 // resident blocks of that size bound the registers per thread (128 x 3: 168
 // registers, 12 warps per SM with 64-thread blocks).
 template <int PH, int LO, int HI, bool MIXED, int MAXT, int MINB>

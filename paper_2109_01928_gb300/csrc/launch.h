@@ -7,11 +7,12 @@
 
 namespace debyefit {
 
-constexpr int N_BUCKETS = 5;  // pole buckets compiled into separate kernels
+// One pass kernel per pole count: every warp of a launch runs the same unrolled
+// code (no instruction-cache thrashing between pole counts) and each N gets the
+// registers it needs. Work units are grouped by N ("buckets").
+constexpr int N_BUCKETS = NMAX;
 constexpr int MAX_BLOCK = 128; // largest pass block (candidates x lanes; mixed Gram shared memory at N = 20)
-__host__ __device__ constexpr int bucket_lo(int b) { return 4 * b + 1; }
-__host__ __device__ constexpr int bucket_hi(int b) { return 4 * b + 4; }
-__host__ __device__ constexpr int bucket_of(int N) { return (N - 1) / 4; }
+__host__ __device__ constexpr int bucket_of(int N) { return N - 1; }
 
 // Work layout for spectra with `per_spectrum` candidates each: `cb` candidates per
 // unit and `ks` lanes per candidate, 64 threads per pass block. Full populations
@@ -31,12 +32,22 @@ inline void choose_layout(int64_t per_spectrum, int cb_opt, int* cb, int* ks) {
   *cb = std::max(1, 64 / *ks);
 }
 
-// Per-N passes (eval.cuh), one translation unit per bucket.
-void launch_pass_b0(int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st);
-void launch_pass_b1(int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st);
-void launch_pass_b2(int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st);
-void launch_pass_b3(int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st);
-void launch_pass_b4(int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st);
+// Per-N passes (eval.cuh); pole counts 1-4, 5-8, 9-12, 13-16 and 17-20 compile in
+// separate translation units (pass_b0.cu .. pass_b4.cu) so that they build in parallel.
+void launch_pass_b0(int N, int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st);
+void launch_pass_b1(int N, int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st);
+void launch_pass_b2(int N, int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st);
+void launch_pass_b3(int N, int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st);
+void launch_pass_b4(int N, int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st);
+inline void launch_pass(int N, int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st) {
+  switch ((N - 1) / 4) {
+    case 0: launch_pass_b0(N, phase, mixed, a, grid, block, st); break;
+    case 1: launch_pass_b1(N, phase, mixed, a, grid, block, st); break;
+    case 2: launch_pass_b2(N, phase, mixed, a, grid, block, st); break;
+    case 3: launch_pass_b3(N, phase, mixed, a, grid, block, st); break;
+    default: launch_pass_b4(N, phase, mixed, a, grid, block, st); break;
+  }
+}
 
 void launch_prep(int64_t n_samples, int64_t S, const int64_t* offsets, const double* omega,
                  const double* er, const double* ei, const double* lo, const double* hi,

@@ -216,13 +216,7 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
       ab.n_units = n;
       const int grid = std::max(1, std::min(n, sms * 16));
       ab.gs = 1;
-      switch (b) {
-        case 0: launch_pass_b0(phase, mixed, ab, grid, cb * ks, st); break;
-        case 1: launch_pass_b1(phase, mixed, ab, grid, cb * ks, st); break;
-        case 2: launch_pass_b2(phase, mixed, ab, grid, cb * ks, st); break;
-        case 3: launch_pass_b3(phase, mixed, ab, grid, cb * ks, st); break;
-        default: launch_pass_b4(phase, mixed, ab, grid, cb * ks, st); break;
-      }
+      launch_pass(b + 1, phase, mixed, ab, grid, cb * ks, st);
     }
   };
   per_bucket(PH_GRAM);

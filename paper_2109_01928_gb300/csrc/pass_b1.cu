@@ -1,36 +1,15 @@
-// Per-N pass kernels for poles N = 5..8 (one translation unit per bucket so
-// the buckets compile in parallel).
-#include "eval.cuh"
-#include "launch.h"
+// Pass kernels for pole counts N = 5..8, one kernel per N (one translation
+// unit per group of four so that the groups compile in parallel).
+#include "pass.cuh"
 
 namespace debyefit {
 
-void launch_pass_b1(int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st) {
-  constexpr int LO = 5, HI = 8;
-  // mixed-precision passes up to 12 poles fit in 168 registers without spills:
-  // cap them for 3 resident 128-thread blocks; larger N keeps the full register
-  // file, and its Gram pass may run two warps per candidate group (256 threads)
-  constexpr int MB_MIXED = HI <= 12 ? 3 : 1;
-  constexpr int MAXT = HI <= 12 ? 128 : 256;
-  if (mixed) {
-    if (phase == PH_GRAM) {
-      const int per_thread = a.gs == 2 ? split_part_floats(HI) : gram_smem_stride(HI);
-      const size_t smem = sizeof(float) * per_thread * block;
-      static bool attr_set = false;
-      if (!attr_set) {
-        const int most = std::max(gram_smem_stride(HI) * MAX_BLOCK, split_part_floats(HI) * 2 * MAX_BLOCK);
-        cudaFuncSetAttribute(k_pass<PH_GRAM, LO, HI, true, MAXT, MB_MIXED>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float) * most));
-        attr_set = true;
-      }
-      k_pass<PH_GRAM, LO, HI, true, MAXT, MB_MIXED><<<grid, block, smem, st>>>(a);
-    }
-    else if (phase == PH_REFINE) k_pass<PH_REFINE, LO, HI, true, MAXT, MB_MIXED><<<grid, block, 0, st>>>(a);
-    else k_pass<PH_GRAD, LO, HI, true, MAXT, 1><<<grid, block, 0, st>>>(a);
-  } else {
-    if (phase == PH_GRAM) k_pass<PH_GRAM, LO, HI, false, MAXT, 1><<<grid, block, 0, st>>>(a);
-    else if (phase == PH_REFINE) k_pass<PH_REFINE, LO, HI, false, MAXT, 1><<<grid, block, 0, st>>>(a);
-    else k_pass<PH_GRAD, LO, HI, false, MAXT, 1><<<grid, block, 0, st>>>(a);
+void launch_pass_b1(int N, int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st) {
+  switch (N) {
+    case 5: launch_pass_n<5>(phase, mixed, a, grid, block, st); break;
+    case 6: launch_pass_n<6>(phase, mixed, a, grid, block, st); break;
+    case 7: launch_pass_n<7>(phase, mixed, a, grid, block, st); break;
+    default: launch_pass_n<8>(phase, mixed, a, grid, block, st); break;
   }
 }
 

@@ -315,7 +315,8 @@ def debye_sync(h: Handle, stream=None):
     h.check(lib().debye_sync(h.ptr, _stream(stream)))
 
 
-KERNEL_KINDS = {"gram": 0, "refine": 1, "grad": 2, "solve": 3, "finish": 4}
+KERNEL_KINDS = {"gram": 0, "refine": 1, "grad": 2, "solve": 3, "finish": 4, "gram_masked": 5,
+                "refine_masked": 6, "grad_masked": 7}
 
 
 def debye_eval_population_noalloc(sp: Spectra, theta, precision: str = "mixed", weights: bool = False,
