@@ -45,6 +45,50 @@ FP32_LANES_PER_SM, SMS, SM_MAX_MHZ = 128, 152, 2070.0
 KERNEL_SOURCES = ["paper_2109_01928_gb300/csrc/eval.cuh", "paper_2109_01928_gb300/csrc/common.cuh"]
 
 
+# ------------------------------------------------------------------ replicas (one process per GPU)
+
+def replica_workload(name: str, rank: int):
+    """Rank r fits its own batch of the workload's shape: the generator seed is r."""
+    return W.workload(name, seed=rank)
+
+
+class RankReduce:
+    """Barrier and max/sum over ranks (NCCL on the GPUs, gloo in the CPU tests); with
+    one rank these are identities. No collective touches the fitted data."""
+
+    def __init__(self, world: int, device=None):
+        self.world = world
+        self.device = device
+
+    def _all_reduce(self, v: float, op) -> float:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device=self.device)
+        dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max(self, v: float) -> float:
+        if self.world == 1:
+            return v
+        import torch.distributed as dist
+        return self._all_reduce(v, dist.ReduceOp.MAX)
+
+    def sum(self, v: float) -> float:
+        if self.world == 1:
+            return v
+        import torch.distributed as dist
+        return self._all_reduce(v, dist.ReduceOp.SUM)
+
+    def rate(self, work: float, seconds: float) -> float:
+        """Whole-job throughput: all ranks' work over the slowest rank's time."""
+        return self.sum(work) / self.max(seconds)
+
+
 # ------------------------------------------------------------------ oracle timing (CPU)
 
 def _oracle_chunk(job):
@@ -221,25 +265,10 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", init_method="env://", device_id=dev)
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    red = RankReduce(world, dev)
+    barrier, max_over_ranks, sum_over_ranks = red.barrier, red.max, red.sum
 
-    def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
-
-    b = W.workload(WORKLOAD, seed=rank)
+    b = replica_workload(WORKLOAD, rank)
     b.P = P_w
     iters = iters_w if args.iters is None else args.iters
     S = b.S

@@ -9,8 +9,8 @@
  *     Cole-Davidson, Jonscher, CRIM: Eqs. 3-6) or by tabulated values (Sec. III-A);
  *   - is approximated by the multi-pole Debye expansion
  *     eps_inf + sum_n d_eps_n / (1 + j w tau_n)                             (Eq. 7);
- *   - a global optimiser (particle swarm or differential evolution) searches the
- *     relaxation times, and for
+ *   - a global optimiser (particle swarm, differential evolution or dual
+ *     annealing) searches the relaxation times, and for
  *     each candidate the weights (eps_inf, d_eps_n) come from damped least squares
  *     over the real and imaginary parts, with negative weights sign-flipped as a
  *     penalty (Sec. III-A, III-B);
@@ -74,6 +74,7 @@ extern "C" {
 /* ------------------------------------------------------------------ search methods */
 #define DEBYE_SEARCH_PSO 0    /* particle swarm (Sec. III-B; Kennedy and Eberhart) */
 #define DEBYE_SEARCH_DE  1    /* differential evolution (Sec. III-B; Storn and Price) */
+#define DEBYE_SEARCH_DA  2    /* dual annealing (Sec. III-B; Tsallis and Stariolo), iters <= 1000 */
 #define DEBYE_DE_RAND1   0    /* mutant x_r1 + F (x_r2 - x_r3), needs P >= 4 */
 #define DEBYE_DE_BEST1   1    /* mutant x_best + F (x_r1 - x_r2), needs P >= 3 */
 
@@ -97,6 +98,8 @@ typedef struct {
   double  de_f_hi;        /*   once per generation; 0 <= lo <= hi <= 2 (default 0.5, 1.0) */
   double  de_cr;          /* binomial crossover rate, 0..1 (default 0.7) */
   int32_t de_strategy;    /* DEBYE_DE_RAND1 (default) or DEBYE_DE_BEST1 */
+  double  da_t0;          /* dual annealing: initial visiting temperature, > 0 (default 5230) */
+  double  da_qa;          /* dual annealing: acceptance parameter, < 1 (default -5) */
 } debye_options;
 
 /* A ragged batch of S spectra, CSR over frequency (all device memory unless _host). */
@@ -122,7 +125,7 @@ typedef struct {
   int32_t  polish_iters;  /* L-BFGS iterations per polished candidate, >= 0 */
   double*  trace;         /* optional [S][iters+1] device: global-best cost per generation */
   double*  evals;         /* optional [1] device: candidate evaluations x K performed */
-  int32_t  method;        /* DEBYE_SEARCH_PSO (0) or DEBYE_SEARCH_DE */
+  int32_t  method;        /* DEBYE_SEARCH_PSO (0), DEBYE_SEARCH_DE or DEBYE_SEARCH_DA */
 } debye_search;
 
 /* Fill *opt with the defaults listed above. */
@@ -162,9 +165,10 @@ int debye_eval_population(debye_handle h, const debye_spectra* spectra, int32_t 
 int debye_cost_grad(debye_handle h, const debye_spectra* spectra, int32_t P, int32_t n_max,
                     const double* theta, double* cost, double* grad, cudaStream_t stream);
 
-/* Whole fit (Sec. III-B, IV): seeded particle swarm or differential evolution
- * over log10(tau) with DLS weights, projected L-BFGS polish of the best
- * polish_topk personal bests (swarm) or population members (evolution), the
+/* Whole fit (Sec. III-B, IV): seeded particle swarm, differential evolution or
+ * dual annealing over log10(tau) with DLS weights, projected L-BFGS polish of
+ * the best polish_topk personal bests (swarm), population members (evolution)
+ * or chain states (annealing; iters = outer iterations of 2N moves each), the
  * best result re-solved in FP64 at damping lam_final with the sign flip, poles
  * sorted by ascending tau. Outputs eps_inf [S], d_eps [S][n_max], tau [S][n_max]
  * (seconds; entries beyond N_s are 0) and final_cost [S] (cost at lam_final). */

@@ -291,6 +291,7 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
   };
   int rc;
   a.n_units = (int)g.units.size();
+  a.lf32 = mixed ? 1 : 0;
   if (a.n_units == 0) return DEBYE_OK;
   if (a.ks < 1 || a.ks > 32 || (a.ks & (a.ks - 1)) || cb * a.ks > MAX_BLOCK)
     return fail(DEBYE_EINTERNAL, "bad work layout (%d candidates x %d lanes)", cb, a.ks);
@@ -347,7 +348,7 @@ static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_
     qe[s] = (int32_t)((s + 1) * P);
   }
   int cb, ks;
-  choose_layout(P, h->cb_option(), &cb, &ks);
+  choose_layout(P, pl.S * (int64_t)P, h->sms, h->opt.cands_per_block, h->tuned_cb, &cb, &ks);
   UnitGroups g;
   build_units(pl, qb, qe, cb, g);
   if ((rc = h->upload_units(g, h->ws_units, st))) return rc;
@@ -411,6 +412,8 @@ void debye_default_options(debye_options* o) {
   o->de_f_hi = 1.0;
   o->de_cr = 0.7;
   o->de_strategy = DEBYE_DE_RAND1;
+  o->da_t0 = 5230.0;
+  o->da_qa = -5.0;
 }
 
 int debye_fit_init(debye_handle* out, const debye_options* opt) {
@@ -430,6 +433,7 @@ int debye_fit_init(debye_handle* out, const debye_options* opt) {
   if (!(o.de_f_lo >= 0.0) || !(o.de_f_hi >= o.de_f_lo) || !(o.de_f_hi <= 2.0)) return DEBYE_EINVAL;
   if (!(o.de_cr >= 0.0) || !(o.de_cr <= 1.0)) return DEBYE_EINVAL;
   if (o.de_strategy != DEBYE_DE_RAND1 && o.de_strategy != DEBYE_DE_BEST1) return DEBYE_EINVAL;
+  if (!(o.da_t0 > 0.0) || !(o.da_t0 < 1e300) || !(o.da_qa < 1.0) || !(o.da_qa > -1e6)) return DEBYE_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();

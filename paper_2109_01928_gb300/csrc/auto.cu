@@ -141,8 +141,10 @@ extern "C" int debye_fit_auto(debye_handle h, const debye_spectra* sp, const deb
   if (se->P < 1 || se->P > 32768) return h->fail(DEBYE_EINVAL, "P = %d outside 1..32768", se->P);
   if (se->iters < 0 || se->polish_iters < 0) return h->fail(DEBYE_EINVAL, "iters < 0 or polish_iters < 0");
   if (se->polish_topk < 0 || se->polish_topk > 64) return h->fail(DEBYE_EINVAL, "polish_topk outside 0..64");
-  if (se->method != DEBYE_SEARCH_PSO && se->method != DEBYE_SEARCH_DE)
-    return h->fail(DEBYE_EINVAL, "method must be DEBYE_SEARCH_PSO or DEBYE_SEARCH_DE");
+  if (se->method != DEBYE_SEARCH_PSO && se->method != DEBYE_SEARCH_DE && se->method != DEBYE_SEARCH_DA)
+    return h->fail(DEBYE_EINVAL, "method must be DEBYE_SEARCH_PSO, DEBYE_SEARCH_DE or DEBYE_SEARCH_DA");
+  if (se->method == DEBYE_SEARCH_DA && se->iters > 1000)
+    return h->fail(DEBYE_EINVAL, "dual annealing: at most 1000 outer iterations");
   if (se->method == DEBYE_SEARCH_DE && se->iters > 0 &&
       se->P < (h->opt.de_strategy == DEBYE_DE_RAND1 ? 4 : 3))
     return h->fail(DEBYE_EINVAL, "differential evolution needs P >= %d",

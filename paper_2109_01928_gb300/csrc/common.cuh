@@ -38,7 +38,7 @@ struct Scratch {
   int32_t nmax;     // pole capacity of theta / weights rows
   int32_t ng;       // per-candidate Gram record: packed (nmax+1) lower triangle + h
   double* G;        // [ng][Q]   Gram (packed) followed by h = A^T b
-  double* L;        // [npk][Q]  Cholesky factor of the scaled damped matrix
+  double* L;        // [npk][Q]  Cholesky factor of the scaled damped matrix (float [npk][Q] if lf32)
   double* dinv;     // [nmax+1][Q] 1 / sqrt(G_ii)
   double* x;        // [nmax+1][Q] current (unflipped) weights
   double* xh;       // [nmax+1][Q] flipped weights
@@ -62,6 +62,7 @@ struct EvalArgs {
   int32_t ks;              // lanes per candidate in the pass kernels (power of two <= 32)
   int32_t zero_b;          // residual pass against b = 0 (t = -A^T A x), for the adjoint refinement
   int32_t gs;              // Gram pass: 2 = each candidate's Gram rows split over two warps
+  int32_t lf32;            // Cholesky factor stored and applied in FP32 (mixed precision)
   double lam;
   Scratch sc;
   int* status;             // device status word
@@ -206,5 +207,7 @@ __host__ __device__ __forceinline__ uint32_t rng_below(uint64_t key, uint32_t m)
 constexpr uint64_t TAG_INIT_POS = 1, TAG_INIT_VEL = 2, TAG_R1 = 3, TAG_R2 = 4;
 // differential evolution: donor indices, forced coordinate, crossover, bound re-draw, F
 constexpr uint64_t TAG_DE_IDX = 5, TAG_DE_J = 6, TAG_DE_CR = 7, TAG_DE_BOUND = 8, TAG_DE_F = 9;
+// dual annealing: uniforms of the visiting deviates, acceptance draws
+constexpr uint64_t TAG_DA_VISIT = 10, TAG_DA_ACCEPT = 11;
 
 }  // namespace debyefit

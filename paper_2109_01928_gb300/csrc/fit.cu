@@ -85,7 +85,7 @@ int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, in
   if (Q > ((int64_t)1 << 31) - 1) return h->fail(DEBYE_EINVAL, "S*P exceeds 2^31-1");
   if ((rc = h->prep_spectra(sp, pl, st))) return rc;
   int cb, ks;
-  choose_layout(P, h->cb_option(), &cb, &ks);
+  choose_layout(P, Q, h->sms, h->opt.cands_per_block, h->tuned_cb, &cb, &ks);
   const bool mixed = h->opt.precision == DEBYE_PREC_MIXED;
   const int nmax = n_max;
 
@@ -114,7 +114,10 @@ int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, in
   sa.de_f_hi = h->opt.de_f_hi;
   sa.de_cr = h->opt.de_cr;
   sa.de_strategy = h->opt.de_strategy;
+  sa.da_t0 = h->opt.da_t0;
+  sa.da_qa = h->opt.da_qa;
   const bool evolve = se->method == DEBYE_SEARCH_DE;
+  const bool anneal = se->method == DEBYE_SEARCH_DA;
   sa.n_poles = sp->n_poles;
   sa.lo = sp->lo;
   sa.hi = sp->hi;
@@ -135,6 +138,14 @@ int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, in
   sa.gbest = (int32_t*)p;
   if ((rc = h->named("swarm.gen", sizeof(int), &p))) return rc;
   sa.gen = (int*)p;
+  if (anneal) {
+    if ((rc = h->named("anneal.cx", qn, &p))) return rc;
+    sa.cx = (double*)p;
+    if ((rc = h->named("anneal.ce", sizeof(double) * Q, &p))) return rc;
+    sa.ce = (double*)p;
+    if ((rc = h->named("anneal.active", Q, &p))) return rc;
+    sa.active = (uint8_t*)p;
+  }
   sa.trace = se->trace;
   sa.evals = se->evals;
   if (se->evals && reset_evals) cudaMemsetAsync(se->evals, 0, sizeof(double), st);
@@ -157,9 +168,29 @@ int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, in
   launch_pso_init(sa, h->sms, st); ++h->launches;
   if ((rc = h->run_eval(ea, g, mixed, steps, cost, nullptr, nullptr, h->sb_eval.g1, cb, st))) return rc;
   launch_pso_best(sa, cost, h->sms, st); ++h->launches;
+  if (anneal) {
+    launch_da_start(sa, h->sms, st);
+    ++h->launches;
+  }
   launch_gen_advance(sa.gen, st); ++h->launches;
   if ((rc = h->check_launch("swarm start"))) return rc;
-  rc = repeat(h, se->iters, st, [&]() -> int {
+  if (anneal) {
+    // one outer iteration: 2 nmax moves (moves beyond 2 N_s are masked for spectrum s),
+    // each evaluated and accepted or rejected, then the per-spectrum best and trace
+    EvalArgs ev = ea;
+    ev.active = sa.active;
+    rc = repeat(h, se->iters, st, [&]() -> int {
+      for (int j = 0; j < 2 * pl.nmax_seen; ++j) {
+        launch_da_visit(sa, j, h->sms, st); ++h->launches;
+        int r = h->run_eval(ev, g, mixed, steps, cost, nullptr, nullptr, h->sb_eval.g1, cb, st);
+        if (r) return r;
+        launch_da_accept(sa, cost, j, h->sms, st); ++h->launches;
+      }
+      launch_da_best(sa, h->sms, st); ++h->launches;
+      launch_gen_advance(sa.gen, st); ++h->launches;
+      return h->check_launch("annealing iteration");
+    });
+  } else rc = repeat(h, se->iters, st, [&]() -> int {
     if (evolve) launch_de_trial(sa, h->sms, st);
     else launch_pso_move(sa, h->sms, st);
     ++h->launches;
@@ -226,8 +257,8 @@ int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, in
       ae[s] = (int32_t)((s + 1) * T);
     }
     int cbp, ksp, cba, ksa;
-    choose_layout((int64_t)T * pa.R, h->cb_option(), &cbp, &ksp);
-    choose_layout(T, h->cb_option(), &cba, &ksa);
+    choose_layout((int64_t)T * pa.R, pl.S * T * pa.R, h->sms, h->opt.cands_per_block, h->tuned_cb, &cbp, &ksp);
+    choose_layout(T, pl.S * T, h->sms, h->opt.cands_per_block, h->tuned_cb, &cba, &ksa);
     UnitGroups gp, ga;
     build_units(pl, pb, pe, cbp, gp);
     build_units(pl, ab, ae, cba, ga);
@@ -293,7 +324,7 @@ int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, in
     fe[s] = (int32_t)(s + 1);
   }
   int cbf, ksf;
-  choose_layout(1, 0, &cbf, &ksf);
+  choose_layout(1, S, h->sms, 0, 0, &cbf, &ksf);
   UnitGroups gf;
   build_units(pl, fb, fe, cbf, gf);
   if ((rc = h->upload_units(gf, h->named_bufs["fin.units"], st))) return rc;
@@ -318,8 +349,10 @@ extern "C" int debye_fit_batch(debye_handle h, const debye_spectra* sp, const de
   if (!sp || !se) return h->fail(DEBYE_EINVAL, "spectra or search is NULL");
   if (se->P < 1 || se->P > 32768) return h->fail(DEBYE_EINVAL, "P = %d outside 1..32768", se->P);
   if (se->iters < 0) return h->fail(DEBYE_EINVAL, "iters < 0");
-  if (se->method != DEBYE_SEARCH_PSO && se->method != DEBYE_SEARCH_DE)
-    return h->fail(DEBYE_EINVAL, "method must be DEBYE_SEARCH_PSO or DEBYE_SEARCH_DE");
+  if (se->method != DEBYE_SEARCH_PSO && se->method != DEBYE_SEARCH_DE && se->method != DEBYE_SEARCH_DA)
+    return h->fail(DEBYE_EINVAL, "method must be DEBYE_SEARCH_PSO, DEBYE_SEARCH_DE or DEBYE_SEARCH_DA");
+  if (se->method == DEBYE_SEARCH_DA && se->iters > 1000)
+    return h->fail(DEBYE_EINVAL, "dual annealing: at most 1000 outer iterations");
   if (se->method == DEBYE_SEARCH_DE && se->iters > 0 &&
       se->P < (h->opt.de_strategy == DEBYE_DE_RAND1 ? 4 : 3))
     return h->fail(DEBYE_EINVAL, "differential evolution needs P >= %d",

@@ -101,7 +101,6 @@ struct debye_ctx {
   int run_eval(debyefit::EvalArgs a, const debyefit::UnitGroups& g, bool mixed, int steps,
                double* cost, double* weights, double* grad, double* g1, int cb, cudaStream_t st);
   int eval_steps(bool with_grad) const;
-  int cb_option() const { return opt.cands_per_block > 0 ? opt.cands_per_block : tuned_cb; }
   int named(const char* name, size_t bytes, void** out);
 
   void free_buf(debyefit::Buf& b) {

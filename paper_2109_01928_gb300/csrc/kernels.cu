@@ -52,37 +52,65 @@ __global__ void k_prep_spectra(int64_t S, const int64_t* __restrict__ offsets,
 }
 
 // ------------------------------------------------------------------ damped solve
-// x0 = M^-1 h per candidate; stores L, D^-1, x0 and the failure flag.
+// Scaling helpers of the factor type T: the FP64 path divides by d = 1/dinv in
+// FP64 (as the plain method reads); the mixed path scales in FP32 by dinv.
+template <typename T>
+struct Scale {
+  T dinv[NMAX1];   // 1 / sqrt(G_ii)
+  double d[NMAX1]; // sqrt(G_ii)
+  __device__ __forceinline__ void load(const Scratch& sc, int64_t q, int n) {
+    for (int i = 0; i < n; ++i) {
+      dinv[i] = (T)sc.dinv[(int64_t)i * sc.Q + q];
+      if constexpr (sizeof(T) == 8) d[i] = 1.0 / sc.dinv[(int64_t)i * sc.Q + q];
+      else d[i] = (double)(1.0f / dinv[i]);
+    }
+  }
+  // D^-1 v for an FP64 vector entry, as T
+  __device__ __forceinline__ T down(double v, int i) const {
+    if constexpr (sizeof(T) == 8) return v / d[i];
+    else return (float)v * dinv[i];
+  }
+  // D^-1 v for a T entry, as FP64
+  __device__ __forceinline__ double up(T v, int i) const {
+    if constexpr (sizeof(T) == 8) return v / d[i];
+    else return (double)(v * dinv[i]);
+  }
+};
+
+// x0 = M^-1 h per candidate; stores L (type T), D^-1, x0 and the failure flag.
+template <typename T>
 __global__ void __launch_bounds__(256) k_solve(EvalArgs a) {
   const int64_t Q = a.sc.Q;
   const int hb = (a.sc.nmax + 1) * (a.sc.nmax + 2) / 2;
+  T* Lg = factor_base_w<T>(a.sc);
   for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
     const Unit u = a.units[ui];
     const int q = u.q0 + (int)threadIdx.x;
     if (q >= u.q1 || (a.active && !a.active[q])) continue;
     const int n = u.N + 1;
-    double L[NPACK_MAX], dinv[NMAX1], z[NMAX1];
-    for (int i = 0; i < n; ++i) dinv[i] = 1.0 / sqrt(a.sc.G[(int64_t)pk(i, i) * Q + q]);
+    T L[NPACK_MAX], dinv[NMAX1], z[NMAX1];
+    for (int i = 0; i < n; ++i) dinv[i] = T(1) / sqrt_t((T)a.sc.G[(int64_t)pk(i, i) * Q + q]);
     for (int i = 0; i < n; ++i) {
-      for (int j = 0; j < i; ++j) L[pk(i, j)] = a.sc.G[(int64_t)pk(i, j) * Q + q] * dinv[i] * dinv[j];
-      L[pk(i, i)] = 1.0 + a.lam;
+      for (int j = 0; j < i; ++j) L[pk(i, j)] = (T)a.sc.G[(int64_t)pk(i, j) * Q + q] * dinv[i] * dinv[j];
+      L[pk(i, i)] = (T)(1.0 + a.lam);
     }
     bool ok = cholesky_packed(L, n);
+    double x0[NMAX1];
     if (ok) {
-      for (int i = 0; i < n; ++i) z[i] = a.sc.G[(int64_t)(hb + i) * Q + q] * dinv[i];
+      for (int i = 0; i < n; ++i) z[i] = (T)a.sc.G[(int64_t)(hb + i) * Q + q] * dinv[i];
       llt_solve(L, z, n);
       for (int i = 0; i < n; ++i) {
-        z[i] *= dinv[i];
-        ok = ok && isfinite(z[i]);
+        x0[i] = (double)(z[i] * dinv[i]);
+        ok = ok && isfinite(x0[i]);
       }
     }
     a.sc.fail[q] = ok ? 0 : 1;
     if (!ok) continue;
     const int npk = n * (n + 1) / 2;
-    for (int e = 0; e < npk; ++e) a.sc.L[(int64_t)e * Q + q] = L[e];
+    for (int e = 0; e < npk; ++e) Lg[(int64_t)e * Q + q] = L[e];
     for (int i = 0; i < n; ++i) {
-      a.sc.dinv[(int64_t)i * Q + q] = dinv[i];
-      a.sc.x[(int64_t)i * Q + q] = z[i];
+      a.sc.dinv[(int64_t)i * Q + q] = (double)dinv[i];
+      a.sc.x[(int64_t)i * Q + q] = x0[i];
     }
   }
 }
@@ -97,10 +125,13 @@ __global__ void __launch_bounds__(256) k_solve(EvalArgs a) {
 // then the sign flip x_hat = x1 + e (e_i = -2 x1_i where d_eps_i < 0, Sec. III-B) and
 //   cost(x_hat) = cost(x1) - 2 e^T g1 + e^T M e,  g1 = g - M dx.
 // Outputs cost[q], weights[q][nmax+1] (optional); keeps x1, x_hat and g1 for the gradient.
+// Sums of the cost identity are FP64; products with the factor are in its type T.
+template <typename T>
 __global__ void __launch_bounds__(256) k_finish(EvalArgs a, int final_step, double* cost,
                                                 double* weights, double* g1_out) {
   const int64_t Q = a.sc.Q;
   const int nm1 = a.sc.nmax + 1;
+  const T* Lg = factor_base<T>(a.sc);
   for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
     const Unit u = a.units[ui];
     const int q = u.q0 + (int)threadIdx.x;
@@ -114,28 +145,31 @@ __global__ void __launch_bounds__(256) k_finish(EvalArgs a, int final_step, doub
       }
       continue;
     }
-    double L[NPACK_MAX], d[NMAX1], x[NMAX1], g[NMAX1], v[NMAX1], w1[NMAX1], tmp[NMAX1];
+    T L[NPACK_MAX], v[NMAX1], w1[NMAX1], tmp[NMAX1];
+    double x[NMAX1], g[NMAX1], dx[NMAX1];
+    Scale<T> sc;
+    sc.load(a.sc, q, n);
     const int npk = n * (n + 1) / 2;
-    for (int e = 0; e < npk; ++e) L[e] = a.sc.L[(int64_t)e * Q + q];
+    for (int e = 0; e < npk; ++e) L[e] = Lg[(int64_t)e * Q + q];
     double cost0 = a.sc.rt[q];
     for (int i = 0; i < n; ++i) {
       const double gii = a.sc.G[(int64_t)pk(i, i) * Q + q];
-      d[i] = 1.0 / a.sc.dinv[(int64_t)i * Q + q];
       x[i] = a.sc.x[(int64_t)i * Q + q];
       g[i] = a.sc.rt[(int64_t)(i + 1) * Q + q] - a.lam * gii * x[i];
       cost0 += a.lam * gii * x[i] * x[i];
-      v[i] = g[i] / d[i];
+      v[i] = sc.down(g[i], i);
     }
     llt_solve(L, v, n);            // v = D dx
+    for (int i = 0; i < n; ++i) dx[i] = sc.up(v[i], i);
     if (!final_step) {
-      for (int i = 0; i < n; ++i) a.sc.x[(int64_t)i * Q + q] = x[i] + v[i] / d[i];
+      for (int i = 0; i < n; ++i) a.sc.x[(int64_t)i * Q + q] = x[i] + dx[i];
       continue;
     }
     lt_mul(L, v, w1, n);           // w1 = L^T D dx
     double dg = 0.0, dmd = 0.0;
     for (int i = 0; i < n; ++i) {
-      dg += (v[i] / d[i]) * g[i];
-      dmd += w1[i] * w1[i];
+      dg += dx[i] * g[i];
+      dmd += (double)w1[i] * (double)w1[i];
     }
     double c = cost0 - 2.0 * dg + dmd;
     // The step must not raise the damped cost, whose value at x is exact: if the
@@ -143,27 +177,27 @@ __global__ void __launch_bounds__(256) k_finish(EvalArgs a, int final_step, doub
     if (!(c >= 0.0 && c <= cost0)) {
       c = cost0;
       for (int i = 0; i < n; ++i) {
-        v[i] = 0.0;
-        w1[i] = 0.0;
+        dx[i] = 0.0;
+        w1[i] = T(0);
       }
     }
     l_mul(L, w1, tmp, n);          // tmp = L L^T D dx; M dx = D tmp
     bool flipped = false;
     double e[NMAX1];
     for (int i = 0; i < n; ++i) {
-      const double x1 = x[i] + v[i] / d[i];
+      const double x1 = x[i] + dx[i];
       x[i] = x1;
-      g[i] -= d[i] * tmp[i];       // g1
+      g[i] -= sc.d[i] * (double)tmp[i];   // g1
       e[i] = (i > 0 && x1 < 0.0) ? -2.0 * x1 : 0.0;
       flipped |= (e[i] != 0.0);
     }
     if (flipped) {
-      for (int i = 0; i < n; ++i) tmp[i] = d[i] * e[i];
+      for (int i = 0; i < n; ++i) tmp[i] = (T)(sc.d[i] * e[i]);
       lt_mul(L, tmp, w1, n);
       double eg = 0.0, eme = 0.0;
       for (int i = 0; i < n; ++i) {
         eg += e[i] * g[i];
-        eme += w1[i] * w1[i];
+        eme += (double)w1[i] * (double)w1[i];
       }
       c = c - 2.0 * eg + eme;
     }
@@ -183,34 +217,38 @@ __global__ void __launch_bounds__(256) k_finish(EvalArgs a, int final_step, doub
 // ------------------------------------------------------------------ gradient
 // w = M^-1 S g_hat with g_hat = g1 - M (x_hat - x1) = h - M x_hat,
 // S = diag(1, sign x1_1, ..., sign x1_N).
+template <typename T>
 __global__ void __launch_bounds__(256) k_grad_prep(EvalArgs a, const double* g1, double* sg_out) {
   const int64_t Q = a.sc.Q;
+  const T* Lg = factor_base<T>(a.sc);
   for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
     const Unit u = a.units[ui];
     const int q = u.q0 + (int)threadIdx.x;
     if (q >= u.q1 || (a.active && !a.active[q])) continue;
     if (a.sc.fail[q]) continue;
     const int n = u.N + 1;
-    double L[NPACK_MAX], d[NMAX1], e[NMAX1], t1[NMAX1], t2[NMAX1];
+    T L[NPACK_MAX], t1[NMAX1], t2[NMAX1];
+    double e[NMAX1];
+    Scale<T> sc;
+    sc.load(a.sc, q, n);
     const int npk = n * (n + 1) / 2;
-    for (int k = 0; k < npk; ++k) L[k] = a.sc.L[(int64_t)k * Q + q];
+    for (int k = 0; k < npk; ++k) L[k] = Lg[(int64_t)k * Q + q];
     for (int i = 0; i < n; ++i) {
-      d[i] = 1.0 / a.sc.dinv[(int64_t)i * Q + q];
       const double x1 = a.sc.x[(int64_t)i * Q + q];
       e[i] = a.sc.xh[(int64_t)i * Q + q] - x1;
-      t1[i] = d[i] * e[i];
+      t1[i] = (T)(sc.d[i] * e[i]);
     }
     lt_mul(L, t1, t2, n);
     l_mul(L, t2, t1, n);           // M e = D t1
     for (int i = 0; i < n; ++i) {
       const double x1 = a.sc.x[(int64_t)i * Q + q];
-      double gh = g1[(int64_t)i * Q + q] - d[i] * t1[i];
+      double gh = g1[(int64_t)i * Q + q] - sc.d[i] * (double)t1[i];
       if (i > 0 && x1 < 0.0) gh = -gh;
       if (sg_out) sg_out[(int64_t)i * Q + q] = gh;   // S g_hat, kept for the refinement of w
-      t2[i] = gh / d[i];
+      t2[i] = sc.down(gh, i);
     }
     llt_solve(L, t2, n);
-    for (int i = 0; i < n; ++i) a.sc.w[(int64_t)i * Q + q] = t2[i] / d[i];
+    for (int i = 0; i < n; ++i) a.sc.w[(int64_t)i * Q + q] = sc.up(t2[i], i);
   }
 }
 
@@ -219,26 +257,30 @@ __global__ void __launch_bounds__(256) k_grad_prep(EvalArgs a, const double* g1,
 //   rho = S g_hat - (A^T A + lam diag G) w,  w <- w + M^-1 rho.
 // In a flipped candidate w is not small and enters the gradient to first order,
 // so the FP32 Gram's error in M^-1 must not reach it.
+template <typename T>
 __global__ void __launch_bounds__(256) k_adjoint_refine(EvalArgs a, const double* sg) {
   const int64_t Q = a.sc.Q;
+  const T* Lg = factor_base<T>(a.sc);
   for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
     const Unit u = a.units[ui];
     const int q = u.q0 + (int)threadIdx.x;
     if (q >= u.q1 || (a.active && !a.active[q])) continue;
     if (a.sc.fail[q]) continue;
     const int n = u.N + 1;
-    double L[NPACK_MAX], d[NMAX1], v[NMAX1], w[NMAX1];
+    T L[NPACK_MAX], v[NMAX1];
+    double w[NMAX1];
+    Scale<T> sc;
+    sc.load(a.sc, q, n);
     const int npk = n * (n + 1) / 2;
-    for (int k = 0; k < npk; ++k) L[k] = a.sc.L[(int64_t)k * Q + q];
+    for (int k = 0; k < npk; ++k) L[k] = Lg[(int64_t)k * Q + q];
     for (int i = 0; i < n; ++i) {
-      d[i] = 1.0 / a.sc.dinv[(int64_t)i * Q + q];
       w[i] = a.sc.w[(int64_t)i * Q + q];
       const double gii = a.sc.G[(int64_t)pk(i, i) * Q + q];
       const double rho = sg[(int64_t)i * Q + q] + a.sc.rt[(int64_t)(i + 1) * Q + q] - a.lam * gii * w[i];
-      v[i] = rho / d[i];
+      v[i] = sc.down(rho, i);
     }
     llt_solve(L, v, n);
-    for (int i = 0; i < n; ++i) a.sc.w[(int64_t)i * Q + q] = w[i] + v[i] / d[i];
+    for (int i = 0; i < n; ++i) a.sc.w[(int64_t)i * Q + q] = w[i] + sc.up(v[i], i);
   }
 }
 
@@ -290,18 +332,27 @@ static int grid_for(int n_units, int sms, int per_sm) {
   return std::max(1, std::min(n_units, sms * per_sm));
 }
 
+// The factor is FP32 when a.lf32 is set (mixed precision), FP64 otherwise.
 void launch_solve(const EvalArgs& a, int block, int sms, cudaStream_t st) {
-  if (a.n_units) k_solve<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a);
+  if (!a.n_units) return;
+  if (a.lf32) k_solve<float><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a);
+  else k_solve<double><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a);
 }
 void launch_finish(const EvalArgs& a, int final_step, double* cost, double* weights, double* g1,
                    int block, int sms, cudaStream_t st) {
-  if (a.n_units) k_finish<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, final_step, cost, weights, g1);
+  if (!a.n_units) return;
+  if (a.lf32) k_finish<float><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, final_step, cost, weights, g1);
+  else k_finish<double><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, final_step, cost, weights, g1);
 }
 void launch_grad_prep(const EvalArgs& a, const double* g1, double* sg_out, int block, int sms, cudaStream_t st) {
-  if (a.n_units) k_grad_prep<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, g1, sg_out);
+  if (!a.n_units) return;
+  if (a.lf32) k_grad_prep<float><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, g1, sg_out);
+  else k_grad_prep<double><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, g1, sg_out);
 }
 void launch_adjoint_refine(const EvalArgs& a, const double* sg, int block, int sms, cudaStream_t st) {
-  if (a.n_units) k_adjoint_refine<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, sg);
+  if (!a.n_units) return;
+  if (a.lf32) k_adjoint_refine<float><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, sg);
+  else k_adjoint_refine<double><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, sg);
 }
 void launch_grad_finish(const EvalArgs& a, double* grad, int block, int sms, cudaStream_t st) {
   if (a.n_units) k_grad_finish<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, grad);

@@ -14,22 +14,35 @@ constexpr int N_BUCKETS = NMAX;
 constexpr int MAX_BLOCK = 128; // largest pass block (candidates x lanes; mixed Gram shared memory at N = 20)
 __host__ __device__ constexpr int bucket_of(int N) { return N - 1; }
 
-// Work layout for spectra with `per_spectrum` candidates each: `cb` candidates per
-// unit and `ks` lanes per candidate, 64 threads per pass block. Full populations
-// get one lane per candidate; a handful of candidates (line-search points, one
-// re-solve per spectrum) get several lanes each so that warps stay full.
-// cb_opt > 0 fixes the candidates per unit (lanes stay 1 unless the spectrum has
-// fewer candidates than a warp).
-inline void choose_layout(int64_t per_spectrum, int cb_opt, int* cb, int* ks) {
-  int p2 = 1;
-  while (p2 < per_spectrum && p2 < 64) p2 <<= 1;
-  if (cb_opt > 0 && per_spectrum >= 32) {
-    *cb = cb_opt;
+// Work layout for spectra with `per_spectrum` candidates each, `total` in the
+// batch: `cb` candidates per unit and `ks` lanes per candidate. A population
+// that fills the GPU (about 2048 resident threads per SM) gets one lane per
+// candidate, `tuned` (debye_autotune's choice, 0 = 64) candidates per unit; a
+// smaller batch (the polish's trial steps and accepted points, the final
+// re-solve, small fits) splits each candidate over ks = 2..32 lanes, sized so
+// that the batch fills the GPU and a 64-thread block holds candidates of one
+// spectrum. `forced` > 0 (the caller's cands_per_block) fixes cb with one lane
+// per candidate whenever a spectrum has at least a warp of candidates.
+inline void choose_layout(int64_t per_spectrum, int64_t total, int sms, int forced, int tuned, int* cb,
+                          int* ks) {
+  const int64_t target = (int64_t)std::max(sms, 1) * 2048;
+  if (forced > 0 && per_spectrum >= 32) {
+    *cb = forced;
     *ks = 1;
     return;
   }
-  *ks = std::min(32, std::max(1, 64 / p2));
-  *cb = std::max(1, 64 / *ks);
+  if (per_spectrum >= 32 && 2 * total >= target) {
+    *cb = tuned > 0 ? tuned : 64;
+    *ks = 1;
+    return;
+  }
+  int p2 = 1;
+  while (p2 < per_spectrum && p2 < 64) p2 <<= 1;
+  int k = 1;
+  while (k < 32 && total * (2 * k) <= target) k <<= 1;
+  k = std::min(32, std::max(k, 64 / p2));
+  *ks = k;
+  *cb = std::max(1, 64 / k);
 }
 
 // Per-N passes (eval.cuh); pole counts 1-4, 5-8, 9-12, 13-16 and 17-20 compile in

@@ -112,7 +112,12 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
       (opt.cands_per_block < 32 || opt.cands_per_block > MAX_BLOCK || opt.cands_per_block % 32))
     return fail_msg(DEBYE_EINVAL, err, err_len, "cands_per_block");
   int cb, ks;
-  choose_layout(P, opt.cands_per_block, &cb, &ks);
+  int sms_l = 1, dev_l = 0;
+  cudaGetDevice(&dev_l);
+  cudaDeviceGetAttribute(&sms_l, cudaDevAttrMultiProcessorCount, dev_l);
+  // one lane per candidate for populations of a warp or more (as large batches get), so
+  // the number of work units stays small
+  choose_layout(P, (int64_t)1 << 40, sms_l, opt.cands_per_block, 0, &cb, &ks);
   const int64_t* offs = sp->offsets_host;
   if (offs[0] != 0) return fail_msg(DEBYE_EINVAL, err, err_len, "offsets[0] must be 0");
 
@@ -207,6 +212,7 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
   a.sc = sc;
   a.status = status;
   const bool mixed = opt.precision == DEBYE_PREC_MIXED;
+  a.lf32 = mixed ? 1 : 0;
   auto per_bucket = [&](int phase) {
     for (int b = 0; b < N_BUCKETS; ++b) {
       const int n = begin[b + 1] - begin[b];

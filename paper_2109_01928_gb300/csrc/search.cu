@@ -8,6 +8,7 @@
 //   v = (omega v + (phi_p r1) (p - x)) + (phi_g r2) (g - x),  x = clip(x + v, lo, hi).
 #include <cmath>
 
+#include "dmath.cuh"
 #include "launch.h"
 #include "search.h"
 
@@ -120,6 +121,124 @@ __global__ void k_de_trial(SwarmArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ dual annealing
+// Generalized simulated annealing chains (Tsallis and Stariolo), one per member:
+// current state in cx/ce, best state in pbx/pbc, trial states written to x for
+// evaluation. Outer iteration t (the device generation counter) has visiting
+// temperature T(t) = T0 (2^(qv-1) - 1) / ((1+t)^(qv-1) - 1) and acceptance
+// temperature T(t)/t; its Markov chain has 2N moves, move j < N displacing every
+// coordinate and move j >= N coordinate j - N, by dx = sigma(T) z1 / |z2|^a with
+// a = (qv-1)/(3-qv), sigma(T) = exp((log T - C_QV) / (3-qv)) and (z1, z2) a
+// polar-method normal pair (capped at |dx| <= 1e8), wrapped periodically into
+// [lo, hi]. A lower energy is accepted; a higher one with probability
+// [1 - (1-qa) dE / T_acc]^(1/(1-qa)) against a uniform draw. All arithmetic is
+// explicit __d*_rn and the fixed-operation log/exp, so the chains are
+// bit-identical to an FP64 implementation of the same sequence.
+constexpr double DA_QV = 2.62;
+constexpr double DA_C_QV = -0.6233798028078907;  // (qv-1) log(A/B) at qv = 2.62 (40-digit evaluation)
+constexpr double DA_TAIL = 1.0e8;
+constexpr int DA_NMAX_SLOTS = 20;                // slot stride per move (pole capacity)
+
+__device__ __forceinline__ double da_temperature(double t0, int t) {
+  const double num = __dsub_rn(dm_exp(__dmul_rn(__dsub_rn(DA_QV, 1.0), dm_log(2.0))), 1.0);
+  const double den = __dsub_rn(dm_exp(__dmul_rn(__dsub_rn(DA_QV, 1.0), dm_log(__dadd_rn((double)t, 1.0)))), 1.0);
+  return __ddiv_rn(__dmul_rn(t0, num), den);
+}
+
+// Copy the evaluated initial members into the chains' current states.
+__global__ void k_da_start(SwarmArgs a) {
+  const int64_t Q = (int64_t)a.S * a.P;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    for (int d = 0; d < a.nmax; ++d) a.cx[q * a.nmax + d] = a.pbx[q * a.nmax + d];
+    a.ce[q] = a.pbc[q];
+  }
+}
+
+__global__ void k_da_visit(SwarmArgs a, int j) {
+  const int64_t Q = (int64_t)a.S * a.P;
+  const int t = *a.gen;
+  const double T = da_temperature(a.da_t0, t);
+  const double sig = dm_exp(__ddiv_rn(__dsub_rn(dm_log(T), DA_C_QV), __dsub_rn(3.0, DA_QV)));
+  const double pw = __ddiv_rn(__dsub_rn(DA_QV, 1.0), __dsub_rn(3.0, DA_QV));
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = q / a.P;
+    const int p = (int)(q % a.P);
+    const int N = a.n_poles[s];
+    if (j >= 2 * N) {
+      a.active[q] = 0;
+      continue;
+    }
+    a.active[q] = 1;
+    const double lo = a.lo[s], hi = a.hi[s], span = __dsub_rn(hi, lo);
+    const uint64_t pv = rng_prefix(a.seed, TAG_DA_VISIT, key_id(a, s), (uint64_t)t);
+    const int d0 = j < N ? 0 : j - N, d1 = j < N ? N : j - N + 1;
+    for (int d = 0; d < a.nmax; ++d) {
+      double xv = a.cx[q * a.nmax + d];
+      if (d >= d0 && d < d1) {
+        double z1 = 0.0, z2 = 0.0;
+        for (int k = 0; k < DM_POLAR_TRIES; ++k) {
+          const uint64_t slot = ((uint64_t)(j * DA_NMAX_SLOTS + d) * DM_POLAR_TRIES + k) * 2;
+          const double u = __dsub_rn(__dmul_rn(2.0, rng_uniform(pv, (uint64_t)p, slot)), 1.0);
+          const double v = __dsub_rn(__dmul_rn(2.0, rng_uniform(pv, (uint64_t)p, slot + 1)), 1.0);
+          const double ss = __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v));
+          if (ss > 0.0 && ss < 1.0) {
+            const double f = __dsqrt_rn(__ddiv_rn(__dmul_rn(-2.0, dm_log(ss)), ss));
+            z1 = __dmul_rn(u, f);
+            z2 = __dmul_rn(v, f);
+            break;
+          }
+        }
+        const double az = fabs(z2);
+        double dx;
+        if (az > 0.0) dx = __ddiv_rn(__dmul_rn(sig, z1), dm_exp(__dmul_rn(pw, dm_log(az))));
+        else dx = copysign(DA_TAIL, z1);
+        dx = fmin(fmax(dx, -DA_TAIL), DA_TAIL);
+        xv = __dadd_rn(xv, dx);
+        if (xv < lo || xv > hi) {
+          double r = fmod(__dsub_rn(xv, lo), span);
+          if (r < 0.0) r = __dadd_rn(r, span);
+          xv = __dadd_rn(lo, r);
+        }
+      }
+      a.x[q * a.nmax + d] = xv;
+    }
+  }
+}
+
+__global__ void k_da_accept(SwarmArgs a, const double* __restrict__ cost, int j) {
+  const int64_t Q = (int64_t)a.S * a.P;
+  const int t = *a.gen;
+  const double T = da_temperature(a.da_t0, t);
+  const double t_acc = __ddiv_rn(T, (double)t);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = q / a.P;
+    const int p = (int)(q % a.P);
+    const int N = a.n_poles[s];
+    if (j >= 2 * N) continue;
+    double et = cost[q];
+    if (!isfinite(et)) et = INFINITY;
+    const double e = a.ce[q];
+    bool acc = et < e;
+    if (!acc && isfinite(et)) {
+      const double tmp = __dsub_rn(1.0, __ddiv_rn(__dmul_rn(__dsub_rn(1.0, a.da_qa), __dsub_rn(et, e)), t_acc));
+      const double pr = tmp > 0.0 ? dm_exp(__ddiv_rn(dm_log(tmp), __dsub_rn(1.0, a.da_qa))) : 0.0;
+      const double u = rng_uniform(rng_prefix(a.seed, TAG_DA_ACCEPT, key_id(a, s), (uint64_t)t), (uint64_t)p,
+                                   (uint64_t)j);
+      acc = u <= pr;
+    }
+    if (!acc) continue;
+    for (int d = 0; d < N; ++d) a.cx[q * a.nmax + d] = a.x[q * a.nmax + d];
+    a.ce[q] = et;
+    if (et < a.pbc[q]) {
+      for (int d = 0; d < N; ++d) a.pbx[q * a.nmax + d] = a.x[q * a.nmax + d];
+      a.pbc[q] = et;
+    }
+  }
+}
+
 // Lexicographic (cost, index) minimum: lowest cost, lowest index on ties.
 __device__ __forceinline__ void argmin_merge(double& c, int& i, double c2, int i2) {
   if (c2 < c || (c2 == c && i2 < i)) {
@@ -180,6 +299,25 @@ __global__ void k_pso_best(SwarmArgs a, const double* __restrict__ cost) {
       a.gbest[s] = bi < a.P ? bi : 0;
       if (a.trace) a.trace[s * (int64_t)(a.iters + 1) + gen] = bc;
       if (a.evals) atomicAdd(a.evals, (double)a.P * (double)(a.offsets[s + 1] - a.offsets[s]));
+    }
+  }
+}
+
+// After an outer iteration of dual annealing: best chain per spectrum (lowest
+// best cost, lowest index on ties), its cost in the trace, and the iteration's
+// evaluations (P chains x 2N moves x K samples) in the counter.
+__global__ void k_da_best(SwarmArgs a) {
+  const int gen = *a.gen;
+  for (int64_t s = blockIdx.x; s < a.S; s += gridDim.x) {
+    double bc = INFINITY;
+    int bi = 0x7fffffff;
+    for (int p = threadIdx.x; p < a.P; p += blockDim.x) argmin_merge(bc, bi, a.pbc[s * a.P + p], p);
+    block_argmin(bc, bi);
+    if (threadIdx.x == 0) {
+      a.gbest[s] = bi < a.P ? bi : 0;
+      if (a.trace) a.trace[s * (int64_t)(a.iters + 1) + gen] = bc;
+      if (a.evals)
+        atomicAdd(a.evals, (double)a.P * 2.0 * (double)a.n_poles[s] * (double)(a.offsets[s + 1] - a.offsets[s]));
     }
   }
 }
@@ -462,6 +600,19 @@ void launch_pso_move(const SwarmArgs& a, int sms, cudaStream_t st) {
 }
 void launch_de_trial(const SwarmArgs& a, int sms, cudaStream_t st) {
   k_de_trial<<<g1d((int64_t)a.S * a.P, sms), 256, 0, st>>>(a);
+}
+void launch_da_start(const SwarmArgs& a, int sms, cudaStream_t st) {
+  k_da_start<<<g1d((int64_t)a.S * a.P, sms), 256, 0, st>>>(a);
+}
+void launch_da_visit(const SwarmArgs& a, int j, int sms, cudaStream_t st) {
+  k_da_visit<<<g1d((int64_t)a.S * a.P, sms), 128, 0, st>>>(a, j);
+}
+void launch_da_accept(const SwarmArgs& a, const double* cost, int j, int sms, cudaStream_t st) {
+  k_da_accept<<<g1d((int64_t)a.S * a.P, sms), 256, 0, st>>>(a, cost, j);
+}
+void launch_da_best(const SwarmArgs& a, int sms, cudaStream_t st) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.S, (int64_t)sms * 8));
+  k_da_best<<<grid, 256, 0, st>>>(a);
 }
 void launch_pso_best(const SwarmArgs& a, const double* cost, int sms, cudaStream_t st) {
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.S, (int64_t)sms * 8));

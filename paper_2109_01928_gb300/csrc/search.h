@@ -11,6 +11,7 @@ struct SwarmArgs {
   double omega, phi_p, phi_g;
   double de_f_lo, de_f_hi, de_cr;  // differential evolution coefficients
   int32_t de_strategy;             // DEBYE_DE_RAND1 or DEBYE_DE_BEST1
+  double da_t0, da_qa;             // dual annealing: initial temperature, acceptance parameter
   const int32_t* n_poles;
   const double* lo;
   const double* hi;
@@ -21,6 +22,9 @@ struct SwarmArgs {
   double* pbx;     // [S*P][nmax] personal-best positions; differential evolution: the population
   double* pbc;     // [S*P]       personal-best costs; differential evolution: population costs
   int32_t* gbest;  // [S]         global-best particle
+  double* cx;      // [S*P][nmax] dual annealing: current chain states
+  double* ce;      // [S*P]       dual annealing: current energies
+  uint8_t* active; // [S*P]       dual annealing: member moved in this step (evaluation mask)
   int* gen;        // generation counter (device)
   double* trace;   // [S][iters+1] or nullptr
   double* evals;   // [1] or nullptr
@@ -56,6 +60,10 @@ struct PolishArgs {
 void launch_pso_init(const SwarmArgs& a, int sms, cudaStream_t st);
 void launch_pso_move(const SwarmArgs& a, int sms, cudaStream_t st);
 void launch_de_trial(const SwarmArgs& a, int sms, cudaStream_t st);
+void launch_da_start(const SwarmArgs& a, int sms, cudaStream_t st);
+void launch_da_visit(const SwarmArgs& a, int j, int sms, cudaStream_t st);
+void launch_da_accept(const SwarmArgs& a, const double* cost, int j, int sms, cudaStream_t st);
+void launch_da_best(const SwarmArgs& a, int sms, cudaStream_t st);
 void launch_pso_best(const SwarmArgs& a, const double* cost, int sms, cudaStream_t st);
 void launch_gen_advance(int* gen, cudaStream_t st);
 void launch_add_scalar(double* dst, double v, cudaStream_t st);

@@ -29,6 +29,7 @@ PREC_FP64 = 0
 PREC_MIXED = 1
 SEARCH_PSO = 0
 SEARCH_DE = 1
+SEARCH_DA = 2
 DE_RAND1 = 0
 DE_BEST1 = 1
 MAX_POLES = 20
@@ -49,7 +50,7 @@ class Options(ctypes.Structure):
                 ("lbfgs_max_trials", ctypes.c_int32), ("lbfgs_c1", ctypes.c_double),
                 ("cands_per_block", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
                 ("de_f_lo", ctypes.c_double), ("de_f_hi", ctypes.c_double), ("de_cr", ctypes.c_double),
-                ("de_strategy", ctypes.c_int32)]
+                ("de_strategy", ctypes.c_int32), ("da_t0", ctypes.c_double), ("da_qa", ctypes.c_double)]
 
 
 class SpectraC(ctypes.Structure):
@@ -265,7 +266,7 @@ def debye_fit_batch(h: Handle, sp: Spectra, P: int, iters: int, seed: int = 0, p
                     out=None, method: str = "pso"):
     """Whole fit of every spectrum: dict of eps_inf [S], d_eps [S, n_max], tau [S, n_max],
     final_cost [S], evals (candidate evaluations x K) and optionally trace [S, iters+1].
-    method: "pso" (particle swarm) or "de" (differential evolution)."""
+    method: "pso" (particle swarm), "de" (differential evolution) or "da" (dual annealing)."""
     import torch
     dev = sp.omega.device
     n_max = sp.n_max if n_max is None else n_max
@@ -279,7 +280,7 @@ def debye_fit_batch(h: Handle, sp: Spectra, P: int, iters: int, seed: int = 0, p
         if trace:
             out["trace"] = torch.empty((S, iters + 1), dtype=torch.float64, device=dev)
     srch = SearchC(P, iters, seed, polish_topk, polish_iters, _ptr(out.get("trace")), _ptr(out["evals"]),
-                   {"pso": SEARCH_PSO, "de": SEARCH_DE}[method])
+                   {"pso": SEARCH_PSO, "de": SEARCH_DE, "da": SEARCH_DA}[method])
     c = sp.c()
     h.check(lib().debye_fit_batch(h.ptr, ctypes.byref(c), ctypes.byref(srch), n_max, _ptr(out["eps_inf"]),
                                   _ptr(out["d_eps"]), _ptr(out["tau"]), _ptr(out["final_cost"]),
@@ -302,7 +303,7 @@ def debye_fit_auto(h: Handle, sp: Spectra, P: int, iters: int, seed: int = 0, po
            "frac_err": torch.empty(S, **f64), "n_chosen": torch.empty(S, dtype=torch.int32, device=dev),
            "evals": torch.zeros(1, **f64)}
     srch = SearchC(P, iters, seed, polish_topk, polish_iters, None, _ptr(out["evals"]),
-                   {"pso": SEARCH_PSO, "de": SEARCH_DE}[method])
+                   {"pso": SEARCH_PSO, "de": SEARCH_DE, "da": SEARCH_DA}[method])
     c = sp.c()
     h.check(lib().debye_fit_auto(h.ptr, ctypes.byref(c), ctypes.byref(srch), n_max, float(threshold), wave,
                                  _ptr(out["eps_inf"]), _ptr(out["d_eps"]), _ptr(out["tau"]),

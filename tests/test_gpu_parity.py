@@ -412,3 +412,48 @@ def test_fit_auto_single_debye_picks_one_pole(D):
         D.debye_sync(h)
     assert out["n_chosen"].item() == 1 and out["frac_err"].item() < 1.0
     assert abs(out["tau"][0, 0].item() - 1e-9) <= 1e-2 * 1e-9
+
+
+# ---------------------------------------------------------------- dual annealing
+
+def test_fit_fp64_da_trace_matches_oracle(D):
+    # visiting deviates and acceptances use fixed-operation log/exp on both sides:
+    # the chains follow the oracle's (FP64 costs agree to ~1e-12)
+    b = W.single_hn()
+    re, im = models.synthesize(b)
+    with D.Handle("fp64") as h:
+        out = D.debye_fit_batch(h, spectra_for(D, b, re, im), P=32, iters=25, seed=0, polish_topk=0,
+                                trace=True, method="da")
+        D.debye_sync(h)
+    r = fit_oracle(b, re, im, 0, 32, 25, 0, 0, method="da")
+    np.testing.assert_allclose(out["trace"].cpu().numpy()[0], r["trace"], rtol=1e-10, atol=0)
+    e_gpu = fitted(b.omega, out["eps_inf"].item(), out["d_eps"].cpu().numpy()[0], out["tau"].cpu().numpy()[0])
+    assert dls.rel_rms(e_gpu, fit.fitted_eps(b.omega, r)) <= 1e-8
+    assert out["evals"].item() == 32 * (25 * 2 * 3 + 1) * 50
+
+
+def test_fit_da_with_polish_ragged_batch(D):
+    # ragged batch (N 2-4: masked moves beyond 2 N_s), 15 outer iterations, top-4 x 20 polish, FP64
+    b = W.mixed_batch(S=4, seed=61, P=16, K_range=(50, 120), N_range=(2, 4))
+    re, im = models.synthesize(b)
+    with D.Handle("fp64") as h:
+        out = D.debye_fit_batch(h, spectra_for(D, b, re, im), P=16, iters=15, seed=5, polish_topk=4,
+                                polish_iters=20, method="da")
+        D.debye_sync(h)
+    for s in range(b.S):
+        a, c = b.offsets[s], b.offsets[s + 1]
+        r = fit_oracle(b, re, im, s, 16, 15, 4, 20, seed=5, method="da")
+        N = int(b.n_poles[s])
+        e_gpu = fitted(b.omega[a:c], out["eps_inf"][s].item(), out["d_eps"][s, :N].cpu().numpy(),
+                       out["tau"][s, :N].cpu().numpy())
+        rr = dls.rel_rms(e_gpu, fit.fitted_eps(b.omega[a:c], r))
+        gcost = out["final_cost"][s].item()
+        assert rr <= 1e-4 or gcost <= r["cost_final"] * (1 + 1e-6), (s, rr, gcost, r["cost_final"])
+
+
+def test_da_rejects_too_many_iterations(D):
+    b = W.single_hn()
+    re, im = models.synthesize(b)
+    with D.Handle("fp64") as h:
+        with pytest.raises(D.DebyeError):
+            D.debye_fit_batch(h, spectra_for(D, b, re, im), P=8, iters=1001, polish_topk=0, method="da")

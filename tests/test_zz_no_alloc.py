@@ -18,6 +18,11 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-10, "mixed": 1e-5}
+# The two entry points may split candidates over different numbers of lanes (the
+# handle path sizes the split to the batch), so sums run in different orders:
+# weights, not stationary like the cost, are compared at the oracle-parity
+# tolerance of their own scale.
+WTOL = {"fp64": 1e-7, "mixed": 2e-3}
 
 
 @pytest.fixture(scope="module")
@@ -45,7 +50,7 @@ def test_noalloc_matches_eval_population_twice(D, prec):
             err = np.abs(c.cpu().numpy() - rc) / rc
             assert err.max() <= TOL[prec], (call, err.max())
             scale = np.abs(rw).max(axis=2, keepdims=True)
-            assert (np.abs(w.cpu().numpy() - rw) / scale).max() <= TOL[prec], call
+            assert (np.abs(w.cpu().numpy() - rw) / scale).max() <= WTOL[prec], call
 
 
 def test_noalloc_rejects_batches_beyond_the_scratch(D):
