@@ -249,7 +249,8 @@ int debye_sync(debye_handle h, cudaStream_t stream);
  * Per kind the library accumulates the number of passes, the summed event time
  * (ms) and the algorithmic FLOPs of the work: per candidate and frequency sample,
  * 4N + 2(N+2)^2 for the Gram pass (basis build plus the unique Gram/right-hand-side
- * products) and 98N + 38 for the float-float residual pass (FMA counted as 2).
+ * products), 98N + 38 for the float-float residual pass and 68N for the
+ * float-float column-sum pass of cost-only mixed evaluations (FMA counted as 2).
  * Passes restricted by an activity mask (the polish line search and its accepted
  * points) are accumulated under their own *_MASKED kinds, with time but no FLOPs. */
 #define DEBYE_KERNEL_GRAM          0
@@ -260,7 +261,9 @@ int debye_sync(debye_handle h, cudaStream_t stream);
 #define DEBYE_KERNEL_GRAM_MASKED   5
 #define DEBYE_KERNEL_REFINE_MASKED 6
 #define DEBYE_KERNEL_GRAD_MASKED   7
-#define DEBYE_KERNEL_KINDS         8
+#define DEBYE_KERNEL_SUMS          8
+#define DEBYE_KERNEL_SUMS_MASKED   9
+#define DEBYE_KERNEL_KINDS         10
 
 /* Number of kernel launches the handle has enqueued (a CUDA-graph replay counts
  * each of its kernel nodes); reset != 0 sets the counter to zero afterwards. */

@@ -98,10 +98,17 @@ int debye_ctx::prof_collect() {
 // basis value, 30 for the two Dot2 residual updates, 30 for the two Dot2 updates
 // of A^T r and 5 for the exact column norm; per sample 38 (target split,
 // renormalisation, ||r||^2 and the eps_inf column).
-static double flops_per_cand_k(int kind, int N) {
-  if (kind == DEBYE_KERNEL_GRAM) return 4.0 * N + 2.0 * (N + 2) * (N + 2);
-  if (kind == DEBYE_KERNEL_REFINE) return 98.0 * N + 38.0;
+static double flops_per_cand_k(int phase, int N) {
+  if (phase == PH_GRAM) return 4.0 * N + 2.0 * (N + 2) * (N + 2);
+  if (phase == PH_REFINE) return 98.0 * N + 38.0;
+  if (phase == PH_SUMS) return 68.0 * N;
   return 0.0;
+}
+
+// Profiling kind of a pass of `phase`, restricted by an activity mask or not.
+static int pass_kind(int phase, bool masked) {
+  if (phase == PH_SUMS) return masked ? DEBYE_KERNEL_SUMS_MASKED : DEBYE_KERNEL_SUMS;
+  return masked ? DEBYE_KERNEL_GRAM_MASKED + phase : phase;
 }
 
 // ------------------------------------------------------------------ spectra plan
@@ -149,7 +156,7 @@ int debye_ctx::prep_spectra(const debye_spectra* sp, const Plan& pl, cudaStream_
   int rc;
   if ((rc = ensure(ws_kf32, sizeof(float4) * std::max<int64_t>(pl.n_samples, 1), "kf32"))) return rc;
   if ((rc = ensure(ws_kff, sizeof(float4) * std::max<int64_t>(pl.n_samples, 1), "kff"))) return rc;
-  if ((rc = ensure(ws_h0, sizeof(double) * std::max<int64_t>(pl.S, 1), "h0"))) return rc;
+  if ((rc = ensure(ws_h0, sizeof(double) * 2 * std::max<int64_t>(pl.S, 1), "h0"))) return rc;
   launch_prep(pl.n_samples, pl.S, sp->offsets, sp->omega, sp->eps_re, sp->eps_im, sp->lo, sp->hi,
               (float4*)ws_kf32.p, (float4*)ws_kff.p, (double*)ws_h0.p, d_status, sms, st);
   launches += (pl.n_samples > 0) + (pl.S > 0);
@@ -252,7 +259,7 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
       if (!a.active)
         for (const Unit& x : g.units)
           fl += (double)(x.q1 - x.q0) * (double)(x.k1 - x.k0) * flops_per_cand_k(phase, x.N);
-      prof_begin(a.active ? DEBYE_KERNEL_GRAM_MASKED + phase : phase, fl, st, pe);
+      prof_begin(pass_kind(phase, a.active != nullptr), fl, st, pe);
     }
     const bool fork = n_nonempty > 1;
     if (fork) cudaEventRecord(ev_fork, st);
@@ -296,6 +303,13 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
   if (a.ks < 1 || a.ks > 32 || (a.ks & (a.ks - 1)) || cb * a.ks > MAX_BLOCK)
     return fail(DEBYE_EINTERNAL, "bad work layout (%d candidates x %d lanes)", cb, a.ks);
   const int gblock = warp_round(cb);
+  if (mixed && !grad && a.bb) {
+    // cost only: one float-float column-sum pass, then weights and cost from the
+    // exact Gram identity of the Debye columns (k_solve_sums)
+    if ((rc = per_bucket(PH_SUMS))) return rc;
+    timed(DEBYE_KERNEL_SOLVE, [&] { launch_solve_sums(a, cost, weights, gblock, sms, st); });
+    return check_launch("column-sum solve");
+  }
   if ((rc = per_bucket(PH_GRAM))) return rc;
   timed(DEBYE_KERNEL_SOLVE, [&] { launch_solve(a, gblock, sms, st); });
   if ((rc = check_launch("solve"))) return rc;
@@ -364,6 +378,7 @@ static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_
   a.eps_re = sp->eps_re;
   a.eps_im = sp->eps_im;
   a.h0 = (const double*)h->ws_h0.p;
+  a.bb = a.h0 + pl.S;
   a.active = nullptr;
   a.ks = ks;
   a.lam = h->opt.lam_search;

@@ -21,7 +21,7 @@ constexpr int NPACK_MAX = NMAX1 * (NMAX1 + 1) / 2;
 // Packed lower-triangular index of (I, J), J <= I.
 __host__ __device__ constexpr int pk(int I, int J) { return I * (I + 1) / 2 + J; }
 
-enum Phase { PH_GRAM = 0, PH_REFINE = 1, PH_GRAD = 2 };
+enum Phase { PH_GRAM = 0, PH_REFINE = 1, PH_GRAD = 2, PH_SUMS = 3 };
 
 struct Unit {
   int32_t s;    // spectrum
@@ -58,6 +58,7 @@ struct EvalArgs {
   const double* eps_re;
   const double* eps_im;
   const double* h0;        // [S] sum_k eps'_k
+  const double* bb;        // [S] b^T b = sum_k eps'_k^2 + eps''_k^2
   const uint8_t* active;   // [Q] optional candidate mask (nullptr: all)
   int32_t ks;              // lanes per candidate in the pass kernels (power of two <= 32)
   int32_t zero_b;          // residual pass against b = 0 (t = -A^T A x), for the adjoint refinement
@@ -152,6 +153,42 @@ __device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, f
   ph = __fmul_rn(ah, bh);
   pl = __fmaf_rn(ah, bh, -ph);
   pl = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, pl));
+}
+
+// Float-float value (hi + lo, |lo| <= ulp(hi)/2 after normalisation) for the
+// per-candidate small-system algebra of the mixed path.
+struct ff {
+  float h, l;
+};
+__device__ __forceinline__ ff ff_of(double v) {
+  ff r;
+  r.h = __double2float_rn(v);
+  r.l = __double2float_rn(v - (double)r.h);
+  return r;
+}
+__device__ __forceinline__ double ff_dbl(ff a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ ff ff_sum(ff a, ff b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  const float h = __fadd_rn(s, e);
+  return ff{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.h, -a.l}; }
+__device__ __forceinline__ ff ff_prod(ff a, ff b) {
+  float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+  const float h = __fadd_rn(p, e);
+  return ff{h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+// a / b: quotient q1 = a_h / b_h corrected by the float-float remainder a - q1 b.
+__device__ __forceinline__ ff ff_quot(ff a, ff b) {
+  const float q1 = __fdiv_rn(a.h, b.h);
+  const ff r = ff_sum(a, ff_neg(ff_prod(ff{q1, 0.f}, b)));
+  const float q2 = __fdiv_rn(r.h, b.h);
+  const float h = __fadd_rn(q1, q2);
+  return ff{h, __fsub_rn(q2, __fsub_rn(h, q1))};
 }
 
 // (hi, lo) renormalised so that hi = fl(hi + lo) (Fast2Sum, |hi| >= |lo|).

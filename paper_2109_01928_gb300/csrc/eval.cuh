@@ -478,6 +478,64 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
   }
 }
 
+// ------------------------------------------------------------------ column-sum pass (mixed, cost only)
+// For the cost-only mixed evaluation (k_solve_sums): per candidate, in float-float,
+//   S_i = sum_k re_i(k)                      (the pole block of the Gram follows from these)
+//   h_i = sum_k re_i(k) eps'_k + im_i(k) eps''_k   (A^T b without the eps_inf row)
+// over the float-float basis. Writes sc.G[i Q + q] = S_i and sc.G[(N + i) Q + q] = h_i.
+// S_i is summed from 1 (re <= 1, so Fast2Sum is exact) and the bias removed at the end.
+template <int N>
+__device__ __forceinline__ void sums_unit(const EvalArgs& a, const Unit& u) {
+  const Lane ln = lane_of(a, u, false);
+  const int q = ln.act ? ln.q : u.q0;
+  const double* th = a.theta + (int64_t)q * a.sc.nmax;
+  const int64_t Q = a.sc.Q;
+  const int64_t kbeg = u.k0 + ln.slice;
+  const int64_t kend = ln.act ? u.k1 : kbeg;
+  const int64_t step = ln.ks;
+  float th_[N], tl_[N], sh[N], sl[N], hh[N], hl[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    th_[i] = tl_[i] = 0.f;
+    if (ln.act) split_double(exp10(th[i]), th_[i], tl_[i]);
+    sh[i] = 1.f;
+    sl[i] = hh[i] = hl[i] = 0.f;
+  }
+  const int64_t k0s = kbeg < u.k1 ? kbeg : u.k0;
+  float4 vhn = __ldg(&a.kf32[k0s]), vln = __ldg(&a.kff[k0s]);
+#pragma unroll 1
+  for (int64_t k = kbeg; k < kend; k += step) {
+    const float4 vh = vhn, vl = vln;
+    if (k + step < kend) {   // next sample in flight during this one
+      vhn = __ldg(&a.kf32[k + step]);
+      vln = __ldg(&a.kff[k + step]);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float reh, rel, imh, iml, xh;
+      basis_ff(vh.x, vl.x, th_[i], tl_[i], reh, rel, imh, iml, xh);
+      const float gs = __fadd_rn(sh[i], reh);                        // Fast2Sum, sh >= 1 >= reh
+      sl[i] = __fadd_rn(sl[i], __fadd_rn(__fsub_rn(reh, __fsub_rn(gs, sh[i])), rel));
+      sh[i] = gs;
+      ff_add_prod(hh[i], hl[i], reh, rel, vh.y, vl.y);
+      ff_add_prod(hh[i], hl[i], imh, iml, vh.z, vl.z);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    group_sum_ff(sh[i], sl[i], ln.ks);
+    group_sum_ff(hh[i], hl[i], ln.ks);
+  }
+  if (ln.act && ln.slice == 0) {
+    double* G = a.sc.G;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      G[(int64_t)i * Q + q] = ((double)sh[i] - (double)ln.ks) + (double)sl[i];
+      G[(int64_t)(N + i) * Q + q] = (double)hh[i] + (double)hl[i];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ gradient pass
 // With x1 (unflipped, sc.x), x_hat (flipped, sc.xh) and w = M^-1 S g_hat (sc.w):
 //   gt[i]        = a_i'^T r_hat,  r_hat = b - A x_hat
@@ -668,6 +726,7 @@ template <int PH, int N, bool MIXED>
 __device__ __forceinline__ void run_phase(const EvalArgs& a, const Unit& u) {
   if constexpr (PH == PH_GRAM) gram_unit<N, MIXED>(a, u);
   else if constexpr (PH == PH_REFINE) refine_unit<N, MIXED>(a, u);
+  else if constexpr (PH == PH_SUMS) sums_unit<N>(a, u);
   else grad_unit<N, MIXED>(a, u);
 }
 

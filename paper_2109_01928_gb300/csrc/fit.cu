@@ -159,6 +159,7 @@ int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, in
   ea.eps_re = sp->eps_re;
   ea.eps_im = sp->eps_im;
   ea.h0 = (const double*)h->ws_h0.p;
+  ea.bb = ea.h0 + pl.S;
   ea.lam = h->opt.lam_search;
   ea.ks = ks;
   ea.status = h->d_status;

@@ -28,22 +28,36 @@ __global__ void k_prep_samples(int64_t n, const double* __restrict__ omega,
 }
 
 __global__ void k_prep_spectra(int64_t S, const int64_t* __restrict__ offsets,
-                               const double* __restrict__ er, const double* __restrict__ lo,
-                               const double* __restrict__ hi, double* __restrict__ h0,
-                               int* status) {
-  __shared__ double red[32];
+                               const double* __restrict__ er, const double* __restrict__ ei,
+                               const double* __restrict__ lo, const double* __restrict__ hi,
+                               double* __restrict__ h0, double* __restrict__ bb, int* status) {
+  __shared__ double red[32], red2[32];
   for (int64_t s = blockIdx.x; s < S; s += gridDim.x) {
     const int64_t a = offsets[s], b = offsets[s + 1];
-    double acc = 0.0;
-    for (int64_t k = a + threadIdx.x; k < b; k += blockDim.x) acc += er[k];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    double acc = 0.0, acc2 = 0.0;
+    for (int64_t k = a + threadIdx.x; k < b; k += blockDim.x) {
+      acc += er[k];
+      acc2 = fma(er[k], er[k], fma(ei[k], ei[k], acc2));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      acc += __shfl_down_sync(0xffffffffu, acc, o);
+      acc2 += __shfl_down_sync(0xffffffffu, acc2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[threadIdx.x >> 5] = acc;
+      red2[threadIdx.x >> 5] = acc2;
+    }
     __syncthreads();
     if (threadIdx.x < 32) {
       acc = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      acc2 = (threadIdx.x < (blockDim.x >> 5)) ? red2[threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_down_sync(0xffffffffu, acc, o);
+        acc2 += __shfl_down_sync(0xffffffffu, acc2, o);
+      }
       if (threadIdx.x == 0) {
         h0[s] = acc;
+        bb[s] = acc2;
         if (!(lo[s] < hi[s]) || !isfinite(lo[s]) || !isfinite(hi[s])) set_status(status, DEBYE_EBOUNDS);
       }
     }
@@ -214,6 +228,110 @@ __global__ void __launch_bounds__(256) k_finish(EvalArgs a, int final_step, doub
   }
 }
 
+// ------------------------------------------------------------------ cost from column sums (mixed)
+// For the Debye columns c_i = 1/(1 + j w tau_i), partial fractions give
+//   Re(c_i conj c_j) = (tau_i Re c_i + tau_j Re c_j) / (tau_i + tau_j),
+// so the pole block of the Gram follows from the column sums S_i = sum_k re_i(k):
+//   G_ij = (tau_i S_i + tau_j S_j) / (tau_i + tau_j),  G_ii = S_i  (re^2 + im^2 = re),
+// and G_0i = S_i, G_00 = K for the eps_inf column. With h = A^T b and b^T b, the
+// damped weights solve M x = h (M = G + lam diag G), and for the flipped x_hat
+//   cost(x_hat) = b^T b - 2 x_hat^T h + x_hat^T M x_hat
+// exactly. M, h, b^T b and the products with M are float-float (the subtraction
+// loses the digits of b^T b / cost, about 4: float-float keeps ~9 of the ~13
+// digits it carries); x comes from an FP32 Cholesky factor of the scaled M and
+// two refinement steps with the float-float residual h - M x.
+constexpr int SUMS_REFINE = 2;
+
+__device__ __forceinline__ ff gram_ff(int i, int j, const ff* tau, const ff* S, ff kk) {
+  if (i == 0 && j == 0) return kk;
+  if (i == 0) return S[j - 1];
+  if (j == 0 || i == j) return S[i - 1];
+  const ff num = ff_sum(ff_prod(tau[i - 1], S[i - 1]), ff_prod(tau[j - 1], S[j - 1]));
+  return ff_quot(num, ff_sum(tau[i - 1], tau[j - 1]));
+}
+
+// (M v)_i in float-float, M = G + lam diag G.
+__device__ __forceinline__ void mvec_ff(int n, const ff* tau, const ff* S, ff kk, ff one_lam, const ff* v,
+                                        ff* out) {
+  for (int i = 0; i < n; ++i) {
+    ff acc{0.f, 0.f};
+    for (int j = 0; j < n; ++j) {
+      ff g = gram_ff(i, j, tau, S, kk);
+      if (i == j) g = ff_prod(g, one_lam);
+      acc = ff_sum(acc, ff_prod(g, v[j]));
+    }
+    out[i] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_solve_sums(EvalArgs a, double* cost, double* weights) {
+  const int64_t Q = a.sc.Q;
+  const int nm1 = a.sc.nmax + 1;
+  for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
+    const Unit u = a.units[ui];
+    const int q = u.q0 + (int)threadIdx.x;
+    if (q >= u.q1 || (a.active && !a.active[q])) continue;
+    const int N = u.N, n = N + 1;
+    ff tau[NMAX], S[NMAX], hv[NMAX1], x[NMAX1], r[NMAX1];
+    float L[NPACK_MAX], d[NMAX1], v[NMAX1];
+    for (int i = 0; i < N; ++i) {
+      tau[i] = ff_of(exp10(a.theta[(int64_t)q * a.sc.nmax + i]));
+      S[i] = ff_of(a.sc.G[(int64_t)i * Q + q]);
+      hv[i + 1] = ff_of(a.sc.G[(int64_t)(N + i) * Q + q]);
+    }
+    hv[0] = ff_of(a.h0[u.s]);
+    const ff kk = ff_of((double)(u.k1 - u.k0));
+    const ff one_lam = ff_of(1.0 + a.lam);
+    // FP32 Cholesky of the Marquardt-scaled damped matrix (unit diagonal + lam)
+    for (int i = 0; i < n; ++i) d[i] = __fsqrt_rn(gram_ff(i, i, tau, S, kk).h);
+    for (int i = 0; i < n; ++i) {
+      for (int j = 0; j < i; ++j) L[pk(i, j)] = __fdiv_rn(gram_ff(i, j, tau, S, kk).h, __fmul_rn(d[i], d[j]));
+      L[pk(i, i)] = (float)(1.0 + a.lam);
+    }
+    bool ok = cholesky_packed(L, n);
+    if (ok) {
+      for (int i = 0; i < n; ++i) x[i] = ff{0.f, 0.f};
+      for (int it = 0; it <= SUMS_REFINE && ok; ++it) {
+        // r = h - M x (the first step has x = 0), dx = M^-1 r through the FP32 factor
+        if (it == 0) {
+          for (int i = 0; i < n; ++i) r[i] = hv[i];
+        } else {
+          mvec_ff(n, tau, S, kk, one_lam, x, r);
+          for (int i = 0; i < n; ++i) r[i] = ff_sum(hv[i], ff_neg(r[i]));
+        }
+        for (int i = 0; i < n; ++i) v[i] = __fdiv_rn(r[i].h, d[i]);
+        llt_solve(L, v, n);
+        for (int i = 0; i < n; ++i) {
+          x[i] = ff_sum(x[i], ff{__fdiv_rn(v[i], d[i]), 0.f});
+          ok = ok && isfinite(x[i].h);
+        }
+      }
+    }
+    a.sc.fail[q] = ok ? 0 : 1;
+    if (!ok) {
+      if (cost) cost[q] = INFINITY;
+      if (weights)
+        for (int j = 0; j < nm1; ++j) weights[(int64_t)q * nm1 + j] = 0.0;
+      continue;
+    }
+    // sign flip of negative d_eps (Sec. III-B), then the exact quadratic cost
+    for (int i = 1; i < n; ++i)
+      if (x[i].h < 0.f) x[i] = ff_neg(x[i]);
+    mvec_ff(n, tau, S, kk, one_lam, x, r);
+    ff c = ff_of(a.bb[u.s]);
+    for (int i = 0; i < n; ++i) {
+      c = ff_sum(c, ff_neg(ff_prod(ff{__fmul_rn(2.f, x[i].h), __fmul_rn(2.f, x[i].l)}, hv[i])));
+      c = ff_sum(c, ff_prod(x[i], r[i]));
+    }
+    double cv = ff_dbl(c);
+    if (!isfinite(cv)) cv = INFINITY;
+    if (cv < 0.0) cv = 0.0;
+    if (cost) cost[q] = cv;
+    if (weights)
+      for (int j = 0; j < nm1; ++j) weights[(int64_t)q * nm1 + j] = j < n ? ff_dbl(x[j]) : 0.0;
+  }
+}
+
 // ------------------------------------------------------------------ gradient
 // w = M^-1 S g_hat with g_hat = g1 - M (x_hat - x1) = h - M x_hat,
 // S = diag(1, sign x1_1, ..., sign x1_N).
@@ -324,12 +442,16 @@ void launch_prep(int64_t n_samples, int64_t S, const int64_t* offsets, const dou
   }
   if (S > 0) {
     int grid = (int)std::min<int64_t>(S, (int64_t)sms * 8);
-    k_prep_spectra<<<grid, 256, 0, st>>>(S, offsets, er, lo, hi, h0, status);
+    k_prep_spectra<<<grid, 256, 0, st>>>(S, offsets, er, ei, lo, hi, h0, h0 + S, status);
   }
 }
 
 static int grid_for(int n_units, int sms, int per_sm) {
   return std::max(1, std::min(n_units, sms * per_sm));
+}
+
+void launch_solve_sums(const EvalArgs& a, double* cost, double* weights, int block, int sms, cudaStream_t st) {
+  if (a.n_units) k_solve_sums<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, cost, weights);
 }
 
 // The factor is FP32 when a.lf32 is set (mixed precision), FP64 otherwise.

@@ -159,7 +159,7 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
   Unit* d_units = (Unit*)cv.take(sizeof(Unit) * n_units);
   float4* kf32 = (float4*)cv.take(sizeof(float4) * n_samples);
   float4* kff = (float4*)cv.take(sizeof(float4) * n_samples);
-  double* h0 = (double*)cv.take(sizeof(double) * S);
+  double* h0 = (double*)cv.take(sizeof(double) * 2 * S);   // sum eps', then b^T b
   Scratch sc{};
   sc.Q = Q;
   sc.nmax = n_max;
@@ -206,6 +206,7 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
   a.eps_re = sp->eps_re;
   a.eps_im = sp->eps_im;
   a.h0 = h0;
+  a.bb = h0 + S;
   a.active = nullptr;
   a.ks = ks;
   a.lam = opt.lam_search;
@@ -225,11 +226,17 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
       launch_pass(b + 1, phase, mixed, ab, grid, cb * ks, st);
     }
   };
-  per_bucket(PH_GRAM);
-  launch_solve(a, warp_round(cb), sms, st);
-  for (int it = 0; it < opt.refine_steps; ++it) {
-    per_bucket(PH_REFINE);
-    launch_finish(a, it + 1 == opt.refine_steps ? 1 : 0, cost, weights, g1, warp_round(cb), sms, st);
+  if (mixed) {
+    // one float-float column-sum pass, weights and cost from the exact Gram identity
+    per_bucket(PH_SUMS);
+    launch_solve_sums(a, cost, weights, warp_round(cb), sms, st);
+  } else {
+    per_bucket(PH_GRAM);
+    launch_solve(a, warp_round(cb), sms, st);
+    for (int it = 0; it < opt.refine_steps; ++it) {
+      per_bucket(PH_REFINE);
+      launch_finish(a, it + 1 == opt.refine_steps ? 1 : 0, cost, weights, g1, warp_round(cb), sms, st);
+    }
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail_msg(DEBYE_ECUDA, err, err_len, cudaGetErrorString(e));

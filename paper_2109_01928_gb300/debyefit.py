@@ -317,7 +317,7 @@ def debye_sync(h: Handle, stream=None):
 
 
 KERNEL_KINDS = {"gram": 0, "refine": 1, "grad": 2, "solve": 3, "finish": 4, "gram_masked": 5,
-                "refine_masked": 6, "grad_masked": 7}
+                "refine_masked": 6, "grad_masked": 7, "sums": 8, "sums_masked": 9}
 
 
 def debye_eval_population_noalloc(sp: Spectra, theta, precision: str = "mixed", weights: bool = False,
