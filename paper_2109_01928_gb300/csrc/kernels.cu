@@ -250,17 +250,19 @@ __device__ __forceinline__ ff gram_ff(int i, int j, const ff* tau, const ff* S, 
   return ff_quot(num, ff_sum(tau[i - 1], tau[j - 1]));
 }
 
-// (M v)_i in float-float, M = G + lam diag G.
+// (M v)_i in float-float, M = G + lam diag G. Every entry is formed where it is
+// used (once per product, serving both of its rows) rather than kept per
+// candidate: the kernel is bound by latency and local memory, not arithmetic.
 __device__ __forceinline__ void mvec_ff(int n, const ff* tau, const ff* S, ff kk, ff one_lam, const ff* v,
                                         ff* out) {
+  for (int i = 0; i < n; ++i) out[i] = ff{0.f, 0.f};
   for (int i = 0; i < n; ++i) {
-    ff acc{0.f, 0.f};
-    for (int j = 0; j < n; ++j) {
-      ff g = gram_ff(i, j, tau, S, kk);
-      if (i == j) g = ff_prod(g, one_lam);
-      acc = ff_sum(acc, ff_prod(g, v[j]));
+    for (int j = 0; j < i; ++j) {
+      const ff g = gram_ff(i, j, tau, S, kk);
+      out[i] = ff_sum(out[i], ff_prod(g, v[j]));
+      out[j] = ff_sum(out[j], ff_prod(g, v[i]));
     }
-    out[i] = acc;
+    out[i] = ff_sum(out[i], ff_prod(ff_prod(gram_ff(i, i, tau, S, kk), one_lam), v[i]));
   }
 }
 
@@ -450,8 +452,10 @@ static int grid_for(int n_units, int sms, int per_sm) {
   return std::max(1, std::min(n_units, sms * per_sm));
 }
 
+// One thread per candidate with per-thread arrays in local memory: a grid of up to
+// 32 blocks per SM keeps enough warps resident to hide that memory's latency.
 void launch_solve_sums(const EvalArgs& a, double* cost, double* weights, int block, int sms, cudaStream_t st) {
-  if (a.n_units) k_solve_sums<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, cost, weights);
+  if (a.n_units) k_solve_sums<<<grid_for(a.n_units, sms, 32), block, 0, st>>>(a, cost, weights);
 }
 
 // The factor is FP32 when a.lf32 is set (mixed precision), FP64 otherwise.
