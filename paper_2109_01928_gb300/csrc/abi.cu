@@ -102,12 +102,13 @@ static double flops_per_cand_k(int phase, int N) {
   if (phase == PH_GRAM) return 4.0 * N + 2.0 * (N + 2) * (N + 2);
   if (phase == PH_REFINE) return 98.0 * N + 38.0;
   if (phase == PH_SUMS) return 68.0 * N;
+  if (phase == PH_SUMSG) return 152.0 * N;
   return 0.0;
 }
 
 // Profiling kind of a pass of `phase`, restricted by an activity mask or not.
 static int pass_kind(int phase, bool masked) {
-  if (phase == PH_SUMS) return masked ? DEBYE_KERNEL_SUMS_MASKED : DEBYE_KERNEL_SUMS;
+  if (phase == PH_SUMS || phase == PH_SUMSG) return masked ? DEBYE_KERNEL_SUMS_MASKED : DEBYE_KERNEL_SUMS;
   return masked ? DEBYE_KERNEL_GRAM_MASKED + phase : phase;
 }
 
@@ -303,11 +304,12 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
   if (a.ks < 1 || a.ks > 32 || (a.ks & (a.ks - 1)) || cb * a.ks > MAX_BLOCK)
     return fail(DEBYE_EINTERNAL, "bad work layout (%d candidates x %d lanes)", cb, a.ks);
   const int gblock = warp_round(cb);
-  if (mixed && !grad && a.bb) {
-    // cost only: one float-float column-sum pass, then weights and cost from the
-    // exact Gram identity of the Debye columns (k_solve_sums)
-    if ((rc = per_bucket(PH_SUMS))) return rc;
-    timed(DEBYE_KERNEL_SOLVE, [&] { launch_solve_sums(a, cost, weights, gblock, sms, st); });
+  if (mixed && a.bb) {
+    // one float-float column-sum pass (with the derivative sums when the gradient is
+    // wanted), then weights, cost and gradient from the exact Gram identity of the
+    // Debye columns (k_solve_sums)
+    if ((rc = per_bucket(grad ? PH_SUMSG : PH_SUMS))) return rc;
+    timed(DEBYE_KERNEL_SOLVE, [&] { launch_solve_sums(a, cost, weights, grad, gblock, sms, st); });
     return check_launch("column-sum solve");
   }
   if ((rc = per_bucket(PH_GRAM))) return rc;

@@ -21,7 +21,7 @@ constexpr int NPACK_MAX = NMAX1 * (NMAX1 + 1) / 2;
 // Packed lower-triangular index of (I, J), J <= I.
 __host__ __device__ constexpr int pk(int I, int J) { return I * (I + 1) / 2 + J; }
 
-enum Phase { PH_GRAM = 0, PH_REFINE = 1, PH_GRAD = 2, PH_SUMS = 3 };
+enum Phase { PH_GRAM = 0, PH_REFINE = 1, PH_GRAD = 2, PH_SUMS = 3, PH_SUMSG = 4 };
 
 struct Unit {
   int32_t s;    // spectrum

@@ -478,13 +478,20 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
   }
 }
 
-// ------------------------------------------------------------------ column-sum pass (mixed, cost only)
-// For the cost-only mixed evaluation (k_solve_sums): per candidate, in float-float,
+// ------------------------------------------------------------------ column-sum pass (mixed)
+// For the mixed evaluation from column sums (k_solve_sums): per candidate, in
+// float-float,
 //   S_i = sum_k re_i(k)                      (the pole block of the Gram follows from these)
 //   h_i = sum_k re_i(k) eps'_k + im_i(k) eps''_k   (A^T b without the eps_inf row)
-// over the float-float basis. Writes sc.G[i Q + q] = S_i and sc.G[(N + i) Q + q] = h_i.
-// S_i is summed from 1 (re <= 1, so Fast2Sum is exact) and the bias removed at the end.
-template <int N>
+// and, with the gradient (GRAD), the same sums over the derivative columns
+// d/d theta_i (theta = log10 tau; via im = x re: d re = -2 ln10 im^2,
+// d im = ln10 im (re - x im)):
+//   D_i = sum_k d re_i(k),   E_i = sum_k d re_i(k) eps'_k + d im_i(k) eps''_k.
+// Writes sc.G[i Q + q] = S_i, sc.G[(N + i) Q + q] = h_i, and with GRAD
+// sc.G[(2N + i) Q + q] = D_i, sc.G[(3N + i) Q + q] = E_i. The same-sign sums S
+// (re <= 1) and -D (<= ln10 / 2) start from a bias (1, 2) so that Fast2Sum is
+// exact; the bias is removed at the end.
+template <int N, bool GRAD>
 __device__ __forceinline__ void sums_unit(const EvalArgs& a, const Unit& u) {
   const Lane ln = lane_of(a, u, false);
   const int q = ln.act ? ln.q : u.q0;
@@ -493,13 +500,22 @@ __device__ __forceinline__ void sums_unit(const EvalArgs& a, const Unit& u) {
   const int64_t kbeg = u.k0 + ln.slice;
   const int64_t kend = ln.act ? u.k1 : kbeg;
   const int64_t step = ln.ks;
+  constexpr float LN10H = 2.3025851249694824f;   // fl(ln 10)
+  constexpr float LN10L = -3.1975436e-08f;       // ln 10 - fl(ln 10)
+  constexpr int NG = GRAD ? N : 1;
   float th_[N], tl_[N], sh[N], sl[N], hh[N], hl[N];
+  float dh[NG], dl[NG], eh[NG], el[NG];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     th_[i] = tl_[i] = 0.f;
     if (ln.act) split_double(exp10(th[i]), th_[i], tl_[i]);
     sh[i] = 1.f;
     sl[i] = hh[i] = hl[i] = 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < NG; ++i) {
+    dh[i] = 2.f;
+    dl[i] = eh[i] = el[i] = 0.f;
   }
   const int64_t k0s = kbeg < u.k1 ? kbeg : u.k0;
   float4 vhn = __ldg(&a.kf32[k0s]), vln = __ldg(&a.kff[k0s]);
@@ -519,6 +535,24 @@ __device__ __forceinline__ void sums_unit(const EvalArgs& a, const Unit& u) {
       sh[i] = gs;
       ff_add_prod(hh[i], hl[i], reh, rel, vh.y, vl.y);
       ff_add_prod(hh[i], hl[i], imh, iml, vh.z, vl.z);
+      if constexpr (GRAD) {
+        // x = w tau in float-float (basis_ff returned only its leading part)
+        float xl_ = __fmaf_rn(vh.x, th_[i], -xh);
+        xl_ = __fmaf_rn(vh.x, tl_[i], __fmaf_rn(vl.x, th_[i], xl_));
+        float s2h, s2l, ndh, ndl, ph, pl, dmh, dml, dih, dil;
+        ff_mul(imh, iml, imh, iml, s2h, s2l);                        // im^2
+        ff_mul(s2h, s2l, 2.0f * LN10H, 2.0f * LN10L, ndh, ndl);      // -d re / d theta >= 0
+        const float gd = __fadd_rn(dh[i], ndh);                      // Fast2Sum, dh >= 2 > ndh
+        dl[i] = __fadd_rn(dl[i], __fadd_rn(__fsub_rn(ndh, __fsub_rn(gd, dh[i])), ndl));
+        dh[i] = gd;
+        ff_mul(xh, xl_, imh, iml, ph, pl);                           // x im
+        two_sum(reh, -ph, dmh, dml);                                 // re - x im
+        dml = __fadd_rn(dml, __fsub_rn(rel, pl));
+        ff_mul(imh, iml, dmh, dml, ph, pl);
+        ff_mul(ph, pl, LN10H, LN10L, dih, dil);                      // d im / d theta
+        ff_add_prod(eh[i], el[i], -ndh, -ndl, vh.y, vl.y);
+        ff_add_prod(eh[i], el[i], dih, dil, vh.z, vl.z);
+      }
     }
   }
 #pragma unroll
@@ -526,12 +560,26 @@ __device__ __forceinline__ void sums_unit(const EvalArgs& a, const Unit& u) {
     group_sum_ff(sh[i], sl[i], ln.ks);
     group_sum_ff(hh[i], hl[i], ln.ks);
   }
+#pragma unroll
+  for (int i = 0; i < NG; ++i) {
+    if constexpr (GRAD) {
+      group_sum_ff(dh[i], dl[i], ln.ks);
+      group_sum_ff(eh[i], el[i], ln.ks);
+    }
+  }
   if (ln.act && ln.slice == 0) {
     double* G = a.sc.G;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       G[(int64_t)i * Q + q] = ((double)sh[i] - (double)ln.ks) + (double)sl[i];
       G[(int64_t)(N + i) * Q + q] = (double)hh[i] + (double)hl[i];
+    }
+    if constexpr (GRAD) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        G[(int64_t)(2 * N + i) * Q + q] = -(((double)dh[i] - 2.0 * (double)ln.ks) + (double)dl[i]);
+        G[(int64_t)(3 * N + i) * Q + q] = (double)eh[i] + (double)el[i];
+      }
     }
   }
 }
@@ -726,7 +774,8 @@ template <int PH, int N, bool MIXED>
 __device__ __forceinline__ void run_phase(const EvalArgs& a, const Unit& u) {
   if constexpr (PH == PH_GRAM) gram_unit<N, MIXED>(a, u);
   else if constexpr (PH == PH_REFINE) refine_unit<N, MIXED>(a, u);
-  else if constexpr (PH == PH_SUMS) sums_unit<N>(a, u);
+  else if constexpr (PH == PH_SUMS) sums_unit<N, false>(a, u);
+  else if constexpr (PH == PH_SUMSG) sums_unit<N, true>(a, u);
   else grad_unit<N, MIXED>(a, u);
 }
 

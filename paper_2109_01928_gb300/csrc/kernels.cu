@@ -266,9 +266,42 @@ __device__ __forceinline__ void mvec_ff(int n, const ff* tau, const ff* S, ff kk
   }
 }
 
-__global__ void __launch_bounds__(256) k_solve_sums(EvalArgs a, double* cost, double* weights) {
+// M^-1 rhs refined twice against the float-float M (FP32 factor L of the scaled M).
+__device__ __forceinline__ bool refined_solve(int n, const float* L, const float* d, const ff* tau, const ff* S,
+                                              ff kk, ff one_lam, const ff* rhs, ff* x, ff* r, float* v) {
+  bool ok = true;
+  for (int i = 0; i < n; ++i) x[i] = ff{0.f, 0.f};
+  for (int it = 0; it <= SUMS_REFINE && ok; ++it) {
+    // r = rhs - M x (the first step has x = 0), dx = M^-1 r through the FP32 factor
+    if (it == 0) {
+      for (int i = 0; i < n; ++i) r[i] = rhs[i];
+    } else {
+      mvec_ff(n, tau, S, kk, one_lam, x, r);
+      for (int i = 0; i < n; ++i) r[i] = ff_sum(rhs[i], ff_neg(r[i]));
+    }
+    for (int i = 0; i < n; ++i) v[i] = __fdiv_rn(r[i].h, d[i]);
+    llt_solve(L, v, n);
+    for (int i = 0; i < n; ++i) {
+      x[i] = ff_sum(x[i], ff{__fdiv_rn(v[i], d[i]), 0.f});
+      ok = ok && isfinite(x[i].h);
+    }
+  }
+  return ok;
+}
+
+// Cost (and, with grad, its derivative in theta) from the column sums. The
+// gradient of cost(x_hat) = b^T b - 2 x_hat^T h + x_hat^T M x_hat, x_hat = s * x*
+// (s the signs of the flip), x* = M^-1 h, is (variable projection with an
+// adjoint for the flip)
+//   d cost / d theta_i = -2 x_hat_i E_i + x_hat^T M_i x_hat + 2 (w_i E_i - w^T M_i x*),
+//   w = M^-1 (s * (M x_hat - h)),
+// with M_i = dM / d theta_i nonzero in row and column i only:
+//   (M_i)_{i0} = D_i,  (M_i)_{ii} = (1 + lam) D_i,
+//   (M_i)_{ij} = tau_i D_i / (tau_i + tau_j) + ln10 tau_i tau_j (S_i - S_j) / (tau_i + tau_j)^2
+// (the derivative of G_ij = (tau_i S_i + tau_j S_j)/(tau_i + tau_j), d tau_i = ln10 tau_i).
+__global__ void __launch_bounds__(256) k_solve_sums(EvalArgs a, double* cost, double* weights, double* grad) {
   const int64_t Q = a.sc.Q;
-  const int nm1 = a.sc.nmax + 1;
+  const int nmax = a.sc.nmax, nm1 = nmax + 1;
   for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
     const Unit u = a.units[ui];
     const int q = u.q0 + (int)threadIdx.x;
@@ -277,7 +310,7 @@ __global__ void __launch_bounds__(256) k_solve_sums(EvalArgs a, double* cost, do
     ff tau[NMAX], S[NMAX], hv[NMAX1], x[NMAX1], r[NMAX1];
     float L[NPACK_MAX], d[NMAX1], v[NMAX1];
     for (int i = 0; i < N; ++i) {
-      tau[i] = ff_of(exp10(a.theta[(int64_t)q * a.sc.nmax + i]));
+      tau[i] = ff_of(exp10(a.theta[(int64_t)q * nmax + i]));
       S[i] = ff_of(a.sc.G[(int64_t)i * Q + q]);
       hv[i + 1] = ff_of(a.sc.G[(int64_t)(N + i) * Q + q]);
     }
@@ -291,35 +324,23 @@ __global__ void __launch_bounds__(256) k_solve_sums(EvalArgs a, double* cost, do
       L[pk(i, i)] = (float)(1.0 + a.lam);
     }
     bool ok = cholesky_packed(L, n);
-    if (ok) {
-      for (int i = 0; i < n; ++i) x[i] = ff{0.f, 0.f};
-      for (int it = 0; it <= SUMS_REFINE && ok; ++it) {
-        // r = h - M x (the first step has x = 0), dx = M^-1 r through the FP32 factor
-        if (it == 0) {
-          for (int i = 0; i < n; ++i) r[i] = hv[i];
-        } else {
-          mvec_ff(n, tau, S, kk, one_lam, x, r);
-          for (int i = 0; i < n; ++i) r[i] = ff_sum(hv[i], ff_neg(r[i]));
-        }
-        for (int i = 0; i < n; ++i) v[i] = __fdiv_rn(r[i].h, d[i]);
-        llt_solve(L, v, n);
-        for (int i = 0; i < n; ++i) {
-          x[i] = ff_sum(x[i], ff{__fdiv_rn(v[i], d[i]), 0.f});
-          ok = ok && isfinite(x[i].h);
-        }
-      }
-    }
+    if (ok) ok = refined_solve(n, L, d, tau, S, kk, one_lam, hv, x, r, v);
     a.sc.fail[q] = ok ? 0 : 1;
     if (!ok) {
       if (cost) cost[q] = INFINITY;
       if (weights)
         for (int j = 0; j < nm1; ++j) weights[(int64_t)q * nm1 + j] = 0.0;
+      if (grad)
+        for (int j = 0; j < nmax; ++j) grad[(int64_t)q * nmax + j] = 0.0;
       continue;
     }
     // sign flip of negative d_eps (Sec. III-B), then the exact quadratic cost
-    for (int i = 1; i < n; ++i)
-      if (x[i].h < 0.f) x[i] = ff_neg(x[i]);
-    mvec_ff(n, tau, S, kk, one_lam, x, r);
+    float sgn[NMAX1];
+    for (int i = 0; i < n; ++i) {
+      sgn[i] = (i > 0 && x[i].h < 0.f) ? -1.f : 1.f;
+      if (sgn[i] < 0.f) x[i] = ff_neg(x[i]);
+    }
+    mvec_ff(n, tau, S, kk, one_lam, x, r);   // r = M x_hat
     ff c = ff_of(a.bb[u.s]);
     for (int i = 0; i < n; ++i) {
       c = ff_sum(c, ff_neg(ff_prod(ff{__fmul_rn(2.f, x[i].h), __fmul_rn(2.f, x[i].l)}, hv[i])));
@@ -331,6 +352,54 @@ __global__ void __launch_bounds__(256) k_solve_sums(EvalArgs a, double* cost, do
     if (cost) cost[q] = cv;
     if (weights)
       for (int j = 0; j < nm1; ++j) weights[(int64_t)q * nm1 + j] = j < n ? ff_dbl(x[j]) : 0.0;
+    if (!grad) continue;
+    // adjoint w = M^-1 (s * (M x_hat - h)); r becomes its right-hand side
+    ff w[NMAX1], rw[NMAX1];
+    for (int i = 0; i < n; ++i) {
+      r[i] = ff_sum(r[i], ff_neg(hv[i]));
+      if (sgn[i] < 0.f) r[i] = ff_neg(r[i]);
+    }
+    if (!refined_solve(n, L, d, tau, S, kk, one_lam, r, w, rw, v)) {
+      for (int j = 0; j < nmax; ++j) grad[(int64_t)q * nmax + j] = 0.0;
+      continue;
+    }
+    const ff ln10 = ff_of(2.302585092994046);
+    for (int i = 0; i < nmax; ++i) {
+      if (i >= N) {
+        grad[(int64_t)q * nmax + i] = 0.0;
+        continue;
+      }
+      const int I = i + 1;
+      const ff Di = ff_of(a.sc.G[(int64_t)(2 * N + i) * Q + q]);
+      const ff Ei = ff_of(a.sc.G[(int64_t)(3 * N + i) * Q + q]);
+      // row i of M_i against x_hat, w and x* (x*_j = s_j x_hat_j), off the diagonal
+      ff ax = ff_prod(Di, x[0]), aw = ff_prod(Di, w[0]), as = ax;
+      for (int j = 0; j < N; ++j) {
+        if (j == i) continue;
+        const ff rr = ff_quot(ff{1.f, 0.f}, ff_sum(tau[i], tau[j]));
+        const ff t1 = ff_prod(ff_prod(tau[i], Di), rr);
+        const ff t2 = ff_prod(ff_prod(ff_prod(ln10, ff_prod(tau[i], tau[j])), ff_sum(S[i], ff_neg(S[j]))),
+                              ff_prod(rr, rr));
+        const ff row = ff_sum(t1, t2);
+        const ff xs = sgn[j + 1] < 0.f ? ff_neg(x[j + 1]) : x[j + 1];
+        ax = ff_sum(ax, ff_prod(row, x[j + 1]));
+        aw = ff_sum(aw, ff_prod(row, w[j + 1]));
+        as = ff_sum(as, ff_prod(row, xs));
+      }
+      const ff diag = ff_prod(Di, one_lam);
+      const ff xhI = x[I], wI = w[I];
+      const ff xsI = sgn[I] < 0.f ? ff_neg(xhI) : xhI;
+      // x_hat^T M_i x_hat = 2 x_hat_i ax + diag x_hat_i^2;  w^T M_i x* = w_i as + x*_i aw + diag w_i x*_i
+      ff gsum = ff_neg(ff_prod(ff{__fmul_rn(2.f, xhI.h), __fmul_rn(2.f, xhI.l)}, Ei));
+      gsum = ff_sum(gsum, ff_prod(ff{__fmul_rn(2.f, xhI.h), __fmul_rn(2.f, xhI.l)}, ax));
+      gsum = ff_sum(gsum, ff_prod(diag, ff_prod(xhI, xhI)));
+      ff adj = ff_prod(wI, Ei);
+      adj = ff_sum(adj, ff_neg(ff_prod(wI, as)));
+      adj = ff_sum(adj, ff_neg(ff_prod(xsI, aw)));
+      adj = ff_sum(adj, ff_neg(ff_prod(diag, ff_prod(wI, xsI))));
+      gsum = ff_sum(gsum, ff{__fmul_rn(2.f, adj.h), __fmul_rn(2.f, adj.l)});
+      grad[(int64_t)q * nmax + i] = ff_dbl(gsum);
+    }
   }
 }
 
@@ -454,8 +523,9 @@ static int grid_for(int n_units, int sms, int per_sm) {
 
 // One thread per candidate with per-thread arrays in local memory: a grid of up to
 // 32 blocks per SM keeps enough warps resident to hide that memory's latency.
-void launch_solve_sums(const EvalArgs& a, double* cost, double* weights, int block, int sms, cudaStream_t st) {
-  if (a.n_units) k_solve_sums<<<grid_for(a.n_units, sms, 32), block, 0, st>>>(a, cost, weights);
+void launch_solve_sums(const EvalArgs& a, double* cost, double* weights, double* grad, int block, int sms,
+                       cudaStream_t st) {
+  if (a.n_units) k_solve_sums<<<grid_for(a.n_units, sms, 32), block, 0, st>>>(a, cost, weights, grad);
 }
 
 // The factor is FP32 when a.lf32 is set (mixed precision), FP64 otherwise.

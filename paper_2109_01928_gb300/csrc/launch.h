@@ -66,8 +66,10 @@ inline void launch_pass(int N, int phase, bool mixed, const EvalArgs& a, int gri
 void launch_prep(int64_t n_samples, int64_t S, const int64_t* offsets, const double* omega,
                  const double* er, const double* ei, const double* lo, const double* hi,
                  float4* kf32, float4* kff, double* h0, int* status, int sms, cudaStream_t st);
-// Mixed cost-only evaluation after the column-sum pass: weights, flip and cost.
-void launch_solve_sums(const EvalArgs& a, double* cost, double* weights, int block, int sms, cudaStream_t st);
+// Mixed evaluation after the column-sum pass: weights, flip, cost and (grad != nullptr,
+// after the pass with derivative sums) the gradient in theta.
+void launch_solve_sums(const EvalArgs& a, double* cost, double* weights, double* grad, int block, int sms,
+                       cudaStream_t st);
 inline int warp_round(int n) { return (n + 31) / 32 * 32; }
 void launch_solve(const EvalArgs& a, int block, int sms, cudaStream_t st);
 void launch_finish(const EvalArgs& a, int final_step, double* cost, double* weights, double* g1,

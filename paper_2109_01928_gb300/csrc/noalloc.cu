@@ -229,7 +229,7 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
   if (mixed) {
     // one float-float column-sum pass, weights and cost from the exact Gram identity
     per_bucket(PH_SUMS);
-    launch_solve_sums(a, cost, weights, warp_round(cb), sms, st);
+    launch_solve_sums(a, cost, weights, nullptr, warp_round(cb), sms, st);
   } else {
     per_bucket(PH_GRAM);
     launch_solve(a, warp_round(cb), sms, st);

@@ -27,6 +27,7 @@ void launch_pass_n(int phase, bool mixed, const EvalArgs& a, int grid, int block
     }
     else if (phase == PH_REFINE) k_pass<PH_REFINE, N, N, true, MAXT, MB_MIXED><<<grid, block, 0, st>>>(a);
     else if (phase == PH_SUMS) k_pass<PH_SUMS, N, N, true, MAXT, MB_MIXED><<<grid, block, 0, st>>>(a);
+    else if (phase == PH_SUMSG) k_pass<PH_SUMSG, N, N, true, MAXT, 1><<<grid, block, 0, st>>>(a);
     else k_pass<PH_GRAD, N, N, true, MAXT, 1><<<grid, block, 0, st>>>(a);
   } else {
     if (phase == PH_GRAM) k_pass<PH_GRAM, N, N, false, MAXT, 1><<<grid, block, 0, st>>>(a);
