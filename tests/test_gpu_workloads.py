@@ -105,3 +105,27 @@ def test_tabulated_full_size_sampled(D):
         a, c = sub.offsets[i], sub.offsets[i + 1]
         ref = float(dls.cost(sub.omega[a:c], re[a:c], im[a:c], th[s, p]))
         assert abs(cost[s, p] - ref) <= COST_TOL["mixed"] * ref, (s, p, cost[s, p], ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tabulated_cost_grad_sampled(D, prec):
+    # N = 20, K = 4096 noisy Debye-sum spectra: cost and gradient of sampled candidates
+    b = W.workload("tabulated_16384_k4096").subset(np.arange(32))
+    re, im = models.synthesize(b)
+    th = W.population(b, 64, seed=4)
+    with D.Handle(prec) as h:
+        cost, grad = D.debye_cost_grad(h, _spectra(D, b, re, im), torch.as_tensor(th, device="cuda"))
+        D.debye_sync(h)
+    cost, grad = cost.cpu().numpy(), grad.cpu().numpy()
+    rng = np.random.default_rng(5)
+    checked = 0
+    for s, p in zip(rng.integers(0, b.S, 16), rng.integers(0, 64, 16)):
+        a, c = b.offsets[s], b.offsets[s + 1]
+        x = dls.damped_solve(dls.basis(b.omega[a:c], th[s, p]), dls.target(re[a:c], im[a:c]), dls.LAM_SEARCH)
+        cref, gref = varpro.cost_grad(b.omega[a:c], re[a:c], im[a:c], th[s, p])
+        assert abs(cost[s, p] - cref) <= COST_TOL[prec] * cref, (s, p)
+        if np.min(np.abs(x[1:])) < 1e-6 * np.abs(x).max():
+            continue
+        assert np.linalg.norm(grad[s, p] - gref) <= GRAD_TOL[prec] * np.linalg.norm(gref), (s, p)
+        checked += 1
+    assert checked >= 8
