@@ -448,8 +448,8 @@ def main():
         "config": {"workload": f"{WORKLOAD}: {S} spectra, K {int(b.K.min())}-{int(b.K.max())} "
                                f"(sum {int(b.K.sum())}), N {int(b.n_poles.min())}-{int(b.n_poles.max())}, "
                                f"P={b.P}, {iters} swarm generations after the first, top-{TOPK} x "
-                               f"{POLISH_ITERS} L-BFGS polish, mixed precision (FP32 Gram, FP64 solve, "
-                               f"float-float residual)",
+                               f"{POLISH_ITERS} L-BFGS polish, mixed precision (float-float column sums, exact "
+                               f"Gram identity, FP32 factor refined in float-float)",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -56,7 +56,8 @@ extern "C" {
 
 /* ------------------------------------------------------------------ precision */
 #define DEBYE_PREC_FP64  0    /* FP64 basis, Gram, solve and residual */
-#define DEBYE_PREC_MIXED 1    /* FP32 basis and Gram, FP64 solve, float-float residual */
+#define DEBYE_PREC_MIXED 1    /* float-float column sums of the Debye basis, exact Gram identity,
+                                 FP32 factor refined in float-float */
 
 #define DEBYE_MAX_POLES 20    /* largest N accepted */
 
@@ -83,7 +84,9 @@ typedef struct debye_ctx* debye_handle;
 /* Solver options. debye_default_options() fills the documented defaults. */
 typedef struct {
   int32_t precision;      /* DEBYE_PREC_FP64 or DEBYE_PREC_MIXED (default MIXED) */
-  int32_t refine_steps;   /* refinement passes after the first solve, 1..4 (default 1) */
+  int32_t refine_steps;   /* FP64 precision: residual passes with refinement after the first
+                             solve, 1..4 (default 1); the mixed path refines on its small
+                             float-float system instead and ignores it */
   double  lam_search;     /* Marquardt damping of search and polish (default 1e-3) */
   double  lam_final;      /* damping of the reported weights (default 1e-3 = lam_search) */
   double  pso_omega;      /* swarm inertia (default 0.5) */

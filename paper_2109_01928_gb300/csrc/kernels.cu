@@ -240,7 +240,12 @@ __global__ void __launch_bounds__(256) k_finish(EvalArgs a, int final_step, doub
 // loses the digits of b^T b / cost, about 4: float-float keeps ~9 of the ~13
 // digits it carries); x comes from an FP32 Cholesky factor of the scaled M and
 // two refinement steps with the float-float residual h - M x.
-constexpr int SUMS_REFINE = 2;
+constexpr int SUMS_REFINE = 2;       // refinement steps with the gradient (x and the adjoint w)
+// Cost-only evaluations take one step: the scaled damped matrix C + lam I has unit
+// diagonal, so kappa <= (n + lam) / lam (2e4 at n = 21, lam = 1e-3) and after one
+// step the weights carry about (kappa 2^-24)^2 = 1.4e-6 relative error, which
+// reaches a flipped candidate's cost at first order; two steps are ~2e-9.
+constexpr int SUMS_REFINE_COST = 1;
 
 __device__ __forceinline__ ff gram_ff(int i, int j, const ff* tau, const ff* S, ff kk) {
   if (i == 0 && j == 0) return kk;
@@ -266,12 +271,13 @@ __device__ __forceinline__ void mvec_ff(int n, const ff* tau, const ff* S, ff kk
   }
 }
 
-// M^-1 rhs refined twice against the float-float M (FP32 factor L of the scaled M).
+// M^-1 rhs through the FP32 factor L of the scaled M, refined `steps` times
+// against the float-float M.
 __device__ __forceinline__ bool refined_solve(int n, const float* L, const float* d, const ff* tau, const ff* S,
-                                              ff kk, ff one_lam, const ff* rhs, ff* x, ff* r, float* v) {
+                                              ff kk, ff one_lam, const ff* rhs, ff* x, ff* r, float* v, int steps) {
   bool ok = true;
   for (int i = 0; i < n; ++i) x[i] = ff{0.f, 0.f};
-  for (int it = 0; it <= SUMS_REFINE && ok; ++it) {
+  for (int it = 0; it <= steps && ok; ++it) {
     // r = rhs - M x (the first step has x = 0), dx = M^-1 r through the FP32 factor
     if (it == 0) {
       for (int i = 0; i < n; ++i) r[i] = rhs[i];
@@ -324,7 +330,7 @@ __global__ void __launch_bounds__(256) k_solve_sums(EvalArgs a, double* cost, do
       L[pk(i, i)] = (float)(1.0 + a.lam);
     }
     bool ok = cholesky_packed(L, n);
-    if (ok) ok = refined_solve(n, L, d, tau, S, kk, one_lam, hv, x, r, v);
+    if (ok) ok = refined_solve(n, L, d, tau, S, kk, one_lam, hv, x, r, v, grad ? SUMS_REFINE : SUMS_REFINE_COST);
     a.sc.fail[q] = ok ? 0 : 1;
     if (!ok) {
       if (cost) cost[q] = INFINITY;
@@ -359,7 +365,7 @@ __global__ void __launch_bounds__(256) k_solve_sums(EvalArgs a, double* cost, do
       r[i] = ff_sum(r[i], ff_neg(hv[i]));
       if (sgn[i] < 0.f) r[i] = ff_neg(r[i]);
     }
-    if (!refined_solve(n, L, d, tau, S, kk, one_lam, r, w, rw, v)) {
+    if (!refined_solve(n, L, d, tau, S, kk, one_lam, r, w, rw, v, SUMS_REFINE)) {
       for (int j = 0; j < nmax; ++j) grad[(int64_t)q * nmax + j] = 0.0;
       continue;
     }
