@@ -236,9 +236,11 @@ int debye_ctx::ensure_scratch(int64_t Q, int nmax, ScratchBufs& sb, Scratch& sc)
   return DEBYE_OK;
 }
 
-// The whole evaluation of one candidate set: Gram pass, FP64 solve,
-// `refine_steps` residual passes with refinement, flip and cost, and optionally
-// the gradient. Units must already be on the device (a.units).
+// The whole evaluation of one candidate set. Mixed precision: the float-float
+// column-sum pass and k_solve_sums (weights, cost and optionally the gradient).
+// FP64: Gram pass, solve, `steps` residual passes with refinement, flip and
+// cost, and optionally the gradient passes. Units must already be on the device
+// (a.units); a.bb must be set (b^T b per spectrum) for the mixed path.
 int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, double* cost,
                         double* weights, double* grad, double* g1, int cb, cudaStream_t st) {
   // The buckets' launches of one pass are independent (disjoint candidates): all but
@@ -276,11 +278,7 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
       ab.units = a.units + g.begin[b];
       ab.n_units = n;
       const int grid = std::max(1, std::min(n, sms * 16));
-      // Gram rows of N >= 13 split over two warps (fewer live accumulators) when each
-      // candidate has one lane
-      ab.gs = (phase == PH_GRAM && mixed && b + 1 >= 13 && a.ks == 1 && cb % 32 == 0) ? 2 : 1;
-      const int pblock = cb * a.ks * ab.gs;
-      launch_pass(b + 1, phase, mixed, ab, grid, pblock, bs);
+      launch_pass(b + 1, phase, ab, grid, cb * a.ks, bs);
       ++launches;
       if (bs != st) {
         cudaEventRecord(ev_join[b], bs);
@@ -299,12 +297,11 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
   };
   int rc;
   a.n_units = (int)g.units.size();
-  a.lf32 = mixed ? 1 : 0;
   if (a.n_units == 0) return DEBYE_OK;
   if (a.ks < 1 || a.ks > 32 || (a.ks & (a.ks - 1)) || cb * a.ks > MAX_BLOCK)
     return fail(DEBYE_EINTERNAL, "bad work layout (%d candidates x %d lanes)", cb, a.ks);
   const int gblock = warp_round(cb);
-  if (mixed && a.bb) {
+  if (mixed) {
     // one float-float column-sum pass (with the derivative sums when the gradient is
     // wanted), then weights, cost and gradient from the exact Gram identity of the
     // Debye columns (k_solve_sums)
@@ -322,18 +319,7 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
     if ((rc = check_launch("finish"))) return rc;
   }
   if (grad) {
-    // S g_hat overwrites g1 (no longer needed) for the adjoint refinement
-    timed(DEBYE_KERNEL_GRAD, [&] { launch_grad_prep(a, g1, mixed ? g1 : nullptr, gblock, sms, st); });
-    if (mixed) {
-      EvalArgs aw = a;   // residual pass on x := w against b = 0: rt = -A^T A w
-      aw.sc.x = a.sc.w;
-      aw.zero_b = 1;
-      EvalArgs saved = a;
-      a = aw;
-      if ((rc = per_bucket(PH_REFINE))) return rc;
-      a = saved;
-      timed(DEBYE_KERNEL_GRAD, [&] { launch_adjoint_refine(a, g1, gblock, sms, st); });
-    }
+    timed(DEBYE_KERNEL_GRAD, [&] { launch_grad_prep(a, g1, nullptr, gblock, sms, st); });
     if ((rc = per_bucket(PH_GRAD))) return rc;
     timed(DEBYE_KERNEL_GRAD, [&] { launch_grad_finish(a, grad, gblock, sms, st); });
     if ((rc = check_launch("gradient"))) return rc;
@@ -393,10 +379,7 @@ static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_
 // first-order in the weights' error through w = M^-1 S g_hat (g_hat carries the
 // FP32 Gram's error times the last correction), so cost+gradient evaluations
 // take at least two passes.
-int debye_ctx::eval_steps(bool with_grad) const {
-  const bool mixed = opt.precision == DEBYE_PREC_MIXED;
-  return (with_grad && mixed) ? std::max(opt.refine_steps, 2) : opt.refine_steps;
-}
+int debye_ctx::eval_steps(bool) const { return opt.refine_steps; }
 
 
 static bool create_side_streams(debye_ctx* h) {

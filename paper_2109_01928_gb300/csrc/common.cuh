@@ -38,7 +38,7 @@ struct Scratch {
   int32_t nmax;     // pole capacity of theta / weights rows
   int32_t ng;       // per-candidate Gram record: packed (nmax+1) lower triangle + h
   double* G;        // [ng][Q]   Gram (packed) followed by h = A^T b
-  double* L;        // [npk][Q]  Cholesky factor of the scaled damped matrix (float [npk][Q] if lf32)
+  double* L;        // [npk][Q]  Cholesky factor of the scaled damped matrix
   double* dinv;     // [nmax+1][Q] 1 / sqrt(G_ii)
   double* x;        // [nmax+1][Q] current (unflipped) weights
   double* xh;       // [nmax+1][Q] flipped weights
@@ -61,9 +61,6 @@ struct EvalArgs {
   const double* bb;        // [S] b^T b = sum_k eps'_k^2 + eps''_k^2
   const uint8_t* active;   // [Q] optional candidate mask (nullptr: all)
   int32_t ks;              // lanes per candidate in the pass kernels (power of two <= 32)
-  int32_t zero_b;          // residual pass against b = 0 (t = -A^T A x), for the adjoint refinement
-  int32_t gs;              // Gram pass: 2 = each candidate's Gram rows split over two warps
-  int32_t lf32;            // Cholesky factor stored and applied in FP32 (mixed precision)
   double lam;
   Scratch sc;
   int* status;             // device status word
@@ -123,17 +120,6 @@ __device__ __forceinline__ void basis_ff(float wh, float wl, float th, float tl,
   xh_out = xh;
 }
 
-// acc (hi, lo) -= w * c, with w and c float-float.
-__device__ __forceinline__ void ff_sub_prod(float& ah, float& al, float wh, float wl, float ch,
-                                            float cl) {
-  float p = __fmul_rn(wh, ch);
-  float pe = __fmaf_rn(wh, ch, -p);
-  pe = __fmaf_rn(wh, cl, __fmaf_rn(wl, ch, pe));
-  float s, e;
-  two_sum(ah, -p, s, e);
-  ah = s;
-  al = __fadd_rn(al, __fsub_rn(e, pe));
-}
 
 // acc (hi, lo) += a * b, a and b float-float (one Dot2 step: TwoProduct by FMA,
 // TwoSum of the leading part, low-order terms gathered in lo).
@@ -191,20 +177,7 @@ __device__ __forceinline__ ff ff_quot(ff a, ff b) {
   return ff{h, __fsub_rn(q2, __fsub_rn(h, q1))};
 }
 
-// (hi, lo) renormalised so that hi = fl(hi + lo) (Fast2Sum, |hi| >= |lo|).
-__device__ __forceinline__ void ff_norm(float& h, float& l) {
-  const float s = __fadd_rn(h, l);
-  l = __fsub_rn(l, __fsub_rn(s, h));
-  h = s;
-}
 
-// acc (hi, lo) += v (single float), exactly up to the final rounding of lo.
-__device__ __forceinline__ void ff_add(float& ah, float& al, float v) {
-  float s, e;
-  two_sum(ah, v, s, e);
-  ah = s;
-  al = __fadd_rn(al, e);
-}
 
 // ------------------------------------------------------------------ SplitMix64
 // Steele, Lea and Flood, "Fast splittable pseudorandom number generators",

@@ -8,15 +8,16 @@
 // used for full populations; ks > 1 keeps warps full when a spectrum has only
 // a few candidates (line-search points, one re-solve per spectrum).
 //
+// Mixed precision (float-float on the FP32 pipe):
+//   sums_unit    column sums S_i = sum re_i and h = A^T b of the Debye basis (and,
+//                for the gradient, the same sums over the derivative columns),
+//                from which k_solve_sums forms the Gram, weights, cost and gradient.
+// FP64 precision:
 //   gram_unit    G = A^T A (packed, (N+1)x(N+1)) and h = A^T b of the stacked
 //                real basis of Eq. 7 (rows: eps' and eps'' of every sample).
 //   refine_unit  r = b - A x at the current weights, rr = ||r||^2 and t = A^T r.
 //   grad_unit    projections of the derivative columns needed by the
 //                variable-projection gradient.
-//
-// MIXED = true : FP32 basis and Gram; residuals, ||r||^2 and every projection on a
-//                residual in float-float (Dot2 / TwoSum).
-// MIXED = false: everything in FP64.
 //
 // No lane returns before the group reduction: lanes without a candidate (the
 // tail of a unit, masked line-search points) contribute zeros.
@@ -30,15 +31,6 @@ struct Acc {
   static constexpr int NP = N * (N + 1) / 2;
 };
 
-// Samples summed in registers before a mixed-precision Gram block is added to
-// the shared-memory accumulators.
-constexpr int GRAM_BLOCK = 64;
-
-// Shared-memory floats per thread needed by the mixed Gram pass for N poles
-// (2N + N(N+1)/2 accumulators, rounded up to an odd stride).
-__host__ __device__ constexpr int gram_smem_stride(int N) { return (2 * N + N * (N + 1) / 2) | 1; }
-
-extern __shared__ __align__(16) unsigned char dyn_smem[];
 
 // ------------------------------------------------------------------ group reductions
 __device__ __forceinline__ float group_sum(float v, int ks) {
@@ -79,255 +71,77 @@ __device__ __forceinline__ Lane lane_of(const EvalArgs& a, const Unit& u, bool n
   return l;
 }
 
-// ------------------------------------------------------------------ Gram, rows split over two warps
-// For large N one thread cannot hold the whole Gram: with a.gs = 2 the block has
-// 2 * cb threads, threads [0, cb) accumulate rows [0, R) of the pair triangle and
-// G_0j, threads [cb, 2 cb) rows [R, N) and h_j, both computing every basis
-// value (R balances the pair counts). ks = 1.
-__host__ __device__ constexpr int split_row(int N) {
-  int r = 0;
-  while (r * (r + 1) < N * (N + 1) / 2) ++r;
-  return r;
-}
-__host__ __device__ constexpr int split_part_floats(int N) {
-  return (N + split_row(N) * (split_row(N) + 1) / 2 > N + N * (N + 1) / 2 - split_row(N) * (split_row(N) + 1) / 2
-              ? N + split_row(N) * (split_row(N) + 1) / 2
-              : N + N * (N + 1) / 2 - split_row(N) * (split_row(N) + 1) / 2) | 1;
-}
-
-template <int N, int R0, int R1, bool FIRST>
-__device__ __forceinline__ void gram_rows(const EvalArgs& a, const Unit& u, int q, bool act) {
-  constexpr int P0 = R0 * (R0 + 1) / 2;
-  constexpr int NPR = R1 * (R1 + 1) / 2 - P0;
-  constexpr int SA = split_part_floats(N);
-  const double* th = a.theta + (int64_t)q * a.sc.nmax;
-  const int64_t Q = a.sc.Q;
-  float* outer = reinterpret_cast<float*>(dyn_smem) + threadIdx.x * SA;
-#pragma unroll
-  for (int e = 0; e < N + NPR; ++e) outer[e] = 0.f;
-  float tau[N];
-#pragma unroll
-  for (int i = 0; i < N; ++i) tau[i] = act ? __double2float_rn(exp10(th[i])) : 0.f;
-  const int64_t kend = act ? u.k1 : u.k0;
-  for (int64_t kb = u.k0; kb < kend; kb += GRAM_BLOCK) {
-    const int64_t ke = min(kend, kb + (int64_t)GRAM_BLOCK);
-    float gv[N], gp[NPR];   // gv: G_0j (first part) or h_j (second part)
-#pragma unroll
-    for (int i = 0; i < N; ++i) gv[i] = 0.f;
-#pragma unroll
-    for (int i = 0; i < NPR; ++i) gp[i] = 0.f;
-    float4 vn = __ldg(&a.kf32[kb]);
-#pragma unroll 1
-    for (int64_t k = kb; k < ke; ++k) {
-      const float4 v = vn;
-      if (k + 1 < kend) vn = __ldg(&a.kf32[k + 1]);
-      float re[N], im[N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const float x = v.x * tau[i];
-        const float r = rcp_approx(fmaf(x, x, 1.0f));
-        re[i] = r;
-        im[i] = x * r;
-      }
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        if constexpr (FIRST) gv[i] += re[i];
-        else gv[i] = fmaf(re[i], v.y, fmaf(im[i], v.z, gv[i]));
-      }
-#pragma unroll
-      for (int i = R0; i < R1; ++i)
-#pragma unroll
-        for (int j = 0; j <= i; ++j)
-          gp[i * (i + 1) / 2 + j - P0] = fmaf(re[i], re[j], fmaf(im[i], im[j], gp[i * (i + 1) / 2 + j - P0]));
-    }
-#pragma unroll
-    for (int i = 0; i < N; ++i) outer[i] += gv[i];
-#pragma unroll
-    for (int i = 0; i < NPR; ++i) outer[N + i] += gp[i];
-  }
-  if (!act) return;
-  double* G = a.sc.G;
-  const int hb = (a.sc.nmax + 1) * (a.sc.nmax + 2) / 2;
-  if constexpr (FIRST) {
-    G[(int64_t)pk(0, 0) * Q + q] = (double)(u.k1 - u.k0);
-#pragma unroll
-    for (int i = 0; i < N; ++i) G[(int64_t)pk(i + 1, 0) * Q + q] = (double)outer[i];
-  } else {
-    G[(int64_t)hb * Q + q] = a.h0[u.s];
-#pragma unroll
-    for (int i = 0; i < N; ++i) G[(int64_t)(hb + 1 + i) * Q + q] = (double)outer[i];
-  }
-#pragma unroll
-  for (int i = R0; i < R1; ++i)
-#pragma unroll
-    for (int j = 0; j <= i; ++j)
-      G[(int64_t)pk(i + 1, j + 1) * Q + q] = (double)outer[N + i * (i + 1) / 2 + j - P0];
-}
-
 // ------------------------------------------------------------------ Gram
-template <int N, bool MIXED>
+template <int N>
 __device__ __forceinline__ void gram_unit(const EvalArgs& a, const Unit& u) {
-  if constexpr (MIXED && N >= 13) {
-    if (a.gs == 2) {
-      const int cbg = (int)blockDim.x / 2;
-      const int part = (int)threadIdx.x / cbg;          // warp-uniform (cbg is a multiple of 32)
-      const int q0 = u.q0 + (int)threadIdx.x % cbg;
-      bool act = q0 < u.q1;
-      if (act && a.active) act = a.active[q0] != 0;
-      const int q = act ? q0 : u.q0;
-      constexpr int R = split_row(N);
-      if (part == 0) gram_rows<N, 0, R, true>(a, u, q, act);
-      else gram_rows<N, R, N, false>(a, u, q, act);
-      return;
-    }
-  }
   const Lane ln = lane_of(a, u, false);
   const int q = ln.act ? ln.q : u.q0;
   constexpr int NP = Acc<N>::NP;
   const double* th = a.theta + (int64_t)q * a.sc.nmax;
   const int64_t Q = a.sc.Q;
   const int64_t kbeg = u.k0 + ln.slice;
-  if constexpr (MIXED) {
-    // Two-level FP32 accumulation: registers sum GRAM_BLOCK of this lane's
-    // samples, then each block is added into the lane's slice of shared memory
-    // (entry e of thread t at outer[t * SA + e], SA odd and known at compile
-    // time, so every access is an immediate offset). The rounding error grows
-    // like (GRAM_BLOCK + K / GRAM_BLOCK) instead of K.
-    constexpr int SA = gram_smem_stride(N);
-    float* outer = reinterpret_cast<float*>(dyn_smem) + threadIdx.x * SA;
+  double tau[N], g0[N], hv[N], gp[NP];
 #pragma unroll
-    for (int e = 0; e < SA; ++e) outer[e] = 0.f;
-    float tau[N];
+  for (int i = 0; i < N; ++i) {
+    tau[i] = ln.act ? exp10(th[i]) : 0.0;
+    g0[i] = 0.0;
+    hv[i] = 0.0;
+  }
 #pragma unroll
-    for (int i = 0; i < N; ++i) tau[i] = ln.act ? __double2float_rn(exp10(th[i])) : 0.f;
-    const int64_t kend = ln.act ? u.k1 : kbeg;
-    const int64_t step = ln.ks;
-    for (int64_t kb = kbeg; kb < kend; kb += step * GRAM_BLOCK) {
-      const int64_t ke = min(kend, kb + step * GRAM_BLOCK);
-      float g0[N], hv[N], gp[NP];
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        g0[i] = 0.f;
-        hv[i] = 0.f;
-      }
-#pragma unroll
-      for (int i = 0; i < NP; ++i) gp[i] = 0.f;
-      float4 vn = __ldg(&a.kf32[kb]);
+  for (int i = 0; i < NP; ++i) gp[i] = 0.0;
+  const int64_t kend = ln.act ? u.k1 : kbeg;
 #pragma unroll 1
-      for (int64_t k = kb; k < ke; k += step) {
-        const float4 v = vn;
-        if (k + step < kend) vn = __ldg(&a.kf32[k + step]);   // next sample in flight
-        float re[N], im[N];
+  for (int64_t k = kbeg; k < kend; k += ln.ks) {
+    const double w = __ldg(&a.omega[k]);
+    const double br = __ldg(&a.eps_re[k]);
+    const double bi = __ldg(&a.eps_im[k]);
+    double re[N], im[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-          const float x = v.x * tau[i];
-          const float r = rcp_approx(fmaf(x, x, 1.0f));
-          re[i] = r;
-          im[i] = x * r;
-        }
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          g0[i] += re[i];
-          hv[i] = fmaf(re[i], v.y, fmaf(im[i], v.z, hv[i]));
-        }
-#pragma unroll
-        for (int i = 0; i < N; ++i)
-#pragma unroll
-          for (int j = 0; j <= i; ++j)
-            gp[i * (i + 1) / 2 + j] = fmaf(re[i], re[j], fmaf(im[i], im[j], gp[i * (i + 1) / 2 + j]));
-      }
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        outer[i] += g0[i];
-        outer[N + i] += hv[i];
-      }
-#pragma unroll
-      for (int i = 0; i < NP; ++i) outer[2 * N + i] += gp[i];
+    for (int i = 0; i < N; ++i) {
+      const double x = w * tau[i];
+      const double r = 1.0 / fma(x, x, 1.0);
+      re[i] = r;
+      im[i] = x * r;
     }
-    const bool wr = ln.act && ln.slice == 0;
-    double* G = a.sc.G;
-    const int hb = (a.sc.nmax + 1) * (a.sc.nmax + 2) / 2;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      g0[i] += re[i];
+      hv[i] = fma(re[i], br, fma(im[i], bi, hv[i]));
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j)
+        gp[i * (i + 1) / 2 + j] = fma(re[i], re[j], fma(im[i], im[j], gp[i * (i + 1) / 2 + j]));
+  }
+  const bool wr = ln.act && ln.slice == 0;
+  double* G = a.sc.G;
+  const int hb = (a.sc.nmax + 1) * (a.sc.nmax + 2) / 2;
+  if (wr) {
+    G[(int64_t)pk(0, 0) * Q + q] = (double)(u.k1 - u.k0);
+    G[(int64_t)hb * Q + q] = a.h0[u.s];
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const double g0s = group_sum(g0[i], ln.ks);
+    const double hs = group_sum(hv[i], ln.ks);
     if (wr) {
-      G[(int64_t)pk(0, 0) * Q + q] = (double)(u.k1 - u.k0);
-      G[(int64_t)hb * Q + q] = a.h0[u.s];
+      G[(int64_t)pk(i + 1, 0) * Q + q] = g0s;
+      G[(int64_t)(hb + 1 + i) * Q + q] = hs;
     }
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const float g0s = group_sum(outer[i], ln.ks);
-      const float hs = group_sum(outer[N + i], ln.ks);
-      if (wr) {
-        G[(int64_t)pk(i + 1, 0) * Q + q] = (double)g0s;
-        G[(int64_t)(hb + 1 + i) * Q + q] = (double)hs;
-      }
-#pragma unroll
-      for (int j = 0; j <= i; ++j) {
-        const float v = group_sum(outer[2 * N + i * (i + 1) / 2 + j], ln.ks);
-        if (wr) G[(int64_t)pk(i + 1, j + 1) * Q + q] = (double)v;
-      }
-    }
-  } else {
-    double tau[N], g0[N], hv[N], gp[NP];
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      tau[i] = ln.act ? exp10(th[i]) : 0.0;
-      g0[i] = 0.0;
-      hv[i] = 0.0;
-    }
-#pragma unroll
-    for (int i = 0; i < NP; ++i) gp[i] = 0.0;
-    const int64_t kend = ln.act ? u.k1 : kbeg;
-#pragma unroll 1
-    for (int64_t k = kbeg; k < kend; k += ln.ks) {
-      const double w = __ldg(&a.omega[k]);
-      const double br = __ldg(&a.eps_re[k]);
-      const double bi = __ldg(&a.eps_im[k]);
-      double re[N], im[N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const double x = w * tau[i];
-        const double r = 1.0 / fma(x, x, 1.0);
-        re[i] = r;
-        im[i] = x * r;
-      }
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        g0[i] += re[i];
-        hv[i] = fma(re[i], br, fma(im[i], bi, hv[i]));
-      }
-#pragma unroll
-      for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int j = 0; j <= i; ++j)
-          gp[i * (i + 1) / 2 + j] = fma(re[i], re[j], fma(im[i], im[j], gp[i * (i + 1) / 2 + j]));
-    }
-    const bool wr = ln.act && ln.slice == 0;
-    double* G = a.sc.G;
-    const int hb = (a.sc.nmax + 1) * (a.sc.nmax + 2) / 2;
-    if (wr) {
-      G[(int64_t)pk(0, 0) * Q + q] = (double)(u.k1 - u.k0);
-      G[(int64_t)hb * Q + q] = a.h0[u.s];
-    }
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const double g0s = group_sum(g0[i], ln.ks);
-      const double hs = group_sum(hv[i], ln.ks);
-      if (wr) {
-        G[(int64_t)pk(i + 1, 0) * Q + q] = g0s;
-        G[(int64_t)(hb + 1 + i) * Q + q] = hs;
-      }
-#pragma unroll
-      for (int j = 0; j <= i; ++j) {
-        const double v = group_sum(gp[i * (i + 1) / 2 + j], ln.ks);
-        if (wr) G[(int64_t)pk(i + 1, j + 1) * Q + q] = v;
-      }
+    for (int j = 0; j <= i; ++j) {
+      const double v = group_sum(gp[i * (i + 1) / 2 + j], ln.ks);
+      if (wr) G[(int64_t)pk(i + 1, j + 1) * Q + q] = v;
     }
   }
+
 }
 
 // ------------------------------------------------------------------ residual pass
 // Reads the weights x (FP64) of candidate q, writes rt[0] = ||b - A x||^2 and
 // rt[1 + j] = (A^T (b - A x))_j, j = 0..N.
-template <int N, bool MIXED>
+template <int N>
 __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
   const Lane ln = lane_of(a, u, true);
   const int q = ln.act ? ln.q : u.q0;
@@ -337,145 +151,47 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
   const int64_t kbeg = u.k0 + ln.slice;
   const int64_t kend = ln.act ? u.k1 : kbeg;
   const int64_t step = ln.ks;
-  if constexpr (MIXED) {
-    // t = A^T r is a float-float dot product (Dot2) of the float-float basis and
-    // residual: the refinement step multiplies its error by M^-1, large along
-    // nearly collinear poles, and a flipped cost is first-order in the weights.
-    // It also sums G_ii = ||a_i||^2 = sum_k re_i(k) (re^2 + im^2 = re for a Debye
-    // column) in float-float: the damping lam G_ii x_i^2 then uses the exact
-    // column norms, not the FP32 Gram's diagonal. The sum starts at 1 so that it
-    // always dominates the next term (re <= 1) and Fast2Sum (Dekker) is exact;
-    // the bias is removed in FP64 at the end.
-    float th_[N], tl_[N], wh[N], wl[N], th_t[N], tl_t[N], gdh[N], gdl[N];
-    float w0h = 0.f, w0l = 0.f;
-    if (ln.act) split_double(X[q], w0h, w0l);
+  double tau[N], w[N], t[N];
+  const double w0 = ln.act ? X[q] : 0.0;
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      th_[i] = tl_[i] = wh[i] = wl[i] = 0.f;
-      if (ln.act) {
-        split_double(exp10(th[i]), th_[i], tl_[i]);
-        split_double(X[(int64_t)(i + 1) * Q + q], wh[i], wl[i]);
-      }
-      th_t[i] = 0.f;
-      tl_t[i] = 0.f;
-      gdh[i] = 1.f;
-      gdl[i] = 0.f;
-    }
-    float t0h = 0.f, t0l = 0.f, rrh = 0.f, rrl = 0.f;
-    const int64_t k0s = kbeg < u.k1 ? kbeg : u.k0;
-    float4 vhn = __ldg(&a.kf32[k0s]), vln = __ldg(&a.kff[k0s]);
-#pragma unroll 1
-    for (int64_t k = kbeg; k < kend; k += step) {
-      const float4 vh = vhn, vl = vln;
-      if (k + step < kend) {   // next sample in flight during this one
-        vhn = __ldg(&a.kf32[k + step]);
-        vln = __ldg(&a.kff[k + step]);
-      }
-      float reh[N], rel[N], imh[N], iml[N];
-      // residual of the real row: eps' - eps_inf - sum x_i re_i; each row is summed
-      // in two independent float-float chains (even / odd poles) merged at the end,
-      // halving the serial TwoSum dependency per sample
-      const float byh = a.zero_b ? 0.f : vh.y, byl = a.zero_b ? 0.f : vl.y;
-      float arh, arl, aih, ail, brh = 0.f, brl = 0.f, bih = 0.f, bil = 0.f;
-      two_sum(byh, -w0h, arh, arl);
-      arl = __fadd_rn(arl, __fsub_rn(byl, w0l));
-      aih = a.zero_b ? 0.f : vh.z;
-      ail = a.zero_b ? 0.f : vl.z;
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        float xh;
-        basis_ff(vh.x, vl.x, th_[i], tl_[i], reh[i], rel[i], imh[i], iml[i], xh);
-        if (i & 1) {
-          ff_sub_prod(brh, brl, wh[i], wl[i], reh[i], rel[i]);
-          ff_sub_prod(bih, bil, wh[i], wl[i], imh[i], iml[i]);
-        } else {
-          ff_sub_prod(arh, arl, wh[i], wl[i], reh[i], rel[i]);
-          ff_sub_prod(aih, ail, wh[i], wl[i], imh[i], iml[i]);
-        }
-      }
-      if (N > 1) {
-        float s, e;
-        two_sum(arh, brh, s, e);
-        arh = s;
-        arl = __fadd_rn(arl, __fadd_rn(brl, e));
-        two_sum(aih, bih, s, e);
-        aih = s;
-        ail = __fadd_rn(ail, __fadd_rn(bil, e));
-      }
-      ff_norm(arh, arl);
-      ff_norm(aih, ail);
-      ff_add(rrh, rrl, __fmul_rn(arh, arh));
-      ff_add(rrh, rrl, __fmul_rn(aih, aih));
-      ff_add(t0h, t0l, arh);
-      t0l = __fadd_rn(t0l, arl);
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        ff_add_prod(th_t[i], tl_t[i], reh[i], rel[i], arh, arl);
-        ff_add_prod(th_t[i], tl_t[i], imh[i], iml[i], aih, ail);
-        const float gs = __fadd_rn(gdh[i], reh[i]);                 // Fast2Sum, gdh >= 1 >= reh
-        gdl[i] = __fadd_rn(gdl[i], __fadd_rn(__fsub_rn(reh[i], __fsub_rn(gs, gdh[i])), rel[i]));
-        gdh[i] = gs;
-      }
-    }
-    group_sum_ff(rrh, rrl, ln.ks);
-    group_sum_ff(t0h, t0l, ln.ks);
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      group_sum_ff(th_t[i], tl_t[i], ln.ks);
-      group_sum_ff(gdh[i], gdl[i], ln.ks);
-    }
-    if (ln.act && ln.slice == 0) {
-      double* R = a.sc.rt;
-      R[q] = (double)rrh + (double)rrl;
-      R[Q + q] = (double)t0h + (double)t0l;
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        R[(int64_t)(i + 2) * Q + q] = (double)th_t[i] + (double)tl_t[i];
-        a.sc.G[(int64_t)pk(i + 1, i + 1) * Q + q] = ((double)gdh[i] - (double)ln.ks) + (double)gdl[i];
-      }
-    }
-  } else {
-    double tau[N], w[N], t[N];
-    const double w0 = ln.act ? X[q] : 0.0;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      tau[i] = ln.act ? exp10(th[i]) : 0.0;
-      w[i] = ln.act ? X[(int64_t)(i + 1) * Q + q] : 0.0;
-      t[i] = 0.0;
-    }
-    double t0 = 0.0, rr = 0.0;
-#pragma unroll 1
-    for (int64_t k = kbeg; k < kend; k += step) {
-      const double om = __ldg(&a.omega[k]);
-      double ar = (a.zero_b ? 0.0 : __ldg(&a.eps_re[k])) - w0;
-      double ai = a.zero_b ? 0.0 : __ldg(&a.eps_im[k]);
-      double re[N], im[N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const double x = om * tau[i];
-        const double r = 1.0 / fma(x, x, 1.0);
-        re[i] = r;
-        im[i] = x * r;
-        ar = fma(-w[i], re[i], ar);
-        ai = fma(-w[i], im[i], ai);
-      }
-      rr = fma(ar, ar, fma(ai, ai, rr));
-      t0 += ar;
-#pragma unroll
-      for (int i = 0; i < N; ++i) t[i] = fma(re[i], ar, fma(im[i], ai, t[i]));
-    }
-    rr = group_sum(rr, ln.ks);
-    t0 = group_sum(t0, ln.ks);
-#pragma unroll
-    for (int i = 0; i < N; ++i) t[i] = group_sum(t[i], ln.ks);
-    if (ln.act && ln.slice == 0) {
-      double* R = a.sc.rt;
-      R[q] = rr;
-      R[Q + q] = t0;
-#pragma unroll
-      for (int i = 0; i < N; ++i) R[(int64_t)(i + 2) * Q + q] = t[i];
-    }
+  for (int i = 0; i < N; ++i) {
+    tau[i] = ln.act ? exp10(th[i]) : 0.0;
+    w[i] = ln.act ? X[(int64_t)(i + 1) * Q + q] : 0.0;
+    t[i] = 0.0;
   }
+  double t0 = 0.0, rr = 0.0;
+#pragma unroll 1
+  for (int64_t k = kbeg; k < kend; k += step) {
+    const double om = __ldg(&a.omega[k]);
+    double ar = __ldg(&a.eps_re[k]) - w0;
+    double ai = __ldg(&a.eps_im[k]);
+    double re[N], im[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const double x = om * tau[i];
+      const double r = 1.0 / fma(x, x, 1.0);
+      re[i] = r;
+      im[i] = x * r;
+      ar = fma(-w[i], re[i], ar);
+      ai = fma(-w[i], im[i], ai);
+    }
+    rr = fma(ar, ar, fma(ai, ai, rr));
+    t0 += ar;
+#pragma unroll
+    for (int i = 0; i < N; ++i) t[i] = fma(re[i], ar, fma(im[i], ai, t[i]));
+  }
+  rr = group_sum(rr, ln.ks);
+  t0 = group_sum(t0, ln.ks);
+#pragma unroll
+  for (int i = 0; i < N; ++i) t[i] = group_sum(t[i], ln.ks);
+  if (ln.act && ln.slice == 0) {
+    double* R = a.sc.rt;
+    R[q] = rr;
+    R[Q + q] = t0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) R[(int64_t)(i + 2) * Q + q] = t[i];
+  }
+
 }
 
 // ------------------------------------------------------------------ column-sum pass (mixed)
@@ -591,7 +307,7 @@ __device__ __forceinline__ void sums_unit(const EvalArgs& a, const Unit& u) {
 //   gt[2N + i]   = a_i'^T r,      r = b - A x1
 //   gt[3N + i]   = a_i'^T (A w)
 // where a_i' = d a_i / d log10(tau_i).
-template <int N, bool MIXED>
+template <int N>
 __device__ __forceinline__ void grad_unit(const EvalArgs& a, const Unit& u) {
   const Lane ln = lane_of(a, u, true);
   const int q = ln.act ? ln.q : u.q0;
@@ -602,188 +318,87 @@ __device__ __forceinline__ void grad_unit(const EvalArgs& a, const Unit& u) {
   const int64_t step = ln.ks;
   constexpr double LN10 = 2.302585092994046;
   auto ld = [&](const double* p) { return ln.act ? *p : 0.0; };
-  if constexpr (MIXED) {
-    // Float-float throughout: r_hat = b - A x_hat, r = b - A x1 and A w are
-    // float-float residual sums (in a flipped candidate r_hat is large and r
-    // small, so r is not formed as r_hat + A e); the derivative columns are
-    // float-float, via im = x re:
-    //   d re / d theta = -2 ln10 im^2,   d im / d theta = ln10 im (re - x im);
-    // the projections are Dot2 / TwoSum sums (the residual of a good fit changes
-    // sign along the spectrum, so they cancel heavily).
-    constexpr float LN10H = 2.3025851249694824f;               // fl(ln 10)
-    constexpr float LN10L = -3.1975436e-08f;                    // ln 10 - fl(ln 10)
-    float th_[N], tl_[N], xhh[N], xhl[N], x1h[N], x1l[N], wh[N], wl[N];
-    float trh_h[N], trh_l[N], taa_h[N], taa_l[N], tr_h[N], tr_l[N], taw_h[N], taw_l[N];
-    float x0h, x0l, x10h, x10l, w0h, w0l;
-    split_double(ld(a.sc.xh + q), x0h, x0l);
-    split_double(ld(a.sc.x + q), x10h, x10l);
-    split_double(ld(a.sc.w + q), w0h, w0l);
+  double tau[N], xh[N], e[N], w[N];
+  double t_rh[N], t_aa[N], t_r[N], t_aw[N];
+  const double x0 = ld(a.sc.xh + q);
+  const double e0 = x0 - ld(a.sc.x + q);
+  const double w0 = ld(a.sc.w + q);
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      split_double(ln.act ? exp10(th[i]) : 0.0, th_[i], tl_[i]);
-      split_double(ld(a.sc.xh + (int64_t)(i + 1) * Q + q), xhh[i], xhl[i]);
-      split_double(ld(a.sc.x + (int64_t)(i + 1) * Q + q), x1h[i], x1l[i]);
-      split_double(ld(a.sc.w + (int64_t)(i + 1) * Q + q), wh[i], wl[i]);
-      trh_h[i] = trh_l[i] = taa_h[i] = taa_l[i] = tr_h[i] = tr_l[i] = taw_h[i] = taw_l[i] = 0.f;
-    }
-    const int64_t k0s = kbeg < u.k1 ? kbeg : u.k0;
-    float4 vhn = __ldg(&a.kf32[k0s]), vln = __ldg(&a.kff[k0s]);
+  for (int i = 0; i < N; ++i) {
+    tau[i] = ln.act ? exp10(th[i]) : 0.0;
+    xh[i] = ld(a.sc.xh + (int64_t)(i + 1) * Q + q);
+    e[i] = xh[i] - ld(a.sc.x + (int64_t)(i + 1) * Q + q);
+    w[i] = ld(a.sc.w + (int64_t)(i + 1) * Q + q);
+    t_rh[i] = t_aa[i] = t_r[i] = t_aw[i] = 0.0;
+  }
 #pragma unroll 1
-    for (int64_t k = kbeg; k < kend; k += step) {
-      const float4 vh = vhn, vl = vln;
-      if (k + step < kend) {
-        vhn = __ldg(&a.kf32[k + step]);
-        vln = __ldg(&a.kff[k + step]);
-      }
-      float reh[N], rel[N], imh[N], iml[N], xv[N];
-      float hrh, hrl, hih, hil, rrh, rrl, rih, ril;
-      two_sum(vh.y, -x0h, hrh, hrl);
-      hrl = __fadd_rn(hrl, __fsub_rn(vl.y, x0l));
-      hih = vh.z;
-      hil = vl.z;
-      two_sum(vh.y, -x10h, rrh, rrl);
-      rrl = __fadd_rn(rrl, __fsub_rn(vl.y, x10l));
-      rih = vh.z;
-      ril = vl.z;
-      float awrh = -w0h, awrl = -w0l, awih = 0.f, awil = 0.f;   // -(A w), accumulated as a residual
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        basis_ff(vh.x, vl.x, th_[i], tl_[i], reh[i], rel[i], imh[i], iml[i], xv[i]);
-        ff_sub_prod(hrh, hrl, xhh[i], xhl[i], reh[i], rel[i]);
-        ff_sub_prod(hih, hil, xhh[i], xhl[i], imh[i], iml[i]);
-        ff_sub_prod(rrh, rrl, x1h[i], x1l[i], reh[i], rel[i]);
-        ff_sub_prod(rih, ril, x1h[i], x1l[i], imh[i], iml[i]);
-        ff_sub_prod(awrh, awrl, wh[i], wl[i], reh[i], rel[i]);
-        ff_sub_prod(awih, awil, wh[i], wl[i], imh[i], iml[i]);
-      }
-      ff_norm(hrh, hrl);
-      ff_norm(hih, hil);
-      ff_norm(rrh, rrl);
-      ff_norm(rih, ril);
-      ff_norm(awrh, awrl);
-      ff_norm(awih, awil);
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        // x = w tau again in float-float (basis_ff returned only its leading part)
-        float xh_ = __fmul_rn(vh.x, th_[i]);
-        float xl_ = __fmaf_rn(vh.x, th_[i], -xh_);
-        xl_ = __fmaf_rn(vh.x, tl_[i], __fmaf_rn(vl.x, th_[i], xl_));
-        float sh, sl, ph, pl, dmh, dml, drh, drl, dih, dil;
-        ff_mul(imh[i], iml[i], imh[i], iml[i], sh, sl);             // im^2
-        ff_mul(sh, sl, -2.0f * LN10H, -2.0f * LN10L, drh, drl);     // d re / d theta
-        ff_mul(xh_, xl_, imh[i], iml[i], ph, pl);                   // x im
-        two_sum(reh[i], -ph, dmh, dml);                             // re - x im
-        dml = __fadd_rn(dml, __fsub_rn(rel[i], pl));
-        ff_mul(imh[i], iml[i], dmh, dml, ph, pl);
-        ff_mul(ph, pl, LN10H, LN10L, dih, dil);                     // d im / d theta
-        ff_add_prod(trh_h[i], trh_l[i], drh, drl, hrh, hrl);
-        ff_add_prod(trh_h[i], trh_l[i], dih, dil, hih, hil);
-        ff_add(taa_h[i], taa_l[i], __fmaf_rn(imh[i], dih, __fmul_rn(reh[i], drh)));
-        ff_add_prod(tr_h[i], tr_l[i], drh, drl, rrh, rrl);
-        ff_add_prod(tr_h[i], tr_l[i], dih, dil, rih, ril);
-        ff_add_prod(taw_h[i], taw_l[i], drh, drl, awrh, awrl);      // accumulates -a'^T (A w)
-        ff_add_prod(taw_h[i], taw_l[i], dih, dil, awih, awil);
-      }
-    }
+  for (int64_t k = kbeg; k < kend; k += step) {
+    const double om = __ldg(&a.omega[k]);
+    double rhr = __ldg(&a.eps_re[k]) - x0, rhi = __ldg(&a.eps_im[k]);
+    double aer = e0, aei = 0.0, awr = w0, awi = 0.0;
+    double re[N], im[N], xv[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      group_sum_ff(trh_h[i], trh_l[i], ln.ks);
-      group_sum_ff(taa_h[i], taa_l[i], ln.ks);
-      group_sum_ff(tr_h[i], tr_l[i], ln.ks);
-      group_sum_ff(taw_h[i], taw_l[i], ln.ks);
+      const double x = om * tau[i];
+      const double r = 1.0 / fma(x, x, 1.0);
+      xv[i] = x;
+      re[i] = r;
+      im[i] = x * r;
+      rhr = fma(-xh[i], re[i], rhr);
+      rhi = fma(-xh[i], im[i], rhi);
+      aer = fma(e[i], re[i], aer);
+      aei = fma(e[i], im[i], aei);
+      awr = fma(w[i], re[i], awr);
+      awi = fma(w[i], im[i], awi);
     }
-    if (ln.act && ln.slice == 0) {
-      double* T = a.sc.gt;
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        T[(int64_t)i * Q + q] = (double)trh_h[i] + (double)trh_l[i];
-        T[(int64_t)(N + i) * Q + q] = (double)taa_h[i] + (double)taa_l[i];
-        T[(int64_t)(2 * N + i) * Q + q] = (double)tr_h[i] + (double)tr_l[i];
-        T[(int64_t)(3 * N + i) * Q + q] = -((double)taw_h[i] + (double)taw_l[i]);
-      }
-    }
-  } else {
-    double tau[N], xh[N], e[N], w[N];
-    double t_rh[N], t_aa[N], t_r[N], t_aw[N];
-    const double x0 = ld(a.sc.xh + q);
-    const double e0 = x0 - ld(a.sc.x + q);
-    const double w0 = ld(a.sc.w + q);
+    const double rr = rhr + aer, ri = rhi + aei;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      tau[i] = ln.act ? exp10(th[i]) : 0.0;
-      xh[i] = ld(a.sc.xh + (int64_t)(i + 1) * Q + q);
-      e[i] = xh[i] - ld(a.sc.x + (int64_t)(i + 1) * Q + q);
-      w[i] = ld(a.sc.w + (int64_t)(i + 1) * Q + q);
-      t_rh[i] = t_aa[i] = t_r[i] = t_aw[i] = 0.0;
-    }
-#pragma unroll 1
-    for (int64_t k = kbeg; k < kend; k += step) {
-      const double om = __ldg(&a.omega[k]);
-      double rhr = __ldg(&a.eps_re[k]) - x0, rhi = __ldg(&a.eps_im[k]);
-      double aer = e0, aei = 0.0, awr = w0, awi = 0.0;
-      double re[N], im[N], xv[N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const double x = om * tau[i];
-        const double r = 1.0 / fma(x, x, 1.0);
-        xv[i] = x;
-        re[i] = r;
-        im[i] = x * r;
-        rhr = fma(-xh[i], re[i], rhr);
-        rhi = fma(-xh[i], im[i], rhi);
-        aer = fma(e[i], re[i], aer);
-        aei = fma(e[i], im[i], aei);
-        awr = fma(w[i], re[i], awr);
-        awi = fma(w[i], im[i], awi);
-      }
-      const double rr = rhr + aer, ri = rhi + aei;
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const double x = xv[i];
-        const double re2l = re[i] * re[i] * LN10;
-        const double dre = -2.0 * x * x * re2l;
-        const double dim = x * (1.0 - x * x) * re2l;
-        t_rh[i] = fma(dre, rhr, fma(dim, rhi, t_rh[i]));
-        t_aa[i] = fma(re[i], dre, fma(im[i], dim, t_aa[i]));
-        t_r[i] = fma(dre, rr, fma(dim, ri, t_r[i]));
-        t_aw[i] = fma(dre, awr, fma(dim, awi, t_aw[i]));
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      t_rh[i] = group_sum(t_rh[i], ln.ks);
-      t_aa[i] = group_sum(t_aa[i], ln.ks);
-      t_r[i] = group_sum(t_r[i], ln.ks);
-      t_aw[i] = group_sum(t_aw[i], ln.ks);
-    }
-    if (ln.act && ln.slice == 0) {
-      double* T = a.sc.gt;
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        T[(int64_t)i * Q + q] = t_rh[i];
-        T[(int64_t)(N + i) * Q + q] = t_aa[i];
-        T[(int64_t)(2 * N + i) * Q + q] = t_r[i];
-        T[(int64_t)(3 * N + i) * Q + q] = t_aw[i];
-      }
+      const double x = xv[i];
+      const double re2l = re[i] * re[i] * LN10;
+      const double dre = -2.0 * x * x * re2l;
+      const double dim = x * (1.0 - x * x) * re2l;
+      t_rh[i] = fma(dre, rhr, fma(dim, rhi, t_rh[i]));
+      t_aa[i] = fma(re[i], dre, fma(im[i], dim, t_aa[i]));
+      t_r[i] = fma(dre, rr, fma(dim, ri, t_r[i]));
+      t_aw[i] = fma(dre, awr, fma(dim, awi, t_aw[i]));
     }
   }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    t_rh[i] = group_sum(t_rh[i], ln.ks);
+    t_aa[i] = group_sum(t_aa[i], ln.ks);
+    t_r[i] = group_sum(t_r[i], ln.ks);
+    t_aw[i] = group_sum(t_aw[i], ln.ks);
+  }
+  if (ln.act && ln.slice == 0) {
+    double* T = a.sc.gt;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      T[(int64_t)i * Q + q] = t_rh[i];
+      T[(int64_t)(N + i) * Q + q] = t_aa[i];
+      T[(int64_t)(2 * N + i) * Q + q] = t_r[i];
+      T[(int64_t)(3 * N + i) * Q + q] = t_aw[i];
+    }
+  }
+
 }
 
 // ------------------------------------------------------------------ N dispatch
-template <int PH, int N, bool MIXED>
+template <int PH, int N>
 __device__ __forceinline__ void run_phase(const EvalArgs& a, const Unit& u) {
-  if constexpr (PH == PH_GRAM) gram_unit<N, MIXED>(a, u);
-  else if constexpr (PH == PH_REFINE) refine_unit<N, MIXED>(a, u);
+  if constexpr (PH == PH_GRAM) gram_unit<N>(a, u);
+  else if constexpr (PH == PH_REFINE) refine_unit<N>(a, u);
   else if constexpr (PH == PH_SUMS) sums_unit<N, false>(a, u);
   else if constexpr (PH == PH_SUMSG) sums_unit<N, true>(a, u);
-  else grad_unit<N, MIXED>(a, u);
+  else grad_unit<N>(a, u);
 }
 
-template <int PH, int LO, int HI, bool MIXED>
+template <int PH, int LO, int HI>
 __device__ __forceinline__ void dispatch_n(const EvalArgs& a, const Unit& u) {
   if constexpr (LO <= HI) {
-    if (u.N == LO) run_phase<PH, LO, MIXED>(a, u);
-    else dispatch_n<PH, LO + 1, HI, MIXED>(a, u);
+    if (u.N == LO) run_phase<PH, LO>(a, u);
+    else dispatch_n<PH, LO + 1, HI>(a, u);
   }
 }
 
@@ -791,7 +406,7 @@ __device__ __forceinline__ void dispatch_n(const EvalArgs& a, const Unit& u) {
 // pole counts compiled into this kernel (the library launches one N per kernel). At most MAXT threads per block; MINB
 // resident blocks of that size bound the registers per thread (128 x 3: 168
 // registers, 12 warps per SM with 64-thread blocks).
-template <int PH, int LO, int HI, bool MIXED, int MAXT, int MINB>
+template <int PH, int LO, int HI, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) k_pass(EvalArgs a) {
   for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
     const Unit u = a.units[ui];
@@ -799,7 +414,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_pass(EvalArgs a) {
       if (threadIdx.x == 0) set_status(a.status, DEBYE_EBOUNDS);
       continue;
     }
-    dispatch_n<PH, LO, HI, MIXED>(a, u);
+    dispatch_n<PH, LO, HI>(a, u);
   }
 }
 

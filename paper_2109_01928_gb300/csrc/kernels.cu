@@ -66,8 +66,8 @@ __global__ void k_prep_spectra(int64_t S, const int64_t* __restrict__ offsets,
 }
 
 // ------------------------------------------------------------------ damped solve
-// Scaling helpers of the factor type T: the FP64 path divides by d = 1/dinv in
-// FP64 (as the plain method reads); the mixed path scales in FP32 by dinv.
+// Scaling helpers of the factor type T: in FP64 a division by d = 1/dinv (as the
+// plain method reads); in FP32 a multiplication by dinv.
 template <typename T>
 struct Scale {
   T dinv[NMAX1];   // 1 / sqrt(G_ii)
@@ -447,38 +447,6 @@ __global__ void __launch_bounds__(256) k_grad_prep(EvalArgs a, const double* g1,
   }
 }
 
-// One refinement step of the adjoint solve M w = S g_hat: with the residual pass
-// run on x := w against b = 0 (rt = -A^T A w in float-float),
-//   rho = S g_hat - (A^T A + lam diag G) w,  w <- w + M^-1 rho.
-// In a flipped candidate w is not small and enters the gradient to first order,
-// so the FP32 Gram's error in M^-1 must not reach it.
-template <typename T>
-__global__ void __launch_bounds__(256) k_adjoint_refine(EvalArgs a, const double* sg) {
-  const int64_t Q = a.sc.Q;
-  const T* Lg = factor_base<T>(a.sc);
-  for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
-    const Unit u = a.units[ui];
-    const int q = u.q0 + (int)threadIdx.x;
-    if (q >= u.q1 || (a.active && !a.active[q])) continue;
-    if (a.sc.fail[q]) continue;
-    const int n = u.N + 1;
-    T L[NPACK_MAX], v[NMAX1];
-    double w[NMAX1];
-    Scale<T> sc;
-    sc.load(a.sc, q, n);
-    const int npk = n * (n + 1) / 2;
-    for (int k = 0; k < npk; ++k) L[k] = Lg[(int64_t)k * Q + q];
-    for (int i = 0; i < n; ++i) {
-      w[i] = a.sc.w[(int64_t)i * Q + q];
-      const double gii = a.sc.G[(int64_t)pk(i, i) * Q + q];
-      const double rho = sg[(int64_t)i * Q + q] + a.sc.rt[(int64_t)(i + 1) * Q + q] - a.lam * gii * w[i];
-      v[i] = sc.down(rho, i);
-    }
-    llt_solve(L, v, n);
-    for (int i = 0; i < n; ++i) a.sc.w[(int64_t)i * Q + q] = w[i] + sc.up(v[i], i);
-  }
-}
-
 __global__ void __launch_bounds__(256) k_grad_finish(EvalArgs a, double* grad) {
   const int64_t Q = a.sc.Q;
   const int nmax = a.sc.nmax;
@@ -534,27 +502,15 @@ void launch_solve_sums(const EvalArgs& a, double* cost, double* weights, double*
   if (a.n_units) k_solve_sums<<<grid_for(a.n_units, sms, 32), block, 0, st>>>(a, cost, weights, grad);
 }
 
-// The factor is FP32 when a.lf32 is set (mixed precision), FP64 otherwise.
 void launch_solve(const EvalArgs& a, int block, int sms, cudaStream_t st) {
-  if (!a.n_units) return;
-  if (a.lf32) k_solve<float><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a);
-  else k_solve<double><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a);
+  if (a.n_units) k_solve<double><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a);
 }
 void launch_finish(const EvalArgs& a, int final_step, double* cost, double* weights, double* g1,
                    int block, int sms, cudaStream_t st) {
-  if (!a.n_units) return;
-  if (a.lf32) k_finish<float><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, final_step, cost, weights, g1);
-  else k_finish<double><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, final_step, cost, weights, g1);
+  if (a.n_units) k_finish<double><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, final_step, cost, weights, g1);
 }
 void launch_grad_prep(const EvalArgs& a, const double* g1, double* sg_out, int block, int sms, cudaStream_t st) {
-  if (!a.n_units) return;
-  if (a.lf32) k_grad_prep<float><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, g1, sg_out);
-  else k_grad_prep<double><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, g1, sg_out);
-}
-void launch_adjoint_refine(const EvalArgs& a, const double* sg, int block, int sms, cudaStream_t st) {
-  if (!a.n_units) return;
-  if (a.lf32) k_adjoint_refine<float><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, sg);
-  else k_adjoint_refine<double><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, sg);
+  if (a.n_units) k_grad_prep<double><<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, g1, sg_out);
 }
 void launch_grad_finish(const EvalArgs& a, double* grad, int block, int sms, cudaStream_t st) {
   if (a.n_units) k_grad_finish<<<grid_for(a.n_units, sms, 8), block, 0, st>>>(a, grad);

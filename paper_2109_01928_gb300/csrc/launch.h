@@ -11,7 +11,7 @@ namespace debyefit {
 // code (no instruction-cache thrashing between pole counts) and each N gets the
 // registers it needs. Work units are grouped by N ("buckets").
 constexpr int N_BUCKETS = NMAX;
-constexpr int MAX_BLOCK = 128; // largest pass block (candidates x lanes; mixed Gram shared memory at N = 20)
+constexpr int MAX_BLOCK = 128; // largest pass block (candidates x lanes)
 __host__ __device__ constexpr int bucket_of(int N) { return N - 1; }
 
 // Work layout for spectra with `per_spectrum` candidates each, `total` in the
@@ -47,18 +47,18 @@ inline void choose_layout(int64_t per_spectrum, int64_t total, int sms, int forc
 
 // Per-N passes (eval.cuh); pole counts 1-4, 5-8, 9-12, 13-16 and 17-20 compile in
 // separate translation units (pass_b0.cu .. pass_b4.cu) so that they build in parallel.
-void launch_pass_b0(int N, int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st);
-void launch_pass_b1(int N, int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st);
-void launch_pass_b2(int N, int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st);
-void launch_pass_b3(int N, int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st);
-void launch_pass_b4(int N, int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st);
-inline void launch_pass(int N, int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st) {
+void launch_pass_b0(int N, int phase, const EvalArgs& a, int grid, int block, cudaStream_t st);
+void launch_pass_b1(int N, int phase, const EvalArgs& a, int grid, int block, cudaStream_t st);
+void launch_pass_b2(int N, int phase, const EvalArgs& a, int grid, int block, cudaStream_t st);
+void launch_pass_b3(int N, int phase, const EvalArgs& a, int grid, int block, cudaStream_t st);
+void launch_pass_b4(int N, int phase, const EvalArgs& a, int grid, int block, cudaStream_t st);
+inline void launch_pass(int N, int phase, const EvalArgs& a, int grid, int block, cudaStream_t st) {
   switch ((N - 1) / 4) {
-    case 0: launch_pass_b0(N, phase, mixed, a, grid, block, st); break;
-    case 1: launch_pass_b1(N, phase, mixed, a, grid, block, st); break;
-    case 2: launch_pass_b2(N, phase, mixed, a, grid, block, st); break;
-    case 3: launch_pass_b3(N, phase, mixed, a, grid, block, st); break;
-    default: launch_pass_b4(N, phase, mixed, a, grid, block, st); break;
+    case 0: launch_pass_b0(N, phase, a, grid, block, st); break;
+    case 1: launch_pass_b1(N, phase, a, grid, block, st); break;
+    case 2: launch_pass_b2(N, phase, a, grid, block, st); break;
+    case 3: launch_pass_b3(N, phase, a, grid, block, st); break;
+    default: launch_pass_b4(N, phase, a, grid, block, st); break;
   }
 }
 
@@ -75,7 +75,6 @@ void launch_solve(const EvalArgs& a, int block, int sms, cudaStream_t st);
 void launch_finish(const EvalArgs& a, int final_step, double* cost, double* weights, double* g1,
                    int block, int sms, cudaStream_t st);
 void launch_grad_prep(const EvalArgs& a, const double* g1, double* sg_out, int block, int sms, cudaStream_t st);
-void launch_adjoint_refine(const EvalArgs& a, const double* sg, int block, int sms, cudaStream_t st);
 void launch_grad_finish(const EvalArgs& a, double* grad, int block, int sms, cudaStream_t st);
 
 }  // namespace debyefit

@@ -213,7 +213,6 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
   a.sc = sc;
   a.status = status;
   const bool mixed = opt.precision == DEBYE_PREC_MIXED;
-  a.lf32 = mixed ? 1 : 0;
   auto per_bucket = [&](int phase) {
     for (int b = 0; b < N_BUCKETS; ++b) {
       const int n = begin[b + 1] - begin[b];
@@ -222,8 +221,7 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
       ab.units = a.units + begin[b];
       ab.n_units = n;
       const int grid = std::max(1, std::min(n, sms * 16));
-      ab.gs = 1;
-      launch_pass(b + 1, phase, mixed, ab, grid, cb * ks, st);
+      launch_pass(b + 1, phase, ab, grid, cb * ks, st);
     }
   };
   if (mixed) {

@@ -5,34 +5,21 @@
 
 namespace debyefit {
 
+// The column-sum passes (PH_SUMS, PH_SUMSG) are the mixed-precision path; the
+// Gram, residual and gradient passes the FP64 path.
 template <int N>
-void launch_pass_n(int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st) {
-  // mixed-precision passes up to 12 poles fit in 168 registers without spills:
-  // cap them for 3 resident 128-thread blocks; larger N keeps the full register
-  // file, and its Gram pass may run two warps per candidate group (256 threads)
-  constexpr int MB_MIXED = N <= 12 ? 3 : 1;
+void launch_pass_n(int phase, const EvalArgs& a, int grid, int block, cudaStream_t st) {
+  // the cost-only column-sum pass up to 12 poles fits in 168 registers without
+  // spills: cap it for 3 resident 128-thread blocks; larger N, the gradient
+  // variant and the FP64 passes keep the full register file
+  constexpr int MB_SUMS = N <= 12 ? 3 : 1;
   constexpr int MAXT = N <= 12 ? 128 : 256;
-  if (mixed) {
-    if (phase == PH_GRAM) {
-      const int per_thread = a.gs == 2 ? split_part_floats(N) : gram_smem_stride(N);
-      const size_t smem = sizeof(float) * per_thread * block;
-      static bool attr_set = false;
-      if (!attr_set) {
-        const int most = std::max(gram_smem_stride(N) * MAX_BLOCK, split_part_floats(N) * 2 * MAX_BLOCK);
-        cudaFuncSetAttribute(k_pass<PH_GRAM, N, N, true, MAXT, MB_MIXED>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float) * most));
-        attr_set = true;
-      }
-      k_pass<PH_GRAM, N, N, true, MAXT, MB_MIXED><<<grid, block, smem, st>>>(a);
-    }
-    else if (phase == PH_REFINE) k_pass<PH_REFINE, N, N, true, MAXT, MB_MIXED><<<grid, block, 0, st>>>(a);
-    else if (phase == PH_SUMS) k_pass<PH_SUMS, N, N, true, MAXT, MB_MIXED><<<grid, block, 0, st>>>(a);
-    else if (phase == PH_SUMSG) k_pass<PH_SUMSG, N, N, true, MAXT, 1><<<grid, block, 0, st>>>(a);
-    else k_pass<PH_GRAD, N, N, true, MAXT, 1><<<grid, block, 0, st>>>(a);
-  } else {
-    if (phase == PH_GRAM) k_pass<PH_GRAM, N, N, false, MAXT, 1><<<grid, block, 0, st>>>(a);
-    else if (phase == PH_REFINE) k_pass<PH_REFINE, N, N, false, MAXT, 1><<<grid, block, 0, st>>>(a);
-    else k_pass<PH_GRAD, N, N, false, MAXT, 1><<<grid, block, 0, st>>>(a);
+  switch (phase) {
+    case PH_SUMS: k_pass<PH_SUMS, N, N, MAXT, MB_SUMS><<<grid, block, 0, st>>>(a); break;
+    case PH_SUMSG: k_pass<PH_SUMSG, N, N, MAXT, 1><<<grid, block, 0, st>>>(a); break;
+    case PH_GRAM: k_pass<PH_GRAM, N, N, MAXT, 1><<<grid, block, 0, st>>>(a); break;
+    case PH_REFINE: k_pass<PH_REFINE, N, N, MAXT, 1><<<grid, block, 0, st>>>(a); break;
+    default: k_pass<PH_GRAD, N, N, MAXT, 1><<<grid, block, 0, st>>>(a); break;
   }
 }
 

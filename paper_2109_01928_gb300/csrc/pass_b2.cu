@@ -4,12 +4,12 @@
 
 namespace debyefit {
 
-void launch_pass_b2(int N, int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st) {
+void launch_pass_b2(int N, int phase, const EvalArgs& a, int grid, int block, cudaStream_t st) {
   switch (N) {
-    case 9: launch_pass_n<9>(phase, mixed, a, grid, block, st); break;
-    case 10: launch_pass_n<10>(phase, mixed, a, grid, block, st); break;
-    case 11: launch_pass_n<11>(phase, mixed, a, grid, block, st); break;
-    default: launch_pass_n<12>(phase, mixed, a, grid, block, st); break;
+    case 9: launch_pass_n<9>(phase, a, grid, block, st); break;
+    case 10: launch_pass_n<10>(phase, a, grid, block, st); break;
+    case 11: launch_pass_n<11>(phase, a, grid, block, st); break;
+    default: launch_pass_n<12>(phase, a, grid, block, st); break;
   }
 }
 

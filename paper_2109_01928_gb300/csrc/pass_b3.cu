@@ -4,12 +4,12 @@
 
 namespace debyefit {
 
-void launch_pass_b3(int N, int phase, bool mixed, const EvalArgs& a, int grid, int block, cudaStream_t st) {
+void launch_pass_b3(int N, int phase, const EvalArgs& a, int grid, int block, cudaStream_t st) {
   switch (N) {
-    case 13: launch_pass_n<13>(phase, mixed, a, grid, block, st); break;
-    case 14: launch_pass_n<14>(phase, mixed, a, grid, block, st); break;
-    case 15: launch_pass_n<15>(phase, mixed, a, grid, block, st); break;
-    default: launch_pass_n<16>(phase, mixed, a, grid, block, st); break;
+    case 13: launch_pass_n<13>(phase, a, grid, block, st); break;
+    case 14: launch_pass_n<14>(phase, a, grid, block, st); break;
+    case 15: launch_pass_n<15>(phase, a, grid, block, st); break;
+    default: launch_pass_n<16>(phase, a, grid, block, st); break;
   }
 }
 

@@ -7,10 +7,9 @@
 //   M^-1 v   = D^-1 (L L^T)^-1 D^-1 v
 //   M v      = D L (L^T (D v))
 //   v^T M v  = || L^T (D v) ||^2
-// The factor and the products with it are computed in type T: double on the
-// FP64 path; float on the mixed path, whose Gram is an FP32 sum already (the
-// factor's rounding, about n 2^-24 relative, is of the order of the Gram's own,
-// and the refinement step against the float-float residual removes both).
+// The factor and the products with it are computed in type T (the FP64 path
+// instantiates double; the mixed path solves its systems in k_solve_sums, with
+// an FP32 copy of the factor refined in float-float).
 #pragma once
 #include "common.cuh"
 
