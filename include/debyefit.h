@@ -246,14 +246,15 @@ int debye_sync(debye_handle h, cudaStream_t stream);
 /* ------------------------------------------------------------------ kernel timing
  * For measurement tools. While enabled, CUDA-graph capture is switched off and
  * every pass of the evaluation is bracketed by CUDA events recorded on the
- * launching stream: a Gram, residual/refinement or gradient pass is one kernel
- * per pole count, launched concurrently on forked streams, and its interval runs
- * from the fork to the join; the FP64 solve and the finish are single launches.
- * Per kind the library accumulates the number of passes, the summed event time
- * (ms) and the algorithmic FLOPs of the work: per candidate and frequency sample,
- * 4N + 2(N+2)^2 for the Gram pass (basis build plus the unique Gram/right-hand-side
- * products), 98N + 38 for the float-float residual pass and 68N for the
- * float-float column-sum pass of cost-only mixed evaluations (FMA counted as 2).
+ * launching stream: a column-sum, Gram, residual/refinement or gradient pass is
+ * one kernel per pole count, launched concurrently on forked streams, and its
+ * interval runs from the fork to the join; the solves and the finish are single
+ * launches. Per kind the library accumulates the number of passes, the summed
+ * event time (ms) and the algorithmic FLOPs of the work, per candidate and
+ * frequency sample (FMA counted as 2): mixed precision, 68N for the float-float
+ * column-sum pass (152N with the derivative sums of a gradient evaluation);
+ * FP64, 4N + 2(N+2)^2 for the Gram pass (basis build plus the unique
+ * Gram/right-hand-side products) and 13N + 5 for the residual pass.
  * Passes restricted by an activity mask (the polish line search and its accepted
  * points) are accumulated under their own *_MASKED kinds, with time but no FLOPs. */
 #define DEBYE_KERNEL_GRAM          0

@@ -100,7 +100,7 @@ int debye_ctx::prof_collect() {
 // renormalisation, ||r||^2 and the eps_inf column).
 static double flops_per_cand_k(int phase, int N) {
   if (phase == PH_GRAM) return 4.0 * N + 2.0 * (N + 2) * (N + 2);
-  if (phase == PH_REFINE) return 98.0 * N + 38.0;
+  if (phase == PH_REFINE) return 13.0 * N + 5.0;
   if (phase == PH_SUMS) return 68.0 * N;
   if (phase == PH_SUMSG) return 152.0 * N;
   return 0.0;

@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256) k_finish(EvalArgs a, int final_step, doub
 // exactly. M, h, b^T b and the products with M are float-float (the subtraction
 // loses the digits of b^T b / cost, about 4: float-float keeps ~9 of the ~13
 // digits it carries); x comes from an FP32 Cholesky factor of the scaled M and
-// two refinement steps with the float-float residual h - M x.
+// refinement steps with the float-float residual h - M x.
 constexpr int SUMS_REFINE = 2;       // refinement steps with the gradient (x and the adjoint w)
 // Cost-only evaluations take one step: the scaled damped matrix C + lam I has unit
 // diagonal, so kappa <= (n + lam) / lam (2e4 at n = 21, lam = 1e-3) and after one
