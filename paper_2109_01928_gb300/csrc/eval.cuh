@@ -203,7 +203,9 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
 // d/d theta_i (theta = log10 tau; via im = x re: d re = -2 ln10 im^2,
 // d im = ln10 im (re - x im)):
 //   D_i = sum_k d re_i(k),   E_i = sum_k d re_i(k) eps'_k + d im_i(k) eps''_k.
-// Writes sc.G[i Q + q] = S_i, sc.G[(N + i) Q + q] = h_i, and with GRAD
+// Writes tau_i = 10^theta_i to sc.x[i Q + q] (the FP64 power is done once per
+// candidate here rather than again in the solve), sc.G[i Q + q] = S_i,
+// sc.G[(N + i) Q + q] = h_i, and with GRAD
 // sc.G[(2N + i) Q + q] = D_i, sc.G[(3N + i) Q + q] = E_i. The same-sign sums S
 // (re <= 1) and -D (<= ln10 / 2) start from a bias (1, 2) so that Fast2Sum is
 // exact; the bias is removed at the end.
@@ -224,7 +226,11 @@ __device__ __forceinline__ void sums_unit(const EvalArgs& a, const Unit& u) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     th_[i] = tl_[i] = 0.f;
-    if (ln.act) split_double(exp10(th[i]), th_[i], tl_[i]);
+    if (ln.act) {
+      const double t = exp10(th[i]);
+      split_double(t, th_[i], tl_[i]);
+      if (ln.slice == 0) a.sc.x[(int64_t)i * Q + q] = t;   // tau for k_solve_sums
+    }
     sh[i] = 1.f;
     sl[i] = hh[i] = hl[i] = 0.f;
   }

@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(256) k_solve_sums(EvalArgs a, double* cost, do
     ff tau[NMAX], S[NMAX], hv[NMAX1], x[NMAX1], r[NMAX1];
     float L[NPACK_MAX], d[NMAX1], v[NMAX1];
     for (int i = 0; i < N; ++i) {
-      tau[i] = ff_of(exp10(a.theta[(int64_t)q * nmax + i]));
+      tau[i] = ff_of(a.sc.x[(int64_t)i * Q + q]);   // 10^theta_i from the column-sum pass
       S[i] = ff_of(a.sc.G[(int64_t)i * Q + q]);
       hv[i + 1] = ff_of(a.sc.G[(int64_t)(N + i) * Q + q]);
     }
