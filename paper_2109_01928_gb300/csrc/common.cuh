@@ -169,10 +169,13 @@ __device__ __forceinline__ ff ff_prod(ff a, ff b) {
   return ff{h, __fsub_rn(e, __fsub_rn(h, p))};
 }
 // a / b: quotient q1 = a_h / b_h corrected by the float-float remainder a - q1 b.
+// Both quotients multiply by the approximate reciprocal of b_h (rcp.approx, about
+// 1 ulp): the float-float remainder carries q1's error, so a / b keeps ~2^-43.
 __device__ __forceinline__ ff ff_quot(ff a, ff b) {
-  const float q1 = __fdiv_rn(a.h, b.h);
+  const float rb = rcp_approx(b.h);
+  const float q1 = __fmul_rn(a.h, rb);
   const ff r = ff_sum(a, ff_neg(ff_prod(ff{q1, 0.f}, b)));
-  const float q2 = __fdiv_rn(r.h, b.h);
+  const float q2 = __fmul_rn(r.h, rb);
   const float h = __fadd_rn(q1, q2);
   return ff{h, __fsub_rn(q2, __fsub_rn(h, q1))};
 }

@@ -271,9 +271,41 @@ __device__ __forceinline__ void mvec_ff(int n, const ff* tau, const ff* S, ff kk
   }
 }
 
-// M^-1 rhs through the FP32 factor L of the scaled M, refined `steps` times
-// against the float-float M.
-__device__ __forceinline__ bool refined_solve(int n, const float* L, const float* d, const ff* tau, const ff* S,
+// FP32 Cholesky L L^T of the scaled damped matrix, with 1 / L_jj stored on the
+// diagonal so that the solves multiply instead of dividing.
+__device__ __forceinline__ bool cholesky_rdiag(float* L, int n) {
+  for (int j = 0; j < n; ++j) {
+    float s = L[pk(j, j)];
+    for (int k = 0; k < j; ++k) s = __fmaf_rn(-L[pk(j, k)], L[pk(j, k)], s);
+    if (!(s > 0.f) || !isfinite(s)) return false;
+    const float inv = __frsqrt_rn(s);
+    L[pk(j, j)] = inv;
+    for (int i = j + 1; i < n; ++i) {
+      float v = L[pk(i, j)];
+      for (int k = 0; k < j; ++k) v = __fmaf_rn(-L[pk(i, k)], L[pk(j, k)], v);
+      L[pk(i, j)] = __fmul_rn(v, inv);
+    }
+  }
+  return true;
+}
+
+// v <- (L L^T)^-1 v for the factor of cholesky_rdiag
+__device__ __forceinline__ void llt_solve_rdiag(const float* L, float* v, int n) {
+  for (int i = 0; i < n; ++i) {
+    float s = v[i];
+    for (int k = 0; k < i; ++k) s = __fmaf_rn(-L[pk(i, k)], v[k], s);
+    v[i] = __fmul_rn(s, L[pk(i, i)]);
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    float s = v[i];
+    for (int k = i + 1; k < n; ++k) s = __fmaf_rn(-L[pk(k, i)], v[k], s);
+    v[i] = __fmul_rn(s, L[pk(i, i)]);
+  }
+}
+
+// M^-1 rhs through the FP32 factor L of the scaled M (scaling dinv = diag(G)^-1/2),
+// refined `steps` times against the float-float M.
+__device__ __forceinline__ bool refined_solve(int n, const float* L, const float* dinv, const ff* tau, const ff* S,
                                               ff kk, ff one_lam, const ff* rhs, ff* x, ff* r, float* v, int steps) {
   bool ok = true;
   for (int i = 0; i < n; ++i) x[i] = ff{0.f, 0.f};
@@ -285,10 +317,10 @@ __device__ __forceinline__ bool refined_solve(int n, const float* L, const float
       mvec_ff(n, tau, S, kk, one_lam, x, r);
       for (int i = 0; i < n; ++i) r[i] = ff_sum(rhs[i], ff_neg(r[i]));
     }
-    for (int i = 0; i < n; ++i) v[i] = __fdiv_rn(r[i].h, d[i]);
-    llt_solve(L, v, n);
+    for (int i = 0; i < n; ++i) v[i] = __fmul_rn(r[i].h, dinv[i]);
+    llt_solve_rdiag(L, v, n);
     for (int i = 0; i < n; ++i) {
-      x[i] = ff_sum(x[i], ff{__fdiv_rn(v[i], d[i]), 0.f});
+      x[i] = ff_sum(x[i], ff{__fmul_rn(v[i], dinv[i]), 0.f});
       ok = ok && isfinite(x[i].h);
     }
   }
@@ -314,7 +346,7 @@ __global__ void __launch_bounds__(256) k_solve_sums(EvalArgs a, double* cost, do
     if (q >= u.q1 || (a.active && !a.active[q])) continue;
     const int N = u.N, n = N + 1;
     ff tau[NMAX], S[NMAX], hv[NMAX1], x[NMAX1], r[NMAX1];
-    float L[NPACK_MAX], d[NMAX1], v[NMAX1];
+    float L[NPACK_MAX], dinv[NMAX1], v[NMAX1];
     for (int i = 0; i < N; ++i) {
       tau[i] = ff_of(a.sc.x[(int64_t)i * Q + q]);   // 10^theta_i from the column-sum pass
       S[i] = ff_of(a.sc.G[(int64_t)i * Q + q]);
@@ -324,13 +356,13 @@ __global__ void __launch_bounds__(256) k_solve_sums(EvalArgs a, double* cost, do
     const ff kk = ff_of((double)(u.k1 - u.k0));
     const ff one_lam = ff_of(1.0 + a.lam);
     // FP32 Cholesky of the Marquardt-scaled damped matrix (unit diagonal + lam)
-    for (int i = 0; i < n; ++i) d[i] = __fsqrt_rn(gram_ff(i, i, tau, S, kk).h);
+    for (int i = 0; i < n; ++i) dinv[i] = __frsqrt_rn(gram_ff(i, i, tau, S, kk).h);   // diag(G)^-1/2
     for (int i = 0; i < n; ++i) {
-      for (int j = 0; j < i; ++j) L[pk(i, j)] = __fdiv_rn(gram_ff(i, j, tau, S, kk).h, __fmul_rn(d[i], d[j]));
+      for (int j = 0; j < i; ++j) L[pk(i, j)] = __fmul_rn(__fmul_rn(gram_ff(i, j, tau, S, kk).h, dinv[i]), dinv[j]);
       L[pk(i, i)] = (float)(1.0 + a.lam);
     }
-    bool ok = cholesky_packed(L, n);
-    if (ok) ok = refined_solve(n, L, d, tau, S, kk, one_lam, hv, x, r, v, grad ? SUMS_REFINE : SUMS_REFINE_COST);
+    bool ok = cholesky_rdiag(L, n);
+    if (ok) ok = refined_solve(n, L, dinv, tau, S, kk, one_lam, hv, x, r, v, grad ? SUMS_REFINE : SUMS_REFINE_COST);
     a.sc.fail[q] = ok ? 0 : 1;
     if (!ok) {
       if (cost) cost[q] = INFINITY;
@@ -365,7 +397,7 @@ __global__ void __launch_bounds__(256) k_solve_sums(EvalArgs a, double* cost, do
       r[i] = ff_sum(r[i], ff_neg(hv[i]));
       if (sgn[i] < 0.f) r[i] = ff_neg(r[i]);
     }
-    if (!refined_solve(n, L, d, tau, S, kk, one_lam, r, w, rw, v, SUMS_REFINE)) {
+    if (!refined_solve(n, L, dinv, tau, S, kk, one_lam, r, w, rw, v, SUMS_REFINE)) {
       for (int j = 0; j < nmax; ++j) grad[(int64_t)q * nmax + j] = 0.0;
       continue;
     }
