@@ -103,6 +103,11 @@ typedef struct {
   int32_t de_strategy;    /* DEBYE_DE_RAND1 (default) or DEBYE_DE_BEST1 */
   double  da_t0;          /* dual annealing: initial visiting temperature, > 0 (default 5230) */
   double  da_qa;          /* dual annealing: acceptance parameter, < 1 (default -5) */
+  int32_t solve_lanes;    /* mixed precision: lanes per candidate of the small-system solve
+                             after the column-sum pass: 1 = one thread per candidate, 32 =
+                             one warp per candidate (lane r: row r), 0 = by size (default: a
+                             warp per candidate when an evaluation has at most 256
+                             candidates per SM). Results agree to rounding either way. */
 } debye_options;
 
 /* A ragged batch of S spectra, CSR over frequency (all device memory unless _host). */

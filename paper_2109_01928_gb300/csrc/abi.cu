@@ -306,7 +306,11 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
     // wanted), then weights, cost and gradient from the exact Gram identity of the
     // Debye columns (k_solve_sums)
     if ((rc = per_bucket(grad ? PH_SUMSG : PH_SUMS))) return rc;
-    timed(DEBYE_KERNEL_SOLVE, [&] { launch_solve_sums(a, cost, weights, grad, gblock, sms, st); });
+    const bool by_warp = solve_sums_by_warp(a.sc.Q, opt.solve_lanes, sms);
+    timed(DEBYE_KERNEL_SOLVE, [&] {
+      if (by_warp) launch_solve_sums_warp(a, cost, weights, grad, cb, sms, st);
+      else launch_solve_sums(a, cost, weights, grad, gblock, sms, st);
+    });
     return check_launch("column-sum solve");
   }
   if ((rc = per_bucket(PH_GRAM))) return rc;
@@ -414,6 +418,7 @@ void debye_default_options(debye_options* o) {
   o->de_strategy = DEBYE_DE_RAND1;
   o->da_t0 = 5230.0;
   o->da_qa = -5.0;
+  o->solve_lanes = 0;
 }
 
 int debye_fit_init(debye_handle* out, const debye_options* opt) {
@@ -434,6 +439,7 @@ int debye_fit_init(debye_handle* out, const debye_options* opt) {
   if (!(o.de_cr >= 0.0) || !(o.de_cr <= 1.0)) return DEBYE_EINVAL;
   if (o.de_strategy != DEBYE_DE_RAND1 && o.de_strategy != DEBYE_DE_BEST1) return DEBYE_EINVAL;
   if (!(o.da_t0 > 0.0) || !(o.da_t0 < 1e300) || !(o.da_qa < 1.0) || !(o.da_qa > -1e6)) return DEBYE_EINVAL;
+  if (o.solve_lanes != 0 && o.solve_lanes != 1 && o.solve_lanes != 32) return DEBYE_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();

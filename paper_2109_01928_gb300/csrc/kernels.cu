@@ -441,6 +441,262 @@ __global__ void __launch_bounds__(256) k_solve_sums(EvalArgs a, double* cost, do
   }
 }
 
+// ------------------------------------------------------------------ cost from column sums, a warp per candidate
+// The algebra of k_solve_sums with lane r holding row r of the (N+1)-square
+// systems, so that its O(N^2) loops run across the lanes: M one row per lane,
+// the factorisation one column per step (rows in parallel), the triangular
+// solves one unknown per step (broadcast by shuffle), the products with M one
+// row per lane and the gradient one pole per lane. It serves evaluations too
+// small to fill the GPU with one thread per candidate (the polish's line-search
+// and accepted points), where k_solve_sums takes the latency of one candidate's
+// serial solve. Each warp keeps M (float-float) and the FP32 factor, both
+// [n1][n1] with n1 = nmax + 1, and the vectors its lanes exchange in shared memory.
+constexpr unsigned FULL_MASK = 0xffffffffu;
+constexpr int WARP_SOLVE_MAX_WARPS = 8;     // candidates in flight per block
+constexpr int WARP_SOLVE_MAX_Q_PER_SM = 256; // auto choice: at most this many candidates per SM
+
+struct WarpSolveMem {
+  ff* M;        // [n1][n1] M = G + lam diag G
+  ff* tau;      // [n1] row r >= 1: tau of pole r - 1
+  ff* S;        // [n1] row r >= 1: column sum S of pole r - 1
+  ff* v;        // [n1] vector multiplied by M
+  ff* xh;       // [n1] flipped weights x_hat
+  ff* w;        // [n1] adjoint
+  float* L;     // [n1][n1] FP32 factor of the scaled M, 1 / L_jj on the diagonal
+  float* dinv;  // [n1] diag(G)^-1/2
+  float* sgn;   // [n1] signs of the flip
+};
+
+__host__ __device__ inline size_t warp_solve_bytes(int n1) {
+  const size_t b = (size_t)n1 * n1 * (sizeof(ff) + sizeof(float)) + (size_t)n1 * (5 * sizeof(ff) + 2 * sizeof(float));
+  return (b + 15) / 16 * 16;
+}
+
+__device__ __forceinline__ WarpSolveMem warp_solve_mem(unsigned char* base, int n1) {
+  WarpSolveMem m;
+  ff* f = reinterpret_cast<ff*>(base);
+  m.M = f;
+  f += n1 * n1;
+  m.tau = f;
+  m.S = f + n1;
+  m.v = f + 2 * n1;
+  m.xh = f + 3 * n1;
+  m.w = f + 4 * n1;
+  float* g = reinterpret_cast<float*>(f + 5 * n1);
+  m.L = g;
+  m.dinv = g + n1 * n1;
+  m.sgn = g + n1 * n1 + n1;
+  return m;
+}
+
+// (M v)_r of the lane's row (zero for lanes r >= n)
+__device__ __forceinline__ ff warp_mrow(const WarpSolveMem& m, int n1, int n, int r, const ff* v) {
+  ff acc{0.f, 0.f};
+  if (r < n)
+    for (int j = 0; j < n; ++j) acc = ff_sum(acc, ff_prod(m.M[r * n1 + j], v[j]));
+  return acc;
+}
+
+// L L^T = D^-1 M D^-1 in FP32 (the same operations as cholesky_rdiag): step j
+// finishes column j, every row below it in its own lane.
+__device__ __forceinline__ bool warp_cholesky(const WarpSolveMem& m, int n1, int n, int r) {
+  for (int j = 0; j < n; ++j) {
+    __syncwarp();
+    float s = 0.f;
+    if (r == j) {
+      s = m.L[j * n1 + j];
+      for (int k = 0; k < j; ++k) s = __fmaf_rn(-m.L[j * n1 + k], m.L[j * n1 + k], s);
+    }
+    s = __shfl_sync(FULL_MASK, s, j);
+    if (!(s > 0.f) || !isfinite(s)) return false;
+    const float inv = __frsqrt_rn(s);
+    if (r == j) m.L[j * n1 + j] = inv;
+    if (r > j && r < n) {
+      float v = m.L[r * n1 + j];
+      for (int k = 0; k < j; ++k) v = __fmaf_rn(-m.L[r * n1 + k], m.L[j * n1 + k], v);
+      m.L[r * n1 + j] = __fmul_rn(v, inv);
+    }
+  }
+  __syncwarp();
+  return true;
+}
+
+// (L L^T)^-1 b, lane r holding b_r and receiving the solution's entry r:
+// forward then backward substitution, one unknown per step.
+__device__ __forceinline__ float warp_llt(const WarpSolveMem& m, int n1, int n, int r, float b) {
+  const float dg = r < n ? m.L[r * n1 + r] : 0.f;
+  float acc = b, y = 0.f;
+  for (int j = 0; j < n; ++j) {
+    const float yj = __shfl_sync(FULL_MASK, __fmul_rn(acc, dg), j);
+    if (r == j) y = yj;
+    if (r > j && r < n) acc = __fmaf_rn(-m.L[r * n1 + j], yj, acc);
+  }
+  acc = y;
+  float x = 0.f;
+  for (int j = n - 1; j >= 0; --j) {
+    const float xj = __shfl_sync(FULL_MASK, __fmul_rn(acc, dg), j);
+    if (r == j) x = xj;
+    if (r < j) acc = __fmaf_rn(-m.L[j * n1 + r], xj, acc);
+  }
+  return x;
+}
+
+// M^-1 rhs (lane r: rhs_r in, x_r out) through the FP32 factor, refined `steps`
+// times against the float-float M. Uses m.v.
+__device__ __forceinline__ bool warp_refined_solve(const WarpSolveMem& m, int n1, int n, int r, ff rhs, ff& x,
+                                                   int steps) {
+  const float di = r < n ? m.dinv[r] : 0.f;
+  x = ff{0.f, 0.f};
+  bool ok = true;
+  for (int it = 0; it <= steps && ok; ++it) {
+    ff res = rhs;
+    if (it > 0) {
+      __syncwarp();
+      if (r < n) m.v[r] = x;
+      __syncwarp();
+      res = ff_sum(rhs, ff_neg(warp_mrow(m, n1, n, r, m.v)));
+    }
+    const float dx = warp_llt(m, n1, n, r, __fmul_rn(res.h, di));
+    x = ff_sum(x, ff{__fmul_rn(dx, di), 0.f});
+    ok = __all_sync(FULL_MASK, r >= n || isfinite(x.h));
+  }
+  return ok;
+}
+
+__global__ void __launch_bounds__(WARP_SOLVE_MAX_WARPS * 32) k_solve_sums_warp(EvalArgs a, double* cost,
+                                                                               double* weights, double* grad) {
+  extern __shared__ __align__(16) unsigned char warp_solve_smem[];
+  const int64_t Q = a.sc.Q;
+  const int nmax = a.sc.nmax, nm1 = nmax + 1, n1 = nm1;
+  const int r = (int)threadIdx.x & 31, wid = (int)threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
+  const WarpSolveMem m = warp_solve_mem(warp_solve_smem + (size_t)wid * warp_solve_bytes(n1), n1);
+  const ff one_lam = ff_of(1.0 + a.lam);
+  for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
+    const Unit u = a.units[ui];
+    const int N = u.N, n = N + 1;
+    const ff kk = ff_of((double)(u.k1 - u.k0));
+    for (int q = u.q0 + wid; q < u.q1; q += nw) {   // warp-uniform from here on
+      if (a.active && !a.active[q]) continue;
+      // row r >= 1 is pole r - 1: tau (from the column-sum pass), S and h
+      ff hv{0.f, 0.f}, gd{0.f, 0.f};
+      __syncwarp();
+      if (r == 0) {
+        hv = ff_of(a.h0[u.s]);
+        gd = kk;
+      } else if (r < n) {
+        m.tau[r] = ff_of(a.sc.x[(int64_t)(r - 1) * Q + q]);
+        gd = ff_of(a.sc.G[(int64_t)(r - 1) * Q + q]);
+        m.S[r] = gd;
+        hv = ff_of(a.sc.G[(int64_t)(N + r - 1) * Q + q]);
+      }
+      if (r < n) m.dinv[r] = __frsqrt_rn(gd.h);
+      __syncwarp();
+      // row r of M and of the scaled FP32 matrix (unit diagonal + lam)
+      if (r < n) {
+        const float dr = m.dinv[r];
+        for (int j = 0; j < n; ++j) {
+          ff g;
+          if (j == r) g = gd;
+          else if (r == 0) g = m.S[j];
+          else if (j == 0) g = gd;
+          else
+            g = ff_quot(ff_sum(ff_prod(m.tau[r], m.S[r]), ff_prod(m.tau[j], m.S[j])), ff_sum(m.tau[r], m.tau[j]));
+          m.M[r * n1 + j] = (j == r) ? ff_prod(g, one_lam) : g;
+          if (j < r) m.L[r * n1 + j] = __fmul_rn(__fmul_rn(g.h, dr), m.dinv[j]);
+        }
+        m.L[r * n1 + r] = (float)(1.0 + a.lam);
+      }
+      bool ok = warp_cholesky(m, n1, n, r);
+      ff x{0.f, 0.f};
+      if (ok) ok = warp_refined_solve(m, n1, n, r, hv, x, grad ? SUMS_REFINE : SUMS_REFINE_COST);
+      if (r == 0) a.sc.fail[q] = ok ? 0 : 1;
+      if (!ok) {
+        if (cost && r == 0) cost[q] = INFINITY;
+        if (weights && r < nm1) weights[(int64_t)q * nm1 + r] = 0.0;
+        if (grad && r < nmax) grad[(int64_t)q * nmax + r] = 0.0;
+        continue;
+      }
+      // sign flip of negative d_eps (Sec. III-B), then the exact quadratic cost
+      const float sg = (r > 0 && r < n && x.h < 0.f) ? -1.f : 1.f;
+      if (sg < 0.f) x = ff_neg(x);
+      __syncwarp();
+      if (r < n) {
+        m.v[r] = x;
+        m.xh[r] = x;
+        m.sgn[r] = sg;
+      }
+      __syncwarp();
+      const ff mx = warp_mrow(m, n1, n, r, m.v);   // (M x_hat)_r
+      ff t{0.f, 0.f};
+      if (r < n) {
+        t = ff_neg(ff_prod(ff{__fmul_rn(2.f, x.h), __fmul_rn(2.f, x.l)}, hv));
+        t = ff_sum(t, ff_prod(x, mx));
+      }
+      for (int o = 16; o > 0; o >>= 1) t = ff_sum(t, ff{__shfl_xor_sync(FULL_MASK, t.h, o),
+                                                        __shfl_xor_sync(FULL_MASK, t.l, o)});
+      double cv = ff_dbl(ff_sum(ff_of(a.bb[u.s]), t));
+      if (!isfinite(cv)) cv = INFINITY;
+      if (cv < 0.0) cv = 0.0;
+      if (cost && r == 0) cost[q] = cv;
+      if (weights && r < nm1) weights[(int64_t)q * nm1 + r] = r < n ? ff_dbl(x) : 0.0;
+      if (!grad) continue;
+      // adjoint w = M^-1 (s * (M x_hat - h))
+      ff rw{0.f, 0.f};
+      if (r < n) {
+        rw = ff_sum(mx, ff_neg(hv));
+        if (sg < 0.f) rw = ff_neg(rw);
+      }
+      ff w;
+      if (!warp_refined_solve(m, n1, n, r, rw, w, SUMS_REFINE)) {
+        if (r < nmax) grad[(int64_t)q * nmax + r] = 0.0;
+        continue;
+      }
+      __syncwarp();
+      if (r < n) m.w[r] = w;
+      __syncwarp();
+      // d cost / d theta_i in lane r = i + 1 (the formula of k_solve_sums)
+      if (r >= 1 && r <= nmax) {
+        const int i = r - 1;
+        double gi = 0.0;
+        if (i < N) {
+          const ff ln10 = ff_of(2.302585092994046);
+          const ff Di = ff_of(a.sc.G[(int64_t)(2 * N + i) * Q + q]);
+          const ff Ei = ff_of(a.sc.G[(int64_t)(3 * N + i) * Q + q]);
+          const ff ti = m.tau[r], Si = m.S[r];
+          ff ax = ff_prod(Di, m.xh[0]), aw = ff_prod(Di, m.w[0]), as = ax;
+          for (int j = 1; j < n; ++j) {
+            if (j == r) continue;
+            const ff rr = ff_quot(ff{1.f, 0.f}, ff_sum(ti, m.tau[j]));
+            const ff t1 = ff_prod(ff_prod(ti, Di), rr);
+            const ff t2 = ff_prod(ff_prod(ff_prod(ln10, ff_prod(ti, m.tau[j])), ff_sum(Si, ff_neg(m.S[j]))),
+                                  ff_prod(rr, rr));
+            const ff row = ff_sum(t1, t2);
+            const ff xj = m.xh[j];
+            const ff xs = m.sgn[j] < 0.f ? ff_neg(xj) : xj;
+            ax = ff_sum(ax, ff_prod(row, xj));
+            aw = ff_sum(aw, ff_prod(row, m.w[j]));
+            as = ff_sum(as, ff_prod(row, xs));
+          }
+          const ff diag = ff_prod(Di, one_lam);
+          const ff xhI = x, wI = w;
+          const ff xsI = sg < 0.f ? ff_neg(xhI) : xhI;
+          const ff x2{__fmul_rn(2.f, xhI.h), __fmul_rn(2.f, xhI.l)};
+          ff gsum = ff_neg(ff_prod(x2, Ei));
+          gsum = ff_sum(gsum, ff_prod(x2, ax));
+          gsum = ff_sum(gsum, ff_prod(diag, ff_prod(xhI, xhI)));
+          ff adj = ff_prod(wI, Ei);
+          adj = ff_sum(adj, ff_neg(ff_prod(wI, as)));
+          adj = ff_sum(adj, ff_neg(ff_prod(xsI, aw)));
+          adj = ff_sum(adj, ff_neg(ff_prod(diag, ff_prod(wI, xsI))));
+          gsum = ff_sum(gsum, ff{__fmul_rn(2.f, adj.h), __fmul_rn(2.f, adj.l)});
+          gi = ff_dbl(gsum);
+        }
+        grad[(int64_t)q * nmax + i] = gi;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ gradient
 // w = M^-1 S g_hat with g_hat = g1 - M (x_hat - x1) = h - M x_hat,
 // S = diag(1, sign x1_1, ..., sign x1_N).
@@ -532,6 +788,22 @@ static int grid_for(int n_units, int sms, int per_sm) {
 void launch_solve_sums(const EvalArgs& a, double* cost, double* weights, double* grad, int block, int sms,
                        cudaStream_t st) {
   if (a.n_units) k_solve_sums<<<grid_for(a.n_units, sms, 32), block, 0, st>>>(a, cost, weights, grad);
+}
+
+bool solve_sums_by_warp(int64_t Q, int lanes, int sms) {
+  if (lanes == 1 || lanes == 32) return lanes == 32;
+  return Q <= (int64_t)sms * WARP_SOLVE_MAX_Q_PER_SM;
+}
+
+// A block of up to 8 warps (one candidate each) per unit, within the default 48 KB
+// of shared memory (6.3 KB per warp at 20 poles).
+void launch_solve_sums_warp(const EvalArgs& a, double* cost, double* weights, double* grad, int cands_per_unit,
+                            int sms, cudaStream_t st) {
+  if (!a.n_units) return;
+  const size_t per = warp_solve_bytes(a.sc.nmax + 1);
+  int warps = std::max(1, std::min(WARP_SOLVE_MAX_WARPS, cands_per_unit));
+  while (warps > 1 && (size_t)warps * per > 48 * 1024) --warps;
+  k_solve_sums_warp<<<grid_for(a.n_units, sms, 16), warps * 32, warps * per, st>>>(a, cost, weights, grad);
 }
 
 void launch_solve(const EvalArgs& a, int block, int sms, cudaStream_t st) {

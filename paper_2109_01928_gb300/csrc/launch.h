@@ -70,6 +70,13 @@ void launch_prep(int64_t n_samples, int64_t S, const int64_t* offsets, const dou
 // after the pass with derivative sums) the gradient in theta.
 void launch_solve_sums(const EvalArgs& a, double* cost, double* weights, double* grad, int block, int sms,
                        cudaStream_t st);
+// The same with one warp per candidate (lane r: row r of the small systems), for
+// evaluations too small to fill the GPU one thread per candidate. solve_sums_by_warp
+// picks it: lanes 1 or 32 force a kernel, 0 takes the warp kernel when the
+// evaluation has at most 256 candidates per SM.
+bool solve_sums_by_warp(int64_t Q, int lanes, int sms);
+void launch_solve_sums_warp(const EvalArgs& a, double* cost, double* weights, double* grad, int cands_per_unit,
+                            int sms, cudaStream_t st);
 inline int warp_round(int n) { return (n + 31) / 32 * 32; }
 void launch_solve(const EvalArgs& a, int block, int sms, cudaStream_t st);
 void launch_finish(const EvalArgs& a, int final_step, double* cost, double* weights, double* g1,

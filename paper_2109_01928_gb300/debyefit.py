@@ -50,7 +50,8 @@ class Options(ctypes.Structure):
                 ("lbfgs_max_trials", ctypes.c_int32), ("lbfgs_c1", ctypes.c_double),
                 ("cands_per_block", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
                 ("de_f_lo", ctypes.c_double), ("de_f_hi", ctypes.c_double), ("de_cr", ctypes.c_double),
-                ("de_strategy", ctypes.c_int32), ("da_t0", ctypes.c_double), ("da_qa", ctypes.c_double)]
+                ("de_strategy", ctypes.c_int32), ("da_t0", ctypes.c_double), ("da_qa", ctypes.c_double),
+                ("solve_lanes", ctypes.c_int32)]
 
 
 class SpectraC(ctypes.Structure):

@@ -36,6 +36,7 @@ def test_default_options(lib):
     assert o.lbfgs_m == 8 and o.lbfgs_max_trials == 20 and o.lbfgs_c1 == 1e-4
     assert (o.de_f_lo, o.de_f_hi, o.de_cr, o.de_strategy) == (0.5, 1.0, 0.7, D.DE_RAND1)
     assert (o.da_t0, o.da_qa) == (5230.0, -5.0)
+    assert o.solve_lanes == 0
 
 
 def test_init_rejects_bad_options(lib):
@@ -47,7 +48,7 @@ def test_init_rejects_bad_options(lib):
     o.cands_per_block = 48
     assert lib.debye_fit_init(ctypes.byref(h), ctypes.byref(o)) == D.DEBYE_EINVAL
     for field, bad in (("de_cr", 1.5), ("de_f_lo", -0.1), ("de_f_hi", 0.25), ("de_strategy", 2),
-                       ("da_t0", 0.0), ("da_qa", 1.0)):
+                       ("da_t0", 0.0), ("da_qa", 1.0), ("solve_lanes", 2), ("solve_lanes", 16)):
         o = D.default_options()
         setattr(o, field, bad)
         assert lib.debye_fit_init(ctypes.byref(h), ctypes.byref(o)) == D.DEBYE_EINVAL
@@ -75,7 +76,8 @@ int main(void) {
   printf("%zu\n", offsetof(debye_spectra, n_poles_host));
   printf("%zu %zu %zu\n", offsetof(debye_options, de_f_lo), offsetof(debye_options, de_strategy),
          offsetof(debye_search, method));
-  printf("%zu %zu\n", offsetof(debye_options, da_t0), offsetof(debye_options, da_qa));
+  printf("%zu %zu %zu\n", offsetof(debye_options, da_t0), offsetof(debye_options, da_qa),
+         offsetof(debye_options, solve_lanes));
   return 0;
 }
 ''')
@@ -99,3 +101,4 @@ int main(void) {
     assert vals[9] == D.Options.de_strategy.offset
     assert vals[10] == D.SearchC.method.offset
     assert vals[11] == D.Options.da_t0.offset and vals[12] == D.Options.da_qa.offset
+    assert vals[13] == D.Options.solve_lanes.offset

@@ -73,14 +73,19 @@ def test_synth_matches_oracle(D):
 
 # ------------------------------------------------------------------ per-candidate cost
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_eval_population_ragged(D, prec):
+# the mixed path's small-system solve in both forms: one thread per candidate
+# (solve_lanes 1) and one warp per candidate (32, the default at these sizes)
+PREC_LANES = [("fp64", 0), ("mixed", 1), ("mixed", 32)]
+
+
+@pytest.mark.parametrize("prec,lanes", PREC_LANES)
+def test_eval_population_ragged(D, prec, lanes):
     b = ragged_batch()
     re, im = models.synthesize(b)
     th = W.population(b, 70, seed=9)
     ref, wref = oracle_costs(b, re, im, th)
     sp = spectra_for(D, b, re, im)
-    with D.Handle(prec) as h:
+    with D.Handle(prec, solve_lanes=lanes) as h:
         cost, w = D.debye_eval_population(h, sp, torch.as_tensor(th, device="cuda"), weights=True)
         D.debye_sync(h)
     cost, w = cost.cpu().numpy(), w.cpu().numpy()
@@ -147,8 +152,8 @@ def test_duplicate_tau_and_tiny_k(D):
     th = W.population(b, 8, seed=1)
     th[:, :, 1] = th[:, :, 0]                     # two identical relaxation times
     ref, _ = oracle_costs(b, re, im, th)
-    for prec in ("fp64", "mixed"):
-        with D.Handle(prec) as h:
+    for prec, lanes in PREC_LANES:
+        with D.Handle(prec, solve_lanes=lanes) as h:
             cost = D.debye_eval_population(h, spectra_for(D, b, re, im), torch.as_tensor(th, device="cuda"))
         assert (np.abs(cost.cpu().numpy() - ref) / ref).max() <= 10 * COST_TOL[prec]
 
@@ -180,12 +185,12 @@ def test_input_errors(D):
 
 # ------------------------------------------------------------------ gradient
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_cost_grad_matches_oracle(D, prec):
+@pytest.mark.parametrize("prec,lanes", PREC_LANES)
+def test_cost_grad_matches_oracle(D, prec, lanes):
     b = W.mixed_batch(S=6, seed=12, P=40, K_range=(60, 500), N_range=(2, 9))
     re, im = models.synthesize(b)
     th = W.population(b, 40, seed=3)
-    with D.Handle(prec) as h:
+    with D.Handle(prec, solve_lanes=lanes) as h:
         cost, grad = D.debye_cost_grad(h, spectra_for(D, b, re, im), torch.as_tensor(th, device="cuda"))
         D.debye_sync(h)
     cost, grad = cost.cpu().numpy(), grad.cpu().numpy()

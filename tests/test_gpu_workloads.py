@@ -107,13 +107,14 @@ def test_tabulated_full_size_sampled(D):
         assert abs(cost[s, p] - ref) <= COST_TOL["mixed"] * ref, (s, p, cost[s, p], ref)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_tabulated_cost_grad_sampled(D, prec):
+@pytest.mark.parametrize("prec,lanes", [("fp64", 0), ("mixed", 1), ("mixed", 32)])
+def test_tabulated_cost_grad_sampled(D, prec, lanes):
     # N = 20, K = 4096 noisy Debye-sum spectra: cost and gradient of sampled candidates
+    # (mixed: the small-system solve one thread and one warp per candidate)
     b = W.workload("tabulated_16384_k4096").subset(np.arange(32))
     re, im = models.synthesize(b)
     th = W.population(b, 64, seed=4)
-    with D.Handle(prec) as h:
+    with D.Handle(prec, solve_lanes=lanes) as h:
         cost, grad = D.debye_cost_grad(h, _spectra(D, b, re, im), torch.as_tensor(th, device="cuda"))
         D.debye_sync(h)
     cost, grad = cost.cpu().numpy(), grad.cpu().numpy()
