@@ -101,7 +101,9 @@ int debye_ctx::prof_collect() {
 static double flops_per_cand_k(int phase, int N) {
   if (phase == PH_GRAM) return 4.0 * N + 2.0 * (N + 2) * (N + 2);
   if (phase == PH_REFINE) return 13.0 * N + 5.0;
-  if (phase == PH_SUMS) return 68.0 * N;
+  // column sums: FP32 operations per (sample, pole) of the float-float sequence (FMA = 2);
+  // the squared form (N <= SQUARED_MAX_N) takes 54 of the general form's 68
+  if (phase == PH_SUMS) return (N <= SQUARED_MAX_N ? 54.0 : 68.0) * N;
   if (phase == PH_SUMSG) return 152.0 * N;
   return 0.0;
 }
@@ -155,8 +157,8 @@ int debye_ctx::load_plan(const debye_spectra* sp, Plan& pl, cudaStream_t st) {
 
 int debye_ctx::prep_spectra(const debye_spectra* sp, const Plan& pl, cudaStream_t st) {
   int rc;
-  if ((rc = ensure(ws_kf32, sizeof(float4) * std::max<int64_t>(pl.n_samples, 1), "kf32"))) return rc;
-  if ((rc = ensure(ws_kff, sizeof(float4) * std::max<int64_t>(pl.n_samples, 1), "kff"))) return rc;
+  if ((rc = ensure(ws_kf32, sizeof(float4) * 2 * std::max<int64_t>(pl.n_samples, 1), "kf32"))) return rc;
+  if ((rc = ensure(ws_kff, sizeof(float4) * 2 * std::max<int64_t>(pl.n_samples, 1), "kff"))) return rc;
   if ((rc = ensure(ws_h0, sizeof(double) * 2 * std::max<int64_t>(pl.S, 1), "h0"))) return rc;
   launch_prep(pl.n_samples, pl.S, sp->offsets, sp->omega, sp->eps_re, sp->eps_im, sp->lo, sp->hi,
               (float4*)ws_kf32.p, (float4*)ws_kff.p, (double*)ws_h0.p, d_status, sms, st);
@@ -366,6 +368,8 @@ static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_
   a.theta = theta;
   a.kf32 = (const float4*)h->ws_kf32.p;
   a.kff = (const float4*)h->ws_kff.p;
+  a.kq32 = a.kf32 + pl.n_samples;
+  a.kqff = a.kff + pl.n_samples;
   a.omega = sp->omega;
   a.eps_re = sp->eps_re;
   a.eps_im = sp->eps_im;

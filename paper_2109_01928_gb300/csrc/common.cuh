@@ -22,6 +22,9 @@ constexpr int NPACK_MAX = NMAX1 * (NMAX1 + 1) / 2;
 __host__ __device__ constexpr int pk(int I, int J) { return I * (I + 1) / 2 + J; }
 
 enum Phase { PH_GRAM = 0, PH_REFINE = 1, PH_GRAD = 2, PH_SUMS = 3, PH_SUMSG = 4 };
+// Cost-only column sums take the squared form (eval.cuh, sums_sq_unit) up to this
+// pole count: 8 registers per pole fit the 168-register cap of that pass up to 12.
+constexpr int SQUARED_MAX_N = 12;
 
 struct Unit {
   int32_t s;    // spectrum
@@ -54,6 +57,8 @@ struct EvalArgs {
   const double* theta;     // [Q][nmax] log10 tau
   const float4* kf32;      // [sum K] {omega_hi, eps'_hi, eps''_hi, 0}
   const float4* kff;       // [sum K] {omega_lo, eps'_lo, eps''_lo, 0}
+  const float4* kq32;      // [sum K] {(omega 2^-30)^2, eps', omega eps''} high parts
+  const float4* kqff;      // [sum K] their low parts (float-float)
   const double* omega;     // [sum K] FP64 inputs
   const double* eps_re;
   const double* eps_im;

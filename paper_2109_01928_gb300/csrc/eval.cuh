@@ -306,6 +306,85 @@ __device__ __forceinline__ void sums_unit(const EvalArgs& a, const Unit& u) {
   }
 }
 
+// ------------------------------------------------------------------ column-sum pass, squared form (mixed, cost only)
+// The cost-only sums of sums_unit with fewer operations per (sample, pole): the
+// basis needs only x^2 = omega^2 tau^2, one float-float product of per-sample
+// omega^2 and per-candidate tau^2 (both scaled by 2^-60 / 2^60, exactly, to keep
+// them far from the float range limits), and with im = x re = omega tau re,
+//   h_i = sum_k re_i(k) eps'_k + tau_i sum_k re_i(k) (omega_k eps''_k),
+// two float-float dot products on the per-sample eps' and omega eps''
+// (k_prep_samples stores {omega^2, eps', omega eps''} in a.kq32 / a.kqff).
+// 1 + x^2 takes Fast2Sum on (max, min). The outputs are those of sums_unit.
+template <int N>
+__device__ __forceinline__ void sums_sq_unit(const EvalArgs& a, const Unit& u) {
+  const Lane ln = lane_of(a, u, false);
+  const int q = ln.act ? ln.q : u.q0;
+  const double* th = a.theta + (int64_t)q * a.sc.nmax;
+  const int64_t Q = a.sc.Q;
+  const int64_t kbeg = u.k0 + ln.slice;
+  const int64_t kend = ln.act ? u.k1 : kbeg;
+  const int64_t step = ln.ks;
+  float t2h[N], t2l[N], sh[N], sl[N], ah[N], al[N], ch[N], cl[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    t2h[i] = t2l[i] = 0.f;
+    if (ln.act) {
+      const double t = exp10(th[i]);
+      const double ts = t * 0x1p30;
+      split_double(ts * ts, t2h[i], t2l[i]);
+      if (ln.slice == 0) a.sc.x[(int64_t)i * Q + q] = t;   // tau for k_solve_sums and the epilogue
+    }
+    sh[i] = 1.f;
+    sl[i] = ah[i] = al[i] = ch[i] = cl[i] = 0.f;
+  }
+  const int64_t k0s = kbeg < u.k1 ? kbeg : u.k0;
+  float4 vhn = __ldg(&a.kq32[k0s]), vln = __ldg(&a.kqff[k0s]);
+#pragma unroll 1
+  for (int64_t k = kbeg; k < kend; k += step) {
+    const float4 vh = vhn, vl = vln;
+    if (k + step < kend) {   // next sample in flight during this one
+      vhn = __ldg(&a.kq32[k + step]);
+      vln = __ldg(&a.kqff[k + step]);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      // x^2 in float-float (the product of the low parts, ~2^-48, is dropped)
+      const float x2h = __fmul_rn(vh.x, t2h[i]);
+      float x2l = __fmaf_rn(vh.x, t2h[i], -x2h);
+      x2l = __fmaf_rn(vh.x, t2l[i], __fmaf_rn(vl.x, t2h[i], x2l));
+      // d = 1 + x^2: Fast2Sum of (max, min), exact
+      const float big = fmaxf(1.f, x2h), small = fminf(1.f, x2h);
+      const float dh = __fadd_rn(big, small);
+      const float dl = __fadd_rn(__fsub_rn(small, __fsub_rn(dh, big)), x2l);
+      // re = 1/d: approximate reciprocal and one Newton step on the float-float d
+      const float r0 = rcp_approx(dh);
+      float e = __fmaf_rn(-dh, r0, 1.0f);
+      e = __fmaf_rn(-dl, r0, e);
+      const float rl = __fmul_rn(r0, e);
+      const float gs = __fadd_rn(sh[i], r0);                         // Fast2Sum, sh >= 1 >= re
+      sl[i] = __fadd_rn(sl[i], __fadd_rn(__fsub_rn(r0, __fsub_rn(gs, sh[i])), rl));
+      sh[i] = gs;
+      ff_add_prod(ah[i], al[i], r0, rl, vh.y, vl.y);                 // re eps'
+      ff_add_prod(ch[i], cl[i], r0, rl, vh.z, vl.z);                 // re omega eps''
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    group_sum_ff(sh[i], sl[i], ln.ks);
+    group_sum_ff(ah[i], al[i], ln.ks);
+    group_sum_ff(ch[i], cl[i], ln.ks);
+  }
+  if (ln.act && ln.slice == 0) {
+    double* G = a.sc.G;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      G[(int64_t)i * Q + q] = ((double)sh[i] - (double)ln.ks) + (double)sl[i];
+      G[(int64_t)(N + i) * Q + q] =
+          ((double)ah[i] + (double)al[i]) + a.sc.x[(int64_t)i * Q + q] * ((double)ch[i] + (double)cl[i]);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ gradient pass
 // With x1 (unflipped, sc.x), x_hat (flipped, sc.xh) and w = M^-1 S g_hat (sc.w):
 //   gt[i]        = a_i'^T r_hat,  r_hat = b - A x_hat
@@ -395,6 +474,7 @@ template <int PH, int N>
 __device__ __forceinline__ void run_phase(const EvalArgs& a, const Unit& u) {
   if constexpr (PH == PH_GRAM) gram_unit<N>(a, u);
   else if constexpr (PH == PH_REFINE) refine_unit<N>(a, u);
+  else if constexpr (PH == PH_SUMS && N <= SQUARED_MAX_N) sums_sq_unit<N>(a, u);
   else if constexpr (PH == PH_SUMS) sums_unit<N, false>(a, u);
   else if constexpr (PH == PH_SUMSG) sums_unit<N, true>(a, u);
   else grad_unit<N>(a, u);

@@ -155,6 +155,8 @@ int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, in
   ea.theta = sa.x;
   ea.kf32 = (const float4*)h->ws_kf32.p;
   ea.kff = (const float4*)h->ws_kff.p;
+  ea.kq32 = ea.kf32 + pl.n_samples;
+  ea.kqff = ea.kff + pl.n_samples;
   ea.omega = sp->omega;
   ea.eps_re = sp->eps_re;
   ea.eps_im = sp->eps_im;

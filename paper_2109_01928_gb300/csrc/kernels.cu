@@ -9,8 +9,10 @@
 namespace debyefit {
 
 // ------------------------------------------------------------------ input preparation
-// Per sample: float-float split of omega, eps', eps'' for the mixed passes and
-// finiteness checks; per spectrum: h0 = sum_k eps'_k (FP64).
+// Per sample: float-float split of omega, eps', eps'' for the mixed passes (the
+// first n records of kf32 / kff) and of (omega 2^-30)^2, eps', omega eps'' for the
+// squared-form column sums (records n .. 2n - 1), and finiteness checks; per
+// spectrum: h0 = sum_k eps'_k and b^T b (FP64).
 __global__ void k_prep_samples(int64_t n, const double* __restrict__ omega,
                                const double* __restrict__ er, const double* __restrict__ ei,
                                float4* __restrict__ kf32, float4* __restrict__ kff, int* status) {
@@ -18,12 +20,17 @@ __global__ void k_prep_samples(int64_t n, const double* __restrict__ omega,
        k += (int64_t)gridDim.x * blockDim.x) {
     const double w = omega[k], a = er[k], b = ei[k];
     if (!(w > 0.0) || !isfinite(w) || !isfinite(a) || !isfinite(b)) set_status(status, DEBYE_ENOTFINITE);
-    float wh, wl, ah, al, bh, bl;
+    float wh, wl, ah, al, bh, bl, w2h, w2l, ch, cl;
     split_double(w, wh, wl);
     split_double(a, ah, al);
     split_double(b, bh, bl);
     kf32[k] = make_float4(wh, ah, bh, 0.f);
     kff[k] = make_float4(wl, al, bl, 0.f);
+    const double ws = w * 0x1p-30;
+    split_double(ws * ws, w2h, w2l);
+    split_double(w * b, ch, cl);
+    kf32[n + k] = make_float4(w2h, ah, ch, 0.f);
+    kff[n + k] = make_float4(w2l, al, cl, 0.f);
   }
 }
 

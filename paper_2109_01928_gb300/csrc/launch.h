@@ -62,6 +62,7 @@ inline void launch_pass(int N, int phase, const EvalArgs& a, int grid, int block
   }
 }
 
+// kf32, kff: [2 n_samples] records (the second half for the squared-form column sums);
 // h0: [2 S] doubles, sum_k eps'_k per spectrum, then b^T b per spectrum.
 void launch_prep(int64_t n_samples, int64_t S, const int64_t* offsets, const double* omega,
                  const double* er, const double* ei, const double* lo, const double* hi,

@@ -157,8 +157,8 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
   const int npk = nm1 * (nm1 + 1) / 2;
   int* status = (int*)cv.take(sizeof(int));
   Unit* d_units = (Unit*)cv.take(sizeof(Unit) * n_units);
-  float4* kf32 = (float4*)cv.take(sizeof(float4) * n_samples);
-  float4* kff = (float4*)cv.take(sizeof(float4) * n_samples);
+  float4* kf32 = (float4*)cv.take(sizeof(float4) * 2 * n_samples);
+  float4* kff = (float4*)cv.take(sizeof(float4) * 2 * n_samples);
   double* h0 = (double*)cv.take(sizeof(double) * 2 * S);   // sum eps', then b^T b
   Scratch sc{};
   sc.Q = Q;
@@ -202,6 +202,8 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
   a.theta = theta;
   a.kf32 = kf32;
   a.kff = kff;
+  a.kq32 = kf32 + n_samples;
+  a.kqff = kff + n_samples;
   a.omega = sp->omega;
   a.eps_re = sp->eps_re;
   a.eps_im = sp->eps_im;
