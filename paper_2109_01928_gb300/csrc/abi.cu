@@ -101,10 +101,10 @@ int debye_ctx::prof_collect() {
 static double flops_per_cand_k(int phase, int N) {
   if (phase == PH_GRAM) return 4.0 * N + 2.0 * (N + 2) * (N + 2);
   if (phase == PH_REFINE) return 13.0 * N + 5.0;
-  // column sums: FP32 operations per (sample, pole) of the float-float sequence (FMA = 2);
-  // the squared form (N <= SQUARED_MAX_N) takes 54 of the general form's 68
-  if (phase == PH_SUMS) return (N <= SQUARED_MAX_N ? 54.0 : 68.0) * N;
-  if (phase == PH_SUMSG) return 152.0 * N;
+  // column sums: FP32 operations per (sample, pole) of the float-float sequence in the
+  // squared form (FMA = 2): 54, and 103 with the derivative sums
+  if (phase == PH_SUMS) return 54.0 * N;
+  if (phase == PH_SUMSG) return 103.0 * N;
   return 0.0;
 }
 

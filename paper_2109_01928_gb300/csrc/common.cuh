@@ -22,9 +22,11 @@ constexpr int NPACK_MAX = NMAX1 * (NMAX1 + 1) / 2;
 __host__ __device__ constexpr int pk(int I, int J) { return I * (I + 1) / 2 + J; }
 
 enum Phase { PH_GRAM = 0, PH_REFINE = 1, PH_GRAD = 2, PH_SUMS = 3, PH_SUMSG = 4 };
-// Cost-only column sums take the squared form (eval.cuh, sums_sq_unit) up to this
-// pole count: 8 registers per pole fit the 168-register cap of that pass up to 12.
-constexpr int SQUARED_MAX_N = 12;
+// The column sums with the derivative sums (eval.cuh, sums_sq_unit) sweep the
+// samples once for up to this many poles (14 registers per pole) and twice, about
+// N/2 poles each, above it; the cost-only sums (8 registers per pole) always sweep
+// once.
+constexpr int SQUARED_CHUNK_GRAD = 11;
 
 struct Unit {
   int32_t s;    // spectrum
@@ -97,34 +99,6 @@ __device__ __forceinline__ void split_double(double v, float& hi, float& lo) {
   hi = __double2float_rn(v);
   lo = __double2float_rn(v - (double)hi);
 }
-
-// Float-float Debye basis value c = 1/(1 + j x) with x = omega * tau:
-// re = 1/(1+x^2), im = x/(1+x^2), each as hi + lo (about 2^-44 relative).
-// The reciprocal is the hardware approximation refined by one Newton-Raphson
-// step on the float-float denominator: r = r0 + r0 (1 - d r0).
-__device__ __forceinline__ void basis_ff(float wh, float wl, float th, float tl,
-                                         float& reh, float& rel, float& imh, float& iml,
-                                         float& xh_out) {
-  float xh = __fmul_rn(wh, th);
-  float xl = __fmaf_rn(wh, th, -xh);
-  xl = __fmaf_rn(wh, tl, __fmaf_rn(wl, th, xl));
-  float sh = __fmul_rn(xh, xh);
-  float sl = __fmaf_rn(xh, xh, -sh);
-  sl = __fmaf_rn(__fmul_rn(2.0f, xh), xl, sl);
-  float dh, de;
-  two_sum(1.0f, sh, dh, de);
-  float dl = __fadd_rn(de, sl);
-  float r0 = rcp_approx(dh);
-  float e = __fmaf_rn(-dh, r0, 1.0f);
-  e = __fmaf_rn(-dl, r0, e);
-  reh = r0;
-  rel = __fmul_rn(r0, e);
-  imh = __fmul_rn(xh, reh);
-  iml = __fmaf_rn(xh, reh, -imh);
-  iml = __fmaf_rn(xh, rel, __fmaf_rn(xl, reh, iml));
-  xh_out = xh;
-}
-
 
 // acc (hi, lo) += a * b, a and b float-float (one Dot2 step: TwoProduct by FMA,
 // TwoSum of the leading part, low-order terms gathered in lo).

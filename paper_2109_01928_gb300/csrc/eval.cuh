@@ -9,7 +9,7 @@
 // a few candidates (line-search points, one re-solve per spectrum).
 //
 // Mixed precision (float-float on the FP32 pipe):
-//   sums_unit    column sums S_i = sum re_i and h = A^T b of the Debye basis (and,
+//   sums_sq_unit column sums S_i = sum re_i and h = A^T b of the Debye basis (and,
 //                for the gradient, the same sums over the derivative columns),
 //                from which k_solve_sums forms the Gram, weights, cost and gradient.
 // FP64 precision:
@@ -200,142 +200,53 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
 //   S_i = sum_k re_i(k)                      (the pole block of the Gram follows from these)
 //   h_i = sum_k re_i(k) eps'_k + im_i(k) eps''_k   (A^T b without the eps_inf row)
 // and, with the gradient (GRAD), the same sums over the derivative columns
-// d/d theta_i (theta = log10 tau; via im = x re: d re = -2 ln10 im^2,
-// d im = ln10 im (re - x im)):
+// d/d theta_i (theta = log10 tau):
 //   D_i = sum_k d re_i(k),   E_i = sum_k d re_i(k) eps'_k + d im_i(k) eps''_k.
-// Writes tau_i = 10^theta_i to sc.x[i Q + q] (the FP64 power is done once per
-// candidate here rather than again in the solve), sc.G[i Q + q] = S_i,
-// sc.G[(N + i) Q + q] = h_i, and with GRAD
-// sc.G[(2N + i) Q + q] = D_i, sc.G[(3N + i) Q + q] = E_i. The same-sign sums S
-// (re <= 1) and -D (<= ln10 / 2) start from a bias (1, 2) so that Fast2Sum is
-// exact; the bias is removed at the end.
-template <int N, bool GRAD>
-__device__ __forceinline__ void sums_unit(const EvalArgs& a, const Unit& u) {
-  const Lane ln = lane_of(a, u, false);
-  const int q = ln.act ? ln.q : u.q0;
-  const double* th = a.theta + (int64_t)q * a.sc.nmax;
+// The basis needs only x^2 = omega^2 tau^2: one float-float product of the
+// per-sample omega^2 and the per-candidate tau^2 (scaled by 2^-60 and 2^60,
+// exactly, to keep both far from the float range limits); 1 + x^2 by Fast2Sum on
+// (max, min); re = 1/(1 + x^2) by the approximate reciprocal and one Newton step.
+// With im = x re = omega tau re,
+//   h_i = sum_k re_i(k) eps'_k + tau_i B_i,   B_i = sum_k re_i(k) (omega_k eps''_k),
+// two Dot2 sums on the per-sample eps' and omega eps'' (k_prep_samples stores
+// {omega^2, eps', omega eps''} in a.kq32 / a.kqff). With u = x^2 re^2 = re (1 - re),
+// d re / d theta = -2 ln10 u and d im / d theta = ln10 x re^2 (1 - x^2)
+// = ln10 omega tau (re - 2u), so
+//   D_i = -2 ln10 U_i,   E_i = ln10 (-2 V_i + tau_i (B_i - 2 W_i)),
+//   U = sum u,  V = sum u eps',  W = sum u (omega eps'').
+// The same-sign sums S (re <= 1) and U (u <= 1/4) start from a bias of 1 so that
+// Fast2Sum is exact; the bias is removed at the end. Writes tau_i = 10^theta_i to
+// sc.x[i Q + q] (the FP64 power is done once per candidate here rather than again
+// in the solve), sc.G[i Q + q] = S_i, sc.G[(N + i) Q + q] = h_i, and with GRAD
+// sc.G[(2N + i) Q + q] = D_i, sc.G[(3N + i) Q + q] = E_i.
+//
+// One sweep over the samples for poles P0 .. P0 + C - 1 of an N-pole candidate:
+template <int N, int P0, int C, bool GRAD>
+__device__ __forceinline__ void sums_sq_sweep(const EvalArgs& a, const Unit& u, const Lane& ln, int q) {
+  const double* th = a.theta + (int64_t)q * a.sc.nmax + P0;
   const int64_t Q = a.sc.Q;
   const int64_t kbeg = u.k0 + ln.slice;
   const int64_t kend = ln.act ? u.k1 : kbeg;
   const int64_t step = ln.ks;
-  constexpr float LN10H = 2.3025851249694824f;   // fl(ln 10)
-  constexpr float LN10L = -3.1975436e-08f;       // ln 10 - fl(ln 10)
-  constexpr int NG = GRAD ? N : 1;
-  float th_[N], tl_[N], sh[N], sl[N], hh[N], hl[N];
-  float dh[NG], dl[NG], eh[NG], el[NG];
+  constexpr int CG = GRAD ? C : 1;
+  float t2h[C], t2l[C], sh[C], sl[C], ah[C], al[C], ch[C], cl[C];
+  float uh[CG], ul[CG], vh_[CG], vl_[CG], wh[CG], wl[CG];
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    th_[i] = tl_[i] = 0.f;
-    if (ln.act) {
-      const double t = exp10(th[i]);
-      split_double(t, th_[i], tl_[i]);
-      if (ln.slice == 0) a.sc.x[(int64_t)i * Q + q] = t;   // tau for k_solve_sums
-    }
-    sh[i] = 1.f;
-    sl[i] = hh[i] = hl[i] = 0.f;
-  }
-#pragma unroll
-  for (int i = 0; i < NG; ++i) {
-    dh[i] = 2.f;
-    dl[i] = eh[i] = el[i] = 0.f;
-  }
-  const int64_t k0s = kbeg < u.k1 ? kbeg : u.k0;
-  float4 vhn = __ldg(&a.kf32[k0s]), vln = __ldg(&a.kff[k0s]);
-#pragma unroll 1
-  for (int64_t k = kbeg; k < kend; k += step) {
-    const float4 vh = vhn, vl = vln;
-    if (k + step < kend) {   // next sample in flight during this one
-      vhn = __ldg(&a.kf32[k + step]);
-      vln = __ldg(&a.kff[k + step]);
-    }
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      float reh, rel, imh, iml, xh;
-      basis_ff(vh.x, vl.x, th_[i], tl_[i], reh, rel, imh, iml, xh);
-      const float gs = __fadd_rn(sh[i], reh);                        // Fast2Sum, sh >= 1 >= reh
-      sl[i] = __fadd_rn(sl[i], __fadd_rn(__fsub_rn(reh, __fsub_rn(gs, sh[i])), rel));
-      sh[i] = gs;
-      ff_add_prod(hh[i], hl[i], reh, rel, vh.y, vl.y);
-      ff_add_prod(hh[i], hl[i], imh, iml, vh.z, vl.z);
-      if constexpr (GRAD) {
-        // x = w tau in float-float (basis_ff returned only its leading part)
-        float xl_ = __fmaf_rn(vh.x, th_[i], -xh);
-        xl_ = __fmaf_rn(vh.x, tl_[i], __fmaf_rn(vl.x, th_[i], xl_));
-        float s2h, s2l, ndh, ndl, ph, pl, dmh, dml, dih, dil;
-        ff_mul(imh, iml, imh, iml, s2h, s2l);                        // im^2
-        ff_mul(s2h, s2l, 2.0f * LN10H, 2.0f * LN10L, ndh, ndl);      // -d re / d theta >= 0
-        const float gd = __fadd_rn(dh[i], ndh);                      // Fast2Sum, dh >= 2 > ndh
-        dl[i] = __fadd_rn(dl[i], __fadd_rn(__fsub_rn(ndh, __fsub_rn(gd, dh[i])), ndl));
-        dh[i] = gd;
-        ff_mul(xh, xl_, imh, iml, ph, pl);                           // x im
-        two_sum(reh, -ph, dmh, dml);                                 // re - x im
-        dml = __fadd_rn(dml, __fsub_rn(rel, pl));
-        ff_mul(imh, iml, dmh, dml, ph, pl);
-        ff_mul(ph, pl, LN10H, LN10L, dih, dil);                      // d im / d theta
-        ff_add_prod(eh[i], el[i], -ndh, -ndl, vh.y, vl.y);
-        ff_add_prod(eh[i], el[i], dih, dil, vh.z, vl.z);
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    group_sum_ff(sh[i], sl[i], ln.ks);
-    group_sum_ff(hh[i], hl[i], ln.ks);
-  }
-#pragma unroll
-  for (int i = 0; i < NG; ++i) {
-    if constexpr (GRAD) {
-      group_sum_ff(dh[i], dl[i], ln.ks);
-      group_sum_ff(eh[i], el[i], ln.ks);
-    }
-  }
-  if (ln.act && ln.slice == 0) {
-    double* G = a.sc.G;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      G[(int64_t)i * Q + q] = ((double)sh[i] - (double)ln.ks) + (double)sl[i];
-      G[(int64_t)(N + i) * Q + q] = (double)hh[i] + (double)hl[i];
-    }
-    if constexpr (GRAD) {
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        G[(int64_t)(2 * N + i) * Q + q] = -(((double)dh[i] - 2.0 * (double)ln.ks) + (double)dl[i]);
-        G[(int64_t)(3 * N + i) * Q + q] = (double)eh[i] + (double)el[i];
-      }
-    }
-  }
-}
-
-// ------------------------------------------------------------------ column-sum pass, squared form (mixed, cost only)
-// The cost-only sums of sums_unit with fewer operations per (sample, pole): the
-// basis needs only x^2 = omega^2 tau^2, one float-float product of per-sample
-// omega^2 and per-candidate tau^2 (both scaled by 2^-60 / 2^60, exactly, to keep
-// them far from the float range limits), and with im = x re = omega tau re,
-//   h_i = sum_k re_i(k) eps'_k + tau_i sum_k re_i(k) (omega_k eps''_k),
-// two float-float dot products on the per-sample eps' and omega eps''
-// (k_prep_samples stores {omega^2, eps', omega eps''} in a.kq32 / a.kqff).
-// 1 + x^2 takes Fast2Sum on (max, min). The outputs are those of sums_unit.
-template <int N>
-__device__ __forceinline__ void sums_sq_unit(const EvalArgs& a, const Unit& u) {
-  const Lane ln = lane_of(a, u, false);
-  const int q = ln.act ? ln.q : u.q0;
-  const double* th = a.theta + (int64_t)q * a.sc.nmax;
-  const int64_t Q = a.sc.Q;
-  const int64_t kbeg = u.k0 + ln.slice;
-  const int64_t kend = ln.act ? u.k1 : kbeg;
-  const int64_t step = ln.ks;
-  float t2h[N], t2l[N], sh[N], sl[N], ah[N], al[N], ch[N], cl[N];
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
+  for (int i = 0; i < C; ++i) {
     t2h[i] = t2l[i] = 0.f;
     if (ln.act) {
       const double t = exp10(th[i]);
       const double ts = t * 0x1p30;
       split_double(ts * ts, t2h[i], t2l[i]);
-      if (ln.slice == 0) a.sc.x[(int64_t)i * Q + q] = t;   // tau for k_solve_sums and the epilogue
+      if (ln.slice == 0) a.sc.x[(int64_t)(P0 + i) * Q + q] = t;   // tau for k_solve_sums and the epilogue
     }
     sh[i] = 1.f;
     sl[i] = ah[i] = al[i] = ch[i] = cl[i] = 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < CG; ++i) {
+    uh[i] = 1.f;
+    ul[i] = vh_[i] = vl_[i] = wh[i] = wl[i] = 0.f;
   }
   const int64_t k0s = kbeg < u.k1 ? kbeg : u.k0;
   float4 vhn = __ldg(&a.kq32[k0s]), vln = __ldg(&a.kqff[k0s]);
@@ -347,7 +258,7 @@ __device__ __forceinline__ void sums_sq_unit(const EvalArgs& a, const Unit& u) {
       vln = __ldg(&a.kqff[k + step]);
     }
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
+    for (int i = 0; i < C; ++i) {
       // x^2 in float-float (the product of the low parts, ~2^-48, is dropped)
       const float x2h = __fmul_rn(vh.x, t2h[i]);
       float x2l = __fmaf_rn(vh.x, t2h[i], -x2h);
@@ -366,22 +277,65 @@ __device__ __forceinline__ void sums_sq_unit(const EvalArgs& a, const Unit& u) {
       sh[i] = gs;
       ff_add_prod(ah[i], al[i], r0, rl, vh.y, vl.y);                 // re eps'
       ff_add_prod(ch[i], cl[i], r0, rl, vh.z, vl.z);                 // re omega eps''
+      if constexpr (GRAD) {
+        float r2h, r2l, qh, ql;
+        ff_mul(r0, rl, r0, rl, r2h, r2l);                            // re^2
+        ff_mul(x2h, x2l, r2h, r2l, qh, ql);                          // u = x^2 re^2
+        const float gu = __fadd_rn(uh[i], qh);                       // Fast2Sum, uh >= 1 >= u
+        ul[i] = __fadd_rn(ul[i], __fadd_rn(__fsub_rn(qh, __fsub_rn(gu, uh[i])), ql));
+        uh[i] = gu;
+        ff_add_prod(vh_[i], vl_[i], qh, ql, vh.y, vl.y);             // u eps'
+        ff_add_prod(wh[i], wl[i], qh, ql, vh.z, vl.z);               // u omega eps''
+      }
     }
   }
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
+  for (int i = 0; i < C; ++i) {
     group_sum_ff(sh[i], sl[i], ln.ks);
     group_sum_ff(ah[i], al[i], ln.ks);
     group_sum_ff(ch[i], cl[i], ln.ks);
   }
+#pragma unroll
+  for (int i = 0; i < CG; ++i) {
+    if constexpr (GRAD) {
+      group_sum_ff(uh[i], ul[i], ln.ks);
+      group_sum_ff(vh_[i], vl_[i], ln.ks);
+      group_sum_ff(wh[i], wl[i], ln.ks);
+    }
+  }
   if (ln.act && ln.slice == 0) {
     double* G = a.sc.G;
+    constexpr double LN10 = 2.302585092994046;
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      G[(int64_t)i * Q + q] = ((double)sh[i] - (double)ln.ks) + (double)sl[i];
-      G[(int64_t)(N + i) * Q + q] =
-          ((double)ah[i] + (double)al[i]) + a.sc.x[(int64_t)i * Q + q] * ((double)ch[i] + (double)cl[i]);
+    for (int i = 0; i < C; ++i) {
+      const int64_t j = P0 + i;
+      const double t = a.sc.x[j * Q + q];
+      const double B = (double)ch[i] + (double)cl[i];
+      G[j * Q + q] = ((double)sh[i] - (double)ln.ks) + (double)sl[i];
+      G[(N + j) * Q + q] = ((double)ah[i] + (double)al[i]) + t * B;
+      if constexpr (GRAD) {
+        const double U = ((double)uh[i] - (double)ln.ks) + (double)ul[i];
+        const double V = (double)vh_[i] + (double)vl_[i];
+        const double W = (double)wh[i] + (double)wl[i];
+        G[(2 * N + j) * Q + q] = -2.0 * LN10 * U;
+        G[(3 * N + j) * Q + q] = LN10 * (-2.0 * V + t * (B - 2.0 * W));
+      }
     }
+  }
+}
+
+// With GRAD, more than SQUARED_CHUNK_GRAD poles take two sweeps of about N/2 poles
+// each (14 registers per pole); the cost-only sums (8 per pole) sweep once.
+template <int N, bool GRAD>
+__device__ __forceinline__ void sums_sq_unit(const EvalArgs& a, const Unit& u) {
+  const Lane ln = lane_of(a, u, false);
+  const int q = ln.act ? ln.q : u.q0;
+  if constexpr (!GRAD || N <= SQUARED_CHUNK_GRAD) {
+    sums_sq_sweep<N, 0, N, GRAD>(a, u, ln, q);
+  } else {
+    constexpr int C1 = (N + 1) / 2;
+    sums_sq_sweep<N, 0, C1, GRAD>(a, u, ln, q);
+    sums_sq_sweep<N, C1, N - C1, GRAD>(a, u, ln, q);
   }
 }
 
@@ -474,9 +428,8 @@ template <int PH, int N>
 __device__ __forceinline__ void run_phase(const EvalArgs& a, const Unit& u) {
   if constexpr (PH == PH_GRAM) gram_unit<N>(a, u);
   else if constexpr (PH == PH_REFINE) refine_unit<N>(a, u);
-  else if constexpr (PH == PH_SUMS && N <= SQUARED_MAX_N) sums_sq_unit<N>(a, u);
-  else if constexpr (PH == PH_SUMS) sums_unit<N, false>(a, u);
-  else if constexpr (PH == PH_SUMSG) sums_unit<N, true>(a, u);
+  else if constexpr (PH == PH_SUMS) sums_sq_unit<N, false>(a, u);
+  else if constexpr (PH == PH_SUMSG) sums_sq_unit<N, true>(a, u);
   else grad_unit<N>(a, u);
 }
 

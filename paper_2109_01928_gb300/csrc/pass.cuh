@@ -11,7 +11,8 @@ template <int N>
 void launch_pass_n(int phase, const EvalArgs& a, int grid, int block, cudaStream_t st) {
   // the cost-only column-sum pass up to 12 poles fits in 168 registers without
   // spills: cap it for 3 resident 128-thread blocks; larger N, the gradient
-  // variant and the FP64 passes keep the full register file
+  // variant and the FP64 passes keep the full register file (one sweep over the
+  // samples keeps a lone active lane's latency low in masked evaluations)
   constexpr int MB_SUMS = N <= 12 ? 3 : 1;
   constexpr int MAXT = N <= 12 ? 128 : 256;
   switch (phase) {

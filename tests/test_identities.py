@@ -5,6 +5,9 @@
   block of the Gram A^T A follows from the column sums S_i = sum_k re_i(k).
 * The damped cost of any x is a quadratic in x: with M = G + lam diag G,
   ||A x - b||^2 + lam sum G_jj x_j^2 = b^T b - 2 x^T h + x^T M x.
+* The squared form of the column sums: with x = w tau, re = 1/(1 + x^2),
+  im = x re and u = x^2 re^2, h_i = sum re_i eps' + tau_i sum re_i (w eps''),
+  d re/d theta = -2 ln10 u and d im/d theta = ln10 w tau (re - 2u) (theta = log10 tau).
 """
 import numpy as np
 
@@ -45,3 +48,32 @@ def test_damped_cost_is_a_quadratic_in_the_weights():
             x = rs.normal(0, 5, N + 1)
             direct = np.sum((A @ x - y) ** 2) + lam * np.sum(np.diag(G) * x * x)
             assert abs(y @ y - 2 * x @ h + x @ M @ x - direct) <= 1e-10 * (y @ y + direct)
+
+
+def test_squared_form_of_the_column_sums_and_their_derivatives():
+    b = W.mixed_batch(S=4, seed=6, P=8, K_range=(50, 400), N_range=(2, 12))
+    re_t, im_t = models.synthesize(b)
+    rs = np.random.default_rng(3)
+    for s in range(b.S):
+        a, c = b.offsets[s], b.offsets[s + 1]
+        om, e1, e2 = b.omega[a:c], re_t[a:c], im_t[a:c]
+        N = int(b.n_poles[s])
+        th = rs.uniform(-12, -6, N)
+        A = dls.basis(om, th)                              # rows: eps' block, then eps'' block
+        K = om.size
+        h = A.T @ dls.target(e1, e2)
+        tau = 10.0 ** th
+        x2 = (om[:, None] * tau[None, :]) ** 2
+        re = 1.0 / (1.0 + x2)
+        u = x2 * re * re
+        np.testing.assert_allclose(u, re * (1.0 - re), rtol=1e-12, atol=1e-15)   # 1 - re cancels for re ~ 1
+        hs = (re * e1[:, None]).sum(0) + tau * (re * (om * e2)[:, None]).sum(0)
+        np.testing.assert_allclose(hs, h[1:], rtol=1e-12)
+        # derivatives in theta against central differences of the basis columns
+        d = 1e-6
+        Ap, Am = dls.basis(om, th + d), dls.basis(om, th - d)
+        dre_fd = (Ap[:K, 1:] - Am[:K, 1:]) / (2 * d)
+        dim_fd = (Ap[K:, 1:] - Am[K:, 1:]) / (2 * d)
+        ln10 = np.log(10.0)
+        np.testing.assert_allclose(-2 * ln10 * u, dre_fd, rtol=1e-6, atol=1e-9)
+        np.testing.assert_allclose(ln10 * om[:, None] * tau * (re - 2 * u), dim_fd, rtol=1e-6, atol=1e-9)
