@@ -107,7 +107,9 @@ typedef struct {
                              after the column-sum pass: 1 = one thread per candidate, 32 =
                              one warp per candidate (lane r: row r), 0 = by size (default: a
                              warp per candidate when an evaluation has at most 256
-                             candidates per SM). Results agree to rounding either way. */
+                             candidates per SM). Results agree to rounding either way.
+                             debye_eval_population_noalloc always takes one thread per
+                             candidate. */
 } debye_options;
 
 /* A ragged batch of S spectra, CSR over frequency (all device memory unless _host). */
@@ -256,8 +258,8 @@ int debye_sync(debye_handle h, cudaStream_t stream);
  * interval runs from the fork to the join; the solves and the finish are single
  * launches. Per kind the library accumulates the number of passes, the summed
  * event time (ms) and the algorithmic FLOPs of the work, per candidate and
- * frequency sample (FMA counted as 2): mixed precision, 68N for the float-float
- * column-sum pass (152N with the derivative sums of a gradient evaluation);
+ * frequency sample (FMA counted as 2): mixed precision, 54N for the float-float
+ * column-sum pass (103N with the derivative sums of a gradient evaluation);
  * FP64, 4N + 2(N+2)^2 for the Gram pass (basis build plus the unique
  * Gram/right-hand-side products) and 13N + 5 for the residual pass.
  * Passes restricted by an activity mask (the polish line search and its accepted
