@@ -445,11 +445,9 @@ def main():
         "warmup": args.warmup, "ms_per_step": sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded HN/CC/CD/Jonscher/CRIM spectra, targets synthesised on the device)",
-        "config": {"workload": f"{WORKLOAD}: {S} spectra, K {int(b.K.min())}-{int(b.K.max())} "
-                               f"(sum {int(b.K.sum())}), N {int(b.n_poles.min())}-{int(b.n_poles.max())}, "
-                               f"P={b.P}, {iters} swarm generations after the first, top-{TOPK} x "
-                               f"{POLISH_ITERS} L-BFGS polish, mixed precision (float-float column sums, exact "
-                               f"Gram identity, FP32 factor refined in float-float)",
+        "config": {"workload": workload_desc(b, iters),
+                   "precision": "mixed (float-float column sums, exact Gram identity, FP32 factor refined "
+                                "in float-float)",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -498,6 +496,13 @@ def kernel_case(S: int, precision: str, P: int, n_poles: int = 0):
                       "mean_cost": float(c.mean())}))
 
 
+def workload_desc(b, iters) -> str:
+    """The timed workload, as both arms name it in `config`."""
+    return (f"{WORKLOAD}: {b.S} spectra, K {int(b.K.min())}-{int(b.K.max())} (sum {int(b.K.sum())}), "
+            f"N {int(b.n_poles.min())}-{int(b.n_poles.max())}, P={b.P}, {iters} swarm generations after the "
+            f"first, top-{TOPK} x {POLISH_ITERS} L-BFGS polish")
+
+
 def reference_arm(args, rank, world):
     """The FP64 oracle on the host cores, on bounded samples of the same workload."""
     if rank != 0:
@@ -517,7 +522,10 @@ def reference_arm(args, rank, world):
                       "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
                       "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                      "config": {"workload": WORKLOAD + " (oracle sample)"}, "cpu_baseline": cpu,
+                      "config": {"workload": workload_desc(W.workload(WORKLOAD), SETTINGS[WORKLOAD][1]),
+                                 "precision": "FP64 oracle (numpy, host cores)",
+                                 "sample": cpu["sample"], "parallelism": f"{cores} host processes"},
+                      "cpu_baseline": cpu,
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
