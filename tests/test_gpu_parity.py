@@ -130,6 +130,55 @@ def test_eval_full_size_sampled(D, prec):
         assert abs(cost[s, p] - ref) <= COST_TOL[prec] * ref, (s, p, cost[s, p], ref)
 
 
+def cond_strata(b, th):
+    """cond(A) of every candidate's basis (2-norm, by SVD) and its stratum index."""
+    edges = [1e3, 1e6, 1e9]
+    cond = np.empty(th.shape[:2])
+    for s in range(b.S):
+        a, c = b.offsets[s], b.offsets[s + 1]
+        N = int(b.n_poles[s])
+        sv = np.linalg.svd(dls.basis(b.omega[a:c], th[s, :, :N]), compute_uv=False)
+        cond[s] = sv[:, 0] / sv[:, -1]
+    return cond, np.searchsorted(edges, cond), ["<1e3", "1e3-1e6", "1e6-1e9", ">=1e9"]
+
+
+def strata_report(rel, idx, names):
+    lines = []
+    for k, nm in enumerate(names):
+        m = idx == k
+        if m.any():
+            lines.append(f"cond(A) {nm:>8s}: {int(m.sum()):5d} candidates, relative cost error "
+                         f"median {np.median(rel[m]):.2e}, max {rel[m].max():.2e}")
+    return "\n".join(lines)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cost_error_by_condition_number(D, prec):
+    # cost errors stratified by the conditioning of the undamped basis (near-
+    # repeated relaxation times push cond(A) past 1e9; the damping keeps the
+    # solved system well conditioned): the tolerance up to cond 1e9, and above
+    # it the allowance of exactly repeated poles (test_duplicate_tau_and_tiny_k)
+    b = W.mixed_batch(S=12, seed=17, P=48, K_range=(40, 600), N_range=(1, 20))
+    re, im = models.synthesize(b)
+    th = W.population(b, 48, seed=5)
+    rs = np.random.default_rng(2)
+    for s in range(b.S):
+        if b.n_poles[s] >= 2:
+            close = rs.choice(48, 16, replace=False)
+            th[s, close, 1] = th[s, close, 0] + 10.0 ** rs.uniform(-8, -2, 16)
+    ref, _ = oracle_costs(b, re, im, th)
+    with D.Handle(prec) as h:
+        cost = D.debye_eval_population(h, spectra_for(D, b, re, im), torch.as_tensor(th, device="cuda"))
+        D.debye_sync(h)
+    rel = np.abs(cost.cpu().numpy() - ref) / ref
+    cond, idx, names = cond_strata(b, th)
+    report = strata_report(rel.ravel(), idx.ravel(), names)
+    print("\n" + prec + "\n" + report)
+    assert (idx == len(names) - 1).sum() >= 20 and (idx == 0).sum() >= 20, report
+    assert rel[idx < len(names) - 1].max() <= COST_TOL[prec], report
+    assert rel.max() <= 10 * COST_TOL[prec], report
+
+
 def test_autotune_then_eval(D, tmp_path):
     b = W.mixed_batch(S=8, seed=4, P=96, K_range=(50, 300), N_range=(2, 10))
     re, im = models.synthesize(b)
