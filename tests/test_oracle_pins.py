@@ -228,6 +228,30 @@ def test_gradient_matches_central_differences(lam):
     assert n_flip > 0   # the penalised branch was exercised
 
 
+def test_gradient_envelope_form_without_flip():
+    # with no weight flipped the weights minimise the damped cost, so its total
+    # derivative equals the partial derivative at fixed weights (envelope theorem):
+    # d/d theta_i [||A x - b||^2 + lam sum_j G_jj x_j^2] with x held at x*(theta),
+    # here by central differences of the basis alone
+    om = grid(1e6, 1e10, 250)
+    re, im = models.split(models.havriliak_negami(om, 3.0, 25.0, 5e-10, 0.6, 0.7))
+    b = dls.target(re, im)
+    rng_ = np.random.default_rng(8)
+    checked = 0
+    for _ in range(40):
+        th = np.sort(rng_.uniform(-11.5, -7.5, 3))
+        x = dls.damped_solve(dls.basis(om, th), b, 1e-3)
+        if np.min(x[1:]) <= 1e-6 * np.abs(x).max():
+            continue
+        _, g = varpro.cost_grad(om, re, im, th, 1e-3)
+        h = 1e-6
+        env = np.array([(dls.cost_at(dls.basis(om, th + h * e), b, x, 1e-3)
+                         - dls.cost_at(dls.basis(om, th - h * e), b, x, 1e-3)) / (2 * h) for e in np.eye(3)])
+        assert np.max(np.abs(g - env)) <= 1e-6 * max(1.0, np.max(np.abs(env))), (th, g, env)
+        checked += 1
+    assert checked >= 5
+
+
 def test_gradient_zero_at_exact_fit():
     om = grid(1e6, 1e10, 300)
     tau = np.array([2e-10, 5e-9])
