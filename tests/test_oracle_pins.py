@@ -168,6 +168,21 @@ def test_exact_recovery_of_debye_sum():
     np.testing.assert_allclose(w, np.concatenate([[2.5], de]), rtol=1e-9)
 
 
+def test_fitter_recovers_an_exact_debye_sum():
+    # with (almost) no damping the search + polish finds the generating poles of
+    # an exact two-pole Debye sum: tau to 1e-6 decades, the weights to 1e-6
+    om = grid(1e6, 1e11, 150)
+    tau = np.array([2e-11, 3e-9])
+    d_eps = np.array([15.0, 40.0])
+    re, im = _debye_sum_target(om, 3.0, d_eps, tau)
+    r = fit.fit_spectrum(om, re, im, 2, -13.0, -6.0, 32, 40, topk=4, polish_iters=60,
+                         lam_search=1e-12, lam_final=0.0)
+    assert np.max(np.abs(np.log10(r["tau"]) - np.log10(tau))) <= 1e-6
+    assert np.all(r["d_eps"] >= 0)
+    np.testing.assert_allclose(r["d_eps"], d_eps, rtol=1e-6)
+    assert abs(r["eps_inf"] - 3.0) <= 1e-6 * 3.0
+
+
 def test_flip_keeps_eps_inf_sign():
     # eps_inf < 0 is not a 'negative weight' of a Debye pole: no penalty
     om = grid(1e6, 1e10, 200)
