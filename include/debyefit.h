@@ -211,22 +211,28 @@ int debye_fit_auto(debye_handle h, const debye_spectra* spectra, const debye_sea
  * or a latency-critical loop where cudaMalloc/cudaFree (which may synchronise the
  * device) are not acceptable.
  *
- * Computes exactly what debye_eval_population computes (costs, and weights if
- * `weights` is not NULL) for the options in `opt` (NULL = defaults), without a
- * handle. It calls no cudaMalloc, cudaFree or other allocating routine: all
- * temporary data lives in one fixed scratch array of DEBYE_NOALLOC_SCRATCH_BYTES
- * (32 MiB) inside the library's device image, held by every GPU that loads the
- * library until the process exits. A batch whose temporaries do not fit (about
- * 2.3 KB per candidate at n_max = 12, plus 32 B per frequency sample), or that
- * needs more than 4096 work units, is rejected with DEBYE_EINVAL and a message.
- * spectra->offsets_host and spectra->n_poles_host are required.
+ * Computes what debye_eval_population computes (costs, and weights if `weights`
+ * is not NULL) for the options in `opt` (NULL = defaults), without a handle. The
+ * results agree with debye_eval_population's to rounding, within the parity
+ * tolerances of the cost (relative 1e-10 with DEBYE_PREC_FP64, 1e-5 with
+ * DEBYE_PREC_MIXED), not bit for bit: the two entry points may split a candidate's
+ * samples over different numbers of lanes, and the mixed-precision solve here is
+ * always the one-thread-per-candidate kernel. It calls no cudaMalloc, cudaFree
+ * or other allocating routine: all temporary data lives in one fixed scratch
+ * array of DEBYE_NOALLOC_SCRATCH_BYTES (32 MiB) inside the library's device
+ * image, held by every GPU that loads the library until the process exits. A
+ * batch whose temporaries do not fit (about 2.3 KB per candidate at n_max = 12,
+ * plus 64 B per frequency sample), or that needs more than 4096 work units, is
+ * rejected with DEBYE_EINVAL and a message. spectra->offsets_host and
+ * spectra->n_poles_host are required.
  *
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture. Every call on a device shares the one array and leaves
- * its contents behind (the call initialises everything it reads); calls whose
- * work overlaps on the GPU race on the array, so order them (one stream, or
- * events). The call returns after the work on `stream` has finished, with
+ * The first call on a device, and the first call after that device's context was
+ * reset (cudaDeviceReset), looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that call before any
+ * stream capture. Every call on a device shares the one array and leaves its
+ * contents behind (the call initialises everything it reads); calls whose work
+ * overlaps on the GPU race on the array, so order them (one stream, or events).
+ * The call returns after the work on `stream` has finished, with
  * DEBYE_ENOTFINITE / DEBYE_EBOUNDS for input problems found on the device.
  * `err` (may be NULL) receives a message of at most err_len bytes. */
 #define DEBYE_NOALLOC_SCRATCH_BYTES (32u << 20)

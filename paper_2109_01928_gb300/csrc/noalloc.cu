@@ -14,6 +14,8 @@
 // Every call on a device uses the same array and leaves its contents behind;
 // calls whose work overlaps on the GPU (different streams or host threads,
 // without ordering between them) race on it and give wrong results.
+#include <cuda.h>
+
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -26,13 +28,56 @@ namespace {
 constexpr size_t SCRATCH_BYTES = DEBYE_NOALLOC_SCRATCH_BYTES;
 constexpr int MAX_UNITS = 4096;
 constexpr int MAX_DEVICES = 64;
+// every sample takes 64 B of the scratch (two float4 records in kf32 and in kff)
+constexpr int64_t MAX_SAMPLES = (int64_t)(SCRATCH_BYTES / (4 * sizeof(float4)));
 
 static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
 
 // Device address of g_scratch per device. In host code `g_scratch` names a host
-// stand-in, not device memory, so the address must come from the runtime.
+// stand-in, not device memory, so the address must come from the runtime
+// (cudaGetSymbolAddress, with the device current). The address is looked up
+// once per device and context: a cudaDeviceReset destroys the device's context
+// and the next context may load the library's device image elsewhere, so a
+// cached address is reused only while the context that it was looked up in
+// (identified by the driver's unique context id) is still current. Where the
+// context id cannot be queried, every call looks the address up.
+struct ScratchSlot {
+  void* ptr = nullptr;
+  unsigned long long ctx_id = 0;
+  bool valid = false;
+};
 std::mutex g_mu;
-void* g_scratch_dev[MAX_DEVICES] = {nullptr};
+ScratchSlot g_slot[MAX_DEVICES];
+
+typedef CUresult(CUDAAPI* ctx_get_current_fn)(CUcontext*);
+typedef CUresult(CUDAAPI* ctx_get_id_fn)(CUcontext, unsigned long long*);
+ctx_get_current_fn g_ctx_get_current = nullptr;
+ctx_get_id_fn g_ctx_get_id = nullptr;
+bool g_entry_points_looked_up = false;
+
+// Driver entry points for the context id (no link-time dependency on libcuda).
+void lookup_entry_points() {
+  if (g_entry_points_looked_up) return;
+  g_entry_points_looked_up = true;
+  void* f = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    g_ctx_get_current = (ctx_get_current_fn)f;
+  f = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    g_ctx_get_id = (ctx_get_id_fn)f;
+  cudaGetLastError();
+}
+
+// Unique id of the current context; false if there is none or it cannot be queried.
+bool current_context_id(unsigned long long* id) {
+  if (!g_ctx_get_current || !g_ctx_get_id) return false;
+  CUcontext c = nullptr;
+  if (g_ctx_get_current(&c) != CUDA_SUCCESS || !c) return false;
+  return g_ctx_get_id(c, id) == CUDA_SUCCESS;
+}
 
 int scratch_address(void** out, char* err, int err_len) {
   int dev = 0;
@@ -43,18 +88,25 @@ int scratch_address(void** out, char* err, int err_len) {
     return DEBYE_ECUDA;
   }
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_dev[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      if (err && err_len > 0)
-        snprintf(err, err_len, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
-      return DEBYE_ECUDA;
-    }
-    g_scratch_dev[dev] = p;
+  lookup_entry_points();
+  unsigned long long id = 0;
+  ScratchSlot& slot = g_slot[dev];
+  if (slot.valid && current_context_id(&id) && id == slot.ctx_id) {
+    *out = slot.ptr;
+    return DEBYE_OK;
   }
-  *out = g_scratch_dev[dev];
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    if (err && err_len > 0)
+      snprintf(err, err_len, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
+    return DEBYE_ECUDA;
+  }
+  slot.ptr = p;
+  slot.valid = current_context_id(&id);   // the lookup made the device's context current
+  slot.ctx_id = id;
+  *out = p;
   return DEBYE_OK;
 }
 
@@ -65,7 +117,7 @@ struct Carve {
   bool ok = true;
   void* take(size_t bytes) {
     const size_t off = (used + 255) & ~(size_t)255;
-    if (off + bytes > SCRATCH_BYTES) {
+    if (!ok || off > SCRATCH_BYTES || bytes > SCRATCH_BYTES - off) {
       ok = false;
       return nullptr;
     }
@@ -108,6 +160,10 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
   const int64_t S = sp->S;
   const int64_t Q = S * (int64_t)P;
   if (Q > ((int64_t)1 << 31) - 1) return fail_msg(DEBYE_EINVAL, err, err_len, "S*P exceeds 2^31-1");
+  // Bounds that keep every byte count below the scratch size (no size_t overflow in
+  // the carving below): 8 B per candidate and 16 B per spectrum at the very least.
+  if (Q > (int64_t)(SCRATCH_BYTES / sizeof(double)) || S > (int64_t)(SCRATCH_BYTES / (2 * sizeof(double))))
+    return fail_msg(DEBYE_EINVAL, err, err_len, "batch needs more than the allocation-free scratch");
   if (opt.cands_per_block != 0 &&
       (opt.cands_per_block < 32 || opt.cands_per_block > MAX_BLOCK || opt.cands_per_block % 32))
     return fail_msg(DEBYE_EINVAL, err, err_len, "cands_per_block");
@@ -131,6 +187,9 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
       const int N = sp->n_poles_host[s];
       if (N < 1 || N > n_max || offs[s + 1] < offs[s])
         return fail_msg(DEBYE_EINVAL, err, err_len, "n_poles outside 1..n_max or offsets decreasing");
+      if (offs[s + 1] > MAX_SAMPLES)
+        return fail_msg(DEBYE_EINVAL, err, err_len, "batch has more frequency samples than the "
+                        "allocation-free scratch holds (64 B per sample)");
       if (bucket_of(N) != b) continue;
       for (int64_t q = s * P; q < (s + 1) * P; q += cb) {
         if (n_units == MAX_UNITS)

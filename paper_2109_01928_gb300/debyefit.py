@@ -121,6 +121,14 @@ def header_functions() -> list[str]:
     return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\*?(debye_\w+)\s*\(", txt, re.M)))
 
 
+def _check_n_max(theta, n_max):
+    """The kernels stride theta [S, P, n_max] rows by n_max: it must be theta's last extent."""
+    nm = theta.shape[2]
+    if n_max is not None and n_max != nm:
+        raise ValueError(f"n_max = {n_max} differs from theta.shape[2] = {nm}")
+    return nm
+
+
 def _ptr(t) -> int | None:
     return None if t is None else t.data_ptr()
 
@@ -236,7 +244,7 @@ def debye_eval_population(h: Handle, sp: Spectra, theta, weights: bool = False, 
     """Cost [S, P] (and weights [S, P, n_max+1]) of the population theta [S, P, n_max]."""
     import torch
     S, P, nm = theta.shape
-    n_max = nm if n_max is None else n_max
+    n_max = _check_n_max(theta, n_max)
     assert theta.dtype == torch.float64 and theta.is_contiguous()
     if cost is None:
         cost = torch.empty((S, P), dtype=torch.float64, device=theta.device)
@@ -328,7 +336,7 @@ def debye_eval_population_noalloc(sp: Spectra, theta, precision: str = "mixed", 
     library (fixed scratch inside the library); the caller provides the outputs."""
     import torch
     S, P, nm = theta.shape
-    n_max = nm if n_max is None else n_max
+    n_max = _check_n_max(theta, n_max)
     o = options if options is not None else default_options()
     o.precision = {"mixed": PREC_MIXED, "fp64": PREC_FP64}[precision]
     if cost is None:

@@ -9,6 +9,7 @@ import math
 import numpy as np
 import pytest
 
+import fitcheck
 import workloads as W
 from oracle import dls, fit, models, varpro
 
@@ -17,6 +18,12 @@ pytestmark = pytest.mark.gpu
 
 COST_TOL = {"fp64": 1e-10, "mixed": 1e-5}
 GRAD_TOL = {"fp64": 1e-8, "mixed": 1e-4}
+# Weights, relative to the largest weight of the candidate. The cost is stationary
+# in the weights, the weights are not: FP64 carries the Cholesky solve's rounding
+# (~1e-13 of the scale at the damped condition number kappa <= (n + lam)/lam);
+# mixed precision the FP32 factor's error after one refinement step,
+# (kappa 2^-24)^2 ~ 1.6e-6 at n = 21, lam = 1e-3.
+WEIGHT_TOL = {"fp64": 1e-10, "mixed": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -93,8 +100,7 @@ def test_eval_population_ragged(D, prec, lanes):
     assert rel.max() <= COST_TOL[prec], f"max relative cost error {rel.max():.3g}"
     # weights: the cost is stationary in x, the weights are checked against their own scale
     scale = np.abs(wref).max(axis=2, keepdims=True)
-    wtol = {"fp64": 1e-7, "mixed": 2e-3}[prec]
-    assert (np.abs(w - wref) / scale).max() <= wtol
+    assert (np.abs(w - wref) / scale).max() <= WEIGHT_TOL[prec]
     # padding beyond N_s + 1 is zero
     for s in range(b.S):
         assert np.all(w[s, :, b.n_poles[s] + 1:] == 0)
@@ -152,31 +158,38 @@ def strata_report(rel, idx, names):
     return "\n".join(lines)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_cost_error_by_condition_number(D, prec):
-    # cost errors stratified by the conditioning of the undamped basis (near-
-    # repeated relaxation times push cond(A) past 1e9; the damping keeps the
-    # solved system well conditioned): the tolerance up to cond 1e9, and above
-    # it the allowance of exactly repeated poles (test_duplicate_tau_and_tiny_k)
+@pytest.mark.parametrize("prec,lanes", PREC_LANES)
+def test_cost_error_by_condition_number(D, prec, lanes):
+    # cost and weight errors stratified by the conditioning of the undamped basis:
+    # near-repeated relaxation times (|theta_1 - theta_0| from 1e-12 to 1e-2
+    # decades, a third of each population, and an exactly repeated triple in
+    # another eighth) push cond(A) up to ~1e16. The Marquardt damping bounds the
+    # scaled damped matrix's condition number by (n + lam)/lam whatever cond(A)
+    # is, so every stratum meets the same tolerance.
     b = W.mixed_batch(S=12, seed=17, P=48, K_range=(40, 600), N_range=(1, 20))
     re, im = models.synthesize(b)
     th = W.population(b, 48, seed=5)
     rs = np.random.default_rng(2)
     for s in range(b.S):
         if b.n_poles[s] >= 2:
-            close = rs.choice(48, 16, replace=False)
-            th[s, close, 1] = th[s, close, 0] + 10.0 ** rs.uniform(-8, -2, 16)
-    ref, _ = oracle_costs(b, re, im, th)
-    with D.Handle(prec) as h:
-        cost = D.debye_eval_population(h, spectra_for(D, b, re, im), torch.as_tensor(th, device="cuda"))
+            close = rs.choice(48, 22, replace=False)
+            th[s, close[:16], 1] = th[s, close[:16], 0] + 10.0 ** rs.uniform(-12, -2, 16)
+            if b.n_poles[s] >= 3:
+                th[s, close[16:], 1] = th[s, close[16:], 0]
+                th[s, close[16:], 2] = th[s, close[16:], 0]
+    ref, wref = oracle_costs(b, re, im, th)
+    with D.Handle(prec, solve_lanes=lanes) as h:
+        cost, w = D.debye_eval_population(h, spectra_for(D, b, re, im), torch.as_tensor(th, device="cuda"),
+                                          weights=True)
         D.debye_sync(h)
     rel = np.abs(cost.cpu().numpy() - ref) / ref
+    wrel = (np.abs(w.cpu().numpy() - wref) / np.abs(wref).max(axis=2, keepdims=True)).max(axis=2)
     cond, idx, names = cond_strata(b, th)
     report = strata_report(rel.ravel(), idx.ravel(), names)
     print("\n" + prec + "\n" + report)
     assert (idx == len(names) - 1).sum() >= 20 and (idx == 0).sum() >= 20, report
-    assert rel[idx < len(names) - 1].max() <= COST_TOL[prec], report
-    assert rel.max() <= 10 * COST_TOL[prec], report
+    assert rel.max() <= COST_TOL[prec], report
+    assert wrel.max() <= WEIGHT_TOL[prec], (wrel.max(), report)
 
 
 def test_autotune_then_eval(D, tmp_path):
@@ -204,7 +217,7 @@ def test_duplicate_tau_and_tiny_k(D):
     for prec, lanes in PREC_LANES:
         with D.Handle(prec, solve_lanes=lanes) as h:
             cost = D.debye_eval_population(h, spectra_for(D, b, re, im), torch.as_tensor(th, device="cuda"))
-        assert (np.abs(cost.cpu().numpy() - ref) / ref).max() <= 10 * COST_TOL[prec]
+        assert (np.abs(cost.cpu().numpy() - ref) / ref).max() <= COST_TOL[prec], (prec, lanes)
 
 
 def test_input_errors(D):
@@ -224,7 +237,9 @@ def test_input_errors(D):
         with pytest.raises(D.DebyeError) as e:
             D.debye_eval_population(h, spectra_for(D, b2, re, im), th)
         assert e.value.code == D.DEBYE_EINVAL
-        with pytest.raises(D.DebyeError):
+        with pytest.raises(D.DebyeError):   # rows of one pole for spectra with two or three
+            D.debye_eval_population(h, spectra_for(D, b, re, im), th[:, :, :1].contiguous())
+        with pytest.raises(ValueError):     # n_max must be theta's row length
             D.debye_eval_population(h, spectra_for(D, b, re, im), th, n_max=1)
         empty = D.make_spectra(np.zeros(1, np.int64), np.zeros(0), np.zeros(0), np.zeros(0),
                                np.zeros(0, np.int32), np.zeros(0), np.zeros(0), device="cuda")
@@ -330,37 +345,39 @@ def test_fit_fp64_swarm_trace_matches_oracle(D):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_fit_with_polish_matches_oracle(D, prec):
-    # FP64: the swarm trajectory is the oracle's, so every spectrum must reach the
-    # oracle's minimum (or a cost at least as low). Mixed: costs differ from the
-    # oracle's by ~1e-7, so a near-tie between particles can send the swarm down
-    # another path; a spectrum counts as matched if it reaches the oracle's minimum
-    # or a cost at least as low, at least 2/3 must match, and the others must be
-    # near-equal local minima (cost within 5 %) of these multimodal fits.
+    # Every spectrum: the fitted spectrum within 1e-4 relative RMS of the oracle's,
+    # or a final cost at most the oracle's x (1 + 1e-6). FP64 follows the oracle's
+    # path and must meet this strictly. In mixed precision the one exception is a
+    # spectrum on which the oracle's own polish is chaotic (its FP64 result moves
+    # past the criterion when its start points move by 1e-9 decades): there the
+    # GPU cost must lie within the oracle's own perturbed spread (fitcheck).
     b = W.mixed_batch(S=6, seed=31, P=64, K_range=(50, 200), N_range=(2, 5))
     re, im = models.synthesize(b)
     with D.Handle(prec) as h:
         out = D.debye_fit_batch(h, spectra_for(D, b, re, im), P=64, iters=60, seed=0, polish_topk=8,
                                 polish_iters=40)
         D.debye_sync(h)
-    matched = 0
+    how = []
     for s in range(b.S):
         a, c = b.offsets[s], b.offsets[s + 1]
-        r = fit_oracle(b, re, im, s, 64, 60, 8, 40)
         N = int(b.n_poles[s])
         e_gpu = fitted(b.omega[a:c], out["eps_inf"][s].item(), out["d_eps"][s, :N].cpu().numpy(),
                        out["tau"][s, :N].cpu().numpy())
-        e_ref = fit.fitted_eps(b.omega[a:c], r)
-        rr = dls.rel_rms(e_gpu, e_ref)
         gcost = out["final_cost"][s].item()
-        ok = rr <= 1e-4 or gcost <= r["cost_final"] * (1 + 1e-6)
-        matched += ok
         if prec == "fp64":
-            assert ok, (s, rr, gcost, r["cost_final"])
+            r = fit_oracle(b, re, im, s, 64, 60, 8, 40)
+            assert fitcheck.agree(e_gpu, gcost, fit.fitted_eps(b.omega[a:c], r), r["cost_final"]), \
+                (s, dls.rel_rms(e_gpu, fit.fitted_eps(b.omega[a:c], r)), gcost, r["cost_final"])
+            how.append("strict")
         else:
-            assert ok or gcost <= r["cost_final"] * 1.05, (s, rr, gcost, r["cost_final"])
+            ok, kind = fitcheck.check_spectrum(b.omega[a:c], re[a:c], im[a:c], N, float(b.lo[s]), float(b.hi[s]),
+                                               64, 60, 0, s, 8, 40, e_gpu, gcost)
+            assert ok, (s, kind, gcost)
+            how.append(kind)
         assert np.all(out["d_eps"][s, :N].cpu().numpy() >= 0)
         assert np.all(np.diff(out["tau"][s, :N].cpu().numpy()) >= 0)
-    assert matched >= (b.S if prec == "fp64" else (2 * b.S) // 3)
+    print(prec, how)
+    assert how.count("strict") >= b.S // 2, how
 
 
 # ---------------------------------------------------------------- differential evolution

@@ -4,6 +4,7 @@ polish-only fit) and the 16384-spectrum K=4096 tabulated workload (costs)."""
 import numpy as np
 import pytest
 
+import fitcheck
 import workloads as W
 from oracle import dls, fit, models, varpro
 
@@ -57,25 +58,27 @@ def test_hn256_cost_grad_sampled(D, hn256, prec):
 
 def test_hn256_polish_fit_sampled(D, hn256):
     # the differentiation workload as the benchmark runs it: 4096 random candidates per
-    # spectrum, the best 32 polished by 50 L-BFGS iterations (captured as a CUDA graph)
+    # spectrum, the best 32 polished by 50 L-BFGS iterations (captured as a CUDA graph).
+    # The starting points are the oracle's (same seeded population, same ranking); every
+    # checked spectrum meets the end-to-end criterion of fitcheck (strict, or within the
+    # oracle's own spread where its polish is chaotic).
     b, re, im = hn256
     with D.Handle("mixed") as h:
         out = D.debye_fit_batch(h, _spectra(D, b, re, im), P=4096, iters=0, seed=0, polish_topk=32,
                                 polish_iters=50)
         D.debye_sync(h)
-    for s in (3, 77):
+    how = []
+    for s in (3, 77, 150):
         a, c = b.offsets[s], b.offsets[s + 1]
-        r = fit.fit_spectrum(b.omega[a:c], re[a:c], im[a:c], 8, -13.0, -5.0, 4096, 0, seed=0, spectrum=s,
-                             topk=32, polish_iters=50)
         e_gpu = models.multi_debye(b.omega[a:c], out["eps_inf"][s].item(), out["d_eps"][s].cpu().numpy(),
                                    out["tau"][s].cpu().numpy())
-        rr = dls.rel_rms(e_gpu, fit.fitted_eps(b.omega[a:c], r))
         g = out["final_cost"][s].item()
-        # the starting points are the oracle's (same seeded population, same ranking); a
-        # polish step decided by a ~1e-7 cost difference may still end in a near-equal minimum
-        assert rr <= 1e-4 or g <= r["cost_final"] * (1 + 1e-6) or g <= r["cost_final"] * 1.01, \
-            (s, rr, g, r["cost_final"])
+        ok, kind = fitcheck.check_spectrum(b.omega[a:c], re[a:c], im[a:c], 8, -13.0, -5.0, 4096, 0, 0, s, 32, 50,
+                                           e_gpu, g)
+        assert ok, (s, kind, g)
+        how.append(kind)
         assert np.all(out["d_eps"][s].cpu().numpy() >= 0)
+    print(how)
 
 
 def test_tabulated_full_size_sampled(D):
