@@ -4,9 +4,13 @@ One step = one debye_fit_batch over the whole workload: seeded particle swarm
 (every generation evaluates the damped least-squares cost of every particle),
 L-BFGS polish of the best personal bests, final FP64 re-solve. The metric is
 candidate evaluations x frequency samples per second (cand*K/s), counted on the
-device over swarm and polish evaluations.
+device over swarm and polish evaluations. The headline workload is the
+1024-spectrum mixed-model batch in mixed precision, next to the plain FP64
+evaluator on the same fit; the single-spectrum, differentiation and tabulated
+workloads are measured under "configs".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--configs all|none|name,...] [--no-fp64] [--no-cpu-baseline]
 
 With N > 1 (torchrun) every rank fits its own batch of the same shape (seed =
 rank): the spectra are independent, so there is no data-path collective, and
@@ -18,7 +22,6 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import multiprocessing as mp
 import os
 import statistics
@@ -38,11 +41,24 @@ WORKLOAD = "mixed_1024"
 # per workload: particles, swarm generations after the first, polished candidates, L-BFGS iterations
 SETTINGS = {"mixed_1024": (256, 200, 8, 50), "single_hn_k50": (64, 100, 8, 50),
             "hn_256_k2000": (4096, 0, 32, 50), "tabulated_16384_k4096": (512, 100, 8, 50)}
-TOPK, POLISH_ITERS = 8, 50
+EXTRA_CONFIGS = ("single_hn_k50", "hn_256_k2000", "tabulated_16384_k4096")
 METRIC = "candidate cost evals x K per sec (batched mixed-precision fit)"
 UNIT = "cand*K/s"
-FP32_LANES_PER_SM, SMS, SM_MAX_MHZ = 128, 152, 2070.0
+# ALU peaks from unit counts and the maximum SM clock: FP32, 152 SMs x 128 lanes x 2 FLOP
+# per FMA; FP64, the nominal GB300 rate (1.25 TFLOP/s dense, 1/64 of FP32)
+SMS, SM_MAX_MHZ = 152, 2070.0
+PEAK_FP32 = SMS * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+PEAK_FP64 = 1.25
 KERNEL_SOURCES = ["paper_2109_01928_gb300/csrc/eval.cuh", "paper_2109_01928_gb300/csrc/common.cuh"]
+CTL_REL = 1e-9          # relative perturbation of the damping in the FP64 control fit
+TAB_SAMPLE = 64         # spectra of the tabulated workload's oracle sample
+
+
+def f_alg(N):
+    """Algorithmic FP32 FLOPs per cand*K of one cost evaluation by the direct method:
+    basis 4N + unique Gram / right-hand-side products 2(N+2)^2 (FMA = 2)."""
+    N = np.asarray(N, dtype=np.float64)
+    return 4 * N + 2 * (N + 2) ** 2
 
 
 # ------------------------------------------------------------------ replicas (one process per GPU)
@@ -98,7 +114,9 @@ def _oracle_chunk(job):
     import workloads as W_
     from oracle import dls, models, pso
     name, P, spectra, gens = job
-    full = W_.workload(name)
+    # the tabulated workload's generator draws every spectrum's noise at once (1 GB for all
+    # 16384): its sample comes from a 64-spectrum batch of the same generator and shape
+    full = W_.tabulated_batch(S=TAB_SAMPLE) if name == "tabulated_16384_k4096" else W_.workload(name)
     work, secs = 0, 0.0
     for s in spectra:
         b = full.subset([s])
@@ -112,13 +130,13 @@ def _oracle_chunk(job):
     return work, secs
 
 
-def oracle_rate(n_spectra: int, gens: int, procs: int, seed: int = 0):
-    """cand*K/s of the oracle on a seeded sample of spectra, split over `procs` spawned
-    processes: total work / the slowest process's compute time."""
+def oracle_rate(name: str, n_spectra: int, gens: int, procs: int, seed: int = 0):
+    """cand*K/s of the oracle on a seeded sample of spectra of workload `name`, split over
+    `procs` spawned processes: total work / the slowest process's compute time."""
     rng = np.random.default_rng(seed)
-    S = W.workload(WORKLOAD).S
-    picks = [int(s) for s in rng.choice(S, n_spectra, replace=False)]
-    chunks = [(WORKLOAD, SETTINGS[WORKLOAD][0], picks[i::procs], gens) for i in range(procs) if picks[i::procs]]
+    S = {"single_hn_k50": 1, "mixed_1024": 1024, "hn_256_k2000": 256, "tabulated_16384_k4096": TAB_SAMPLE}[name]
+    picks = [int(s) for s in rng.choice(S, min(n_spectra, S), replace=False)]
+    chunks = [(name, SETTINGS[name][0], picks[i::procs], gens) for i in range(procs) if picks[i::procs]]
     # one BLAS thread per process, so `procs` is the number of cores used
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[v] = "1"
@@ -126,27 +144,34 @@ def oracle_rate(n_spectra: int, gens: int, procs: int, seed: int = 0):
         res = pool.map(_oracle_chunk, chunks)
     work = sum(r[0] for r in res)
     wall = max(r[1] for r in res)
-    return work / wall, work, wall
+    return work / wall, work, wall, len(chunks)
 
 
-def cpu_baseline(quick: bool):
-    cores = os.cpu_count() or 1
-    b = W.workload(WORKLOAD)
-    heavy = float(np.mean(b.K)) * SETTINGS[WORKLOAD][0] > 3e5   # per-spectrum oracle work
-    n1, nall = (4, cores) if (quick or heavy) else (16, max(4 * cores, 32))
-    r1, w1, t1 = oracle_rate(n1, 2, 1)
-    ra, wa, ta = oracle_rate(nall, 2, cores)
+def cpu_model() -> str:
     try:
-        model = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
-        model = next((l.split(":", 1)[1].strip() for l in model.splitlines() if "Model name" in l), "")
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        return next((l.split(":", 1)[1].strip() for l in txt.splitlines() if "Model name" in l), "")
     except Exception:
-        model = ""
-    return {"value": ra, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{nall} seeded spectra of {WORKLOAD}, full population P={SETTINGS[WORKLOAD][0]}, 2 swarm generations "
-                      f"(init + 1 update), numpy FP64 QR per candidate, {cores} spawned processes; "
+        return ""
+
+
+def cpu_baseline(name: str, quick: bool):
+    """The oracle on the host cores: one process, then one process per core."""
+    cores = os.cpu_count() or 1
+    n1, nall = (4, cores) if quick else (16, max(4 * cores, 32))
+    if name == "tabulated_16384_k4096":      # ~9 s of oracle time per spectrum
+        n1, nall = 1, min(2 * cores, TAB_SAMPLE)
+    r1, _, t1, _ = oracle_rate(name, n1, 2, 1)
+    ra, _, ta, used = oracle_rate(name, nall, 2, cores)
+    src = (f"of a {TAB_SAMPLE}-spectrum batch drawn like {name}" if name == "tabulated_16384_k4096"
+           else f"of {name}")
+    return {"value": ra, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{nall} seeded spectra "
+                      f"{src}, full population P={SETTINGS[name][0]}, 2 swarm "
+                      f"generations (init + 1 update), numpy FP64 QR per candidate, {used} spawned processes; "
                       f"rate = total work / slowest process's compute time",
             "single_thread": {"value": r1, "sample": f"{n1} spectra, 1 process", "seconds": t1},
-            "seconds": ta, "cpu_model": model}
+            "seconds": ta, "cpu_model": cpu_model()}
 
 
 # ------------------------------------------------------------------ clocks
@@ -196,7 +221,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ------------------------------------------------------------------ GPU arm
+# ------------------------------------------------------------------ GPU helpers
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
@@ -205,13 +230,13 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def load_traffic(kind: str):
-    """DRAM bytes per launch of kernel `kind` from the committed ncu summary, if the kernel
+def load_traffic(key: str):
+    """DRAM bytes per pass recorded under `key` in the committed ncu summary, if the kernel
     source is unchanged since it was captured."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
-        e = d.get(kind)
+        e = d.get(key)
         if e and e.get("source_hash") == kernel_source_hash():
             return e["dram_bytes_per_launch"]
     except Exception:
@@ -219,8 +244,278 @@ def load_traffic(kind: str):
     return None
 
 
+class Bench:
+    """A workload on the device (targets synthesised by the library) and its fit calls."""
+
+    def __init__(self, D, torch, dev, name: str, seed: int = 0, b=None):
+        self.D, self.torch, self.dev, self.name = D, torch, dev, name
+        self.P, self.iters, self.topk, self.polish_iters = SETTINGS[name]
+        self.b = b if b is not None else W.workload(name, seed=seed)
+        self.b.P = self.P
+        self.seed = seed
+        b = self.b
+        tt = self.tt
+        self.offsets_d, self.omega_d = tt(b.offsets, torch.int64), tt(b.omega)
+        with D.Handle("fp64") as hs:
+            noise = (tt(b.noise_re), tt(b.noise_im)) if b.noise_re is not None else (None, None)
+            self.eps_re_d, self.eps_im_d = D.debye_synth_targets(
+                hs, self.offsets_d, self.omega_d, tt(b.model, torch.int32), tt(b.params),
+                tt(b.pole_offsets, torch.int64), tt(b.pole_tau), tt(b.pole_deps), *noise)
+            D.debye_sync(hs)
+        self.sp = D.Spectra(self.offsets_d, self.omega_d, self.eps_re_d, self.eps_im_d,
+                            tt(b.n_poles, torch.int32), tt(b.lo), tt(b.hi),
+                            np.ascontiguousarray(b.offsets, np.int64), np.ascontiguousarray(b.n_poles, np.int32))
+        # F(N)-weighted and 54N-weighted cand*K of one full-population evaluation
+        wK = b.K.astype(np.float64) * self.P
+        self.candk_pass = float(wK.sum())
+        self.alg_flops_pass = float(np.sum(wK * f_alg(b.n_poles)))
+
+    def tt(self, a, dt=None):
+        dt = dt or self.torch.float64
+        return self.torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=self.dev)
+
+    def fit(self, h, out=None, sp=None, iters=None, topk=None):
+        return self.D.debye_fit_batch(h, sp or self.sp, P=self.P, iters=self.iters if iters is None else iters,
+                                      seed=self.seed, polish_topk=self.topk if topk is None else topk,
+                                      polish_iters=self.polish_iters, n_max=self.b.n_max, out=out)
+
+    def population(self, seed):
+        return self.torch.as_tensor(W.population(self.b, self.P, seed=seed), device=self.dev)
+
+
+def timed_fits(bn: Bench, h, steps, warmup, flush, barrier=lambda: None, host_io=False, warm_iters=None):
+    """Per-step CUDA-event times (ms) and cand*K per step of whole fits; L2 flushed between
+    steps. warm_iters: generations of each warm-up fit (default: the workload's)."""
+    torch, D = bn.torch, bn.D
+    out = None
+    for _ in range(warmup):
+        out = bn.fit(h, out, iters=warm_iters)
+    torch.cuda.synchronize()
+    times, evals = [], []
+    pinned = None
+    if host_io:
+        b = bn.b
+        pinned = {k: torch.as_tensor(v).pin_memory() for k, v in (
+            ("offsets", np.ascontiguousarray(b.offsets, np.int64)), ("omega", b.omega),
+            ("eps_re", bn.eps_re_d.cpu().numpy()), ("eps_im", bn.eps_im_d.cpu().numpy()),
+            ("n_poles", np.ascontiguousarray(b.n_poles, np.int32)), ("lo", b.lo), ("hi", b.hi))}
+        dev_in = {k: torch.empty_like(v, device=bn.dev) for k, v in pinned.items()}
+        res_host = {k: torch.empty(s, dtype=torch.float64).pin_memory()
+                    for k, s in (("eps_inf", (b.S,)), ("d_eps", (b.S, b.n_max)), ("tau", (b.S, b.n_max)),
+                                 ("final_cost", (b.S,)))}
+    barrier()
+    torch.cuda.synchronize()
+    D.debye_launch_count(h, reset=True)
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if host_io:
+            for k in pinned:
+                dev_in[k].copy_(pinned[k], non_blocking=True)
+            spx = D.Spectra(dev_in["offsets"], dev_in["omega"], dev_in["eps_re"], dev_in["eps_im"],
+                            dev_in["n_poles"], dev_in["lo"], dev_in["hi"], bn.sp.offsets_host, bn.sp.n_poles_host)
+            out = bn.fit(h, out, spx)
+            for k in res_host:
+                res_host[k].copy_(out[k], non_blocking=True)
+        else:
+            out = bn.fit(h, out)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        evals.append(out["evals"].item())
+    barrier()
+    torch.cuda.synchronize()
+    launches = D.debye_launch_count(h)
+    h2d = sum(v.numel() * v.element_size() for v in pinned.values()) if host_io else 0
+    d2h = sum(v.numel() * v.element_size() for v in res_host.values()) if host_io else 0
+    return {"times": times, "evals": evals, "out": out, "h2d": h2d, "d2h": d2h, "launches": launches}
+
+
+def profile(D, h, run):
+    """Per-kind pass counts, milliseconds and issued FLOPs of `run()` with kernel timing on."""
+    D.debye_profile_enable(h, True)
+    run()
+    import torch
+    torch.cuda.synchronize()
+    prof = D.debye_profile_read(h)
+    D.debye_profile_enable(h, False)
+    return prof
+
+
+def roofline_mixed(bn: Bench, prof, traffic_key):
+    """Roofline of the column-sum pass (the dominant kernel of every mixed evaluation) over the
+    full-population passes of the profiled run: achieved = algorithmic FLOPs by the direct
+    method's count F(N) = 4N + 2(N+2)^2 per cand*K (every unmasked candidate) / event time;
+    frac_issued counts the pass's own float-float operations (54N per cand*K)."""
+    n, ms, issued = prof["sums"]
+    if n == 0 or ms <= 0:
+        return None
+    alg = n * bn.alg_flops_pass
+    sec = ms * 1e-3
+    ach = alg / sec / 1e12
+    ach_issued = issued / sec / 1e12
+    return {"bound": "alu", "kernel": "column-sum pass (k_pass<PH_SUMS, N>, one kernel per pole count)",
+            "achieved": ach, "peak": PEAK_FP32, "unit": "TFLOP/s", "frac": ach / PEAK_FP32,
+            "traffic": load_traffic(traffic_key), "passes": n, "ms_per_pass": ms / n,
+            "cand_k_per_s": n * bn.candk_pass / sec,
+            "flop_count": "F(N) = 4N + 2(N+2)^2 per cand*K (basis + unique Gram/RHS products of the "
+                          "direct method), K-weighted over the batch",
+            "achieved_issued": ach_issued, "frac_issued": ach_issued / PEAK_FP32,
+            "issued_note": "the pass's own FP32 operations (54N per cand*K): float-float sums with "
+                           "TwoSum/Dot2/Newton steps, i.e. the direct count plus precision overhead "
+                           "minus the Gram products the partial-fraction identity removes",
+            "peak_note": "FP32 ALU peak of measured-free unit counts: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz"}
+
+
+def per_kind_ms(prof):
+    return {k: v[1] for k, v in prof.items() if v[0]}
+
+
+def fit_agreement(b, out_a, out_b):
+    """Per-spectrum agreement of two fits of batch b (a: the arm under test, b: the FP64 fit):
+    relative RMS between the fitted spectra, damped-cost ratio, fit error against the target."""
+    from oracle import models as om
+    re = b.extra.get("_re")
+    rr, ratio, fe_a, fe_b = [], [], [], []
+    for s in range(b.S):
+        a, c = b.offsets[s], b.offsets[s + 1]
+        N = int(b.n_poles[s])
+        ea = om.multi_debye(b.omega[a:c], out_a["eps_inf"][s], out_a["d_eps"][s, :N], out_a["tau"][s, :N])
+        eb = om.multi_debye(b.omega[a:c], out_b["eps_inf"][s], out_b["d_eps"][s, :N], out_b["tau"][s, :N])
+        rr.append(float(np.linalg.norm(ea - eb) / np.linalg.norm(eb)))
+        ratio.append(out_a["final_cost"][s] / out_b["final_cost"][s])
+        if re is not None:
+            tgt = re[0][a:c] - 1j * re[1][a:c]
+            fe_a.append(float(np.linalg.norm(ea - tgt) / np.linalg.norm(tgt)))
+            fe_b.append(float(np.linalg.norm(eb - tgt) / np.linalg.norm(tgt)))
+    rr, ratio = np.array(rr), np.array(ratio)
+    worse = ratio > 1 + 1e-6
+    fail = (rr > 1e-4) & worse
+    res = {"median_rel_rms": float(np.median(rr)), "frac_rel_rms_le_1e-4": float(np.mean(rr <= 1e-4)),
+           "frac_cost_le_fp64": float(np.mean(~worse)), "n_fail_both": int(fail.sum()),
+           "worst_cost_ratio": float(ratio.max()), "n_better_by_1e-6": int(np.sum(ratio < 1 - 1e-6))}
+    if fe_a:
+        fe_a, fe_b = np.array(fe_a), np.array(fe_b)
+        res["fit_error_vs_target"] = {"median": float(np.median(fe_a)), "median_fp64": float(np.median(fe_b)),
+                                      "mean": float(fe_a.mean()), "mean_fp64": float(fe_b.mean()),
+                                      "frac_lower_than_fp64": float(np.mean(fe_a < fe_b))}
+    return res
+
+
+def host_out(out):
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+# ------------------------------------------------------------------ extra configurations
+
+def config_single_hn(D, torch, dev, flush, steps):
+    """The paper-like single-target fit (HN, K = 50, N = 3, P = 64, 100 generations, FP64 plain
+    method; mixed precision beside it): latency of one whole fit."""
+    bn = Bench(D, torch, dev, "single_hn_k50")
+    res = {"workload": "single_hn_k50: 1 HN spectrum (eps_inf 3.4, d_eps 2.7, tau0 8e-10 s, alpha 0.91, "
+                       "beta 0.45), K=50 over 1e8-1e10 Hz, N=3, log10 tau in [-13,-6], P=64, 100 generations "
+                       "after the first, top-8 x 50 L-BFGS polish, seed 0"}
+    for prec in ("fp64", "mixed"):
+        with D.Handle(prec) as h:
+            r = timed_fits(bn, h, steps, 3, flush)
+        res[prec] = {"ms_per_fit": float(np.mean(r["times"])), "value": sum(r["evals"]) / (sum(r["times"]) * 1e-3),
+                     "unit": UNIT, "final_cost": float(r["out"]["final_cost"][0].item()), "steps": steps}
+    return res
+
+
+def config_hn256(D, torch, dev, flush, steps):
+    """The differentiation workload: cost + VarPro gradient of 256 x 4096 fed-in candidates
+    (K = 2000, N = 8) in both precisions, and the polish fit (top-32 x 50 L-BFGS, graph-captured)."""
+    bn = Bench(D, torch, dev, "hn_256_k2000")
+    b = bn.b
+    th = bn.population(0)
+    res = {"workload": "hn_256_k2000: 256 HN spectra, K=2000 over 1e6-1e10 Hz, N=8, 4096 fed-in candidates "
+                       "per spectrum; cost+gradient of the population; fit = best 32 polished by 50 L-BFGS "
+                       "iterations (CUDA graph)"}
+    for prec in ("fp64", "mixed"):
+        with D.Handle(prec) as h:
+            cost, grad = D.debye_cost_grad(h, bn.sp, th)
+            torch.cuda.synchronize()
+            t = []
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                D.debye_cost_grad(h, bn.sp, th, cost=cost, grad=grad)
+                e1.record()
+                torch.cuda.synchronize()
+                t.append(e0.elapsed_time(e1))
+            prof = profile(D, h, lambda: D.debye_cost_grad(h, bn.sp, th, cost=cost, grad=grad))
+            entry = {"cost_grad_ms": float(np.mean(t)),
+                     "cost_grad_value": bn.candk_pass / (np.mean(t) * 1e-3), "unit": UNIT,
+                     "per_kind_ms": per_kind_ms(prof)}
+            if prec == "mixed":
+                n, ms, issued = prof["sums"]
+                if n:
+                    entry["sums_grad_pass"] = {"ms": ms / n, "achieved_issued": issued / (ms * 1e-3) / 1e12,
+                                               "frac_issued": issued / (ms * 1e-3) / 1e12 / PEAK_FP32,
+                                               "note": "pass with the derivative sums, its own 103N FP32 "
+                                                       "operations per cand*K"}
+                r = timed_fits(bn, h, steps, 1, flush)
+                entry["fit_ms"] = float(np.mean(r["times"]))
+                entry["fit_value"] = sum(r["evals"]) / (sum(r["times"]) * 1e-3)
+            res[prec] = entry
+    return res
+
+
+def config_tabulated(D, torch, dev, flush):
+    """The tabulated workload at full size: 16384 spectra x 4096 samples, N = 20, P = 512,
+    100 generations, top-8 x 50 polish; one warm-up fit of one generation (allocation,
+    graph capture paths), one timed fit; the column-sum pass's roofline from a profiled
+    three-generation fit without the polish (its full-population passes are identical in every
+    generation)."""
+    bn = Bench(D, torch, dev, "tabulated_16384_k4096")
+    res = {"workload": "tabulated_16384_k4096: 16384 spectra (40 random Debye poles + Jonscher tail, 1% "
+                       "Gaussian noise), K=4096 over 1e5-1e10 Hz, N=20, P=512, 100 generations after the "
+                       "first, top-8 x 50 L-BFGS polish, mixed precision"}
+    with D.Handle("mixed") as h:
+        r = timed_fits(bn, h, 1, 1, flush, warm_iters=1)
+        res["ms_per_step"] = float(r["times"][0])
+        res["value"] = r["evals"][0] / (r["times"][0] * 1e-3)
+        res["unit"] = UNIT
+        res["cand_k_per_step"] = r["evals"][0]
+        prof = profile(D, h, lambda: bn.fit(h, r["out"], iters=2, topk=0))
+        res["roofline"] = roofline_mixed(bn, prof, "sums_tabulated_16384_k4096")
+        res["per_kind_ms_3_generations"] = per_kind_ms(prof)
+    return res
+
+
+def fp64_arm(D, torch, bn: Bench, precision: str, steps: int, flush, red, mixed_value):
+    """An FP64 evaluator on the headline fit: rate over `steps` timed fits (one warm-up), the
+    roofline of its Gram pass (one full-population evaluation, kernel timing on)."""
+    h = D.Handle(precision)
+    D.debye_autotune(h, bn.sp, bn.population(2))
+    r = timed_fits(bn, h, steps, 1, flush, red.barrier)
+    v = red.sum(sum(r["evals"])) / red.max(sum(r["times"]) * 1e-3)
+    out = host_out(r["out"])
+    th_pop = bn.population(1)
+    D.debye_eval_population(h, bn.sp, th_pop)
+    pd = profile(D, h, lambda: D.debye_eval_population(h, bn.sp, th_pop))
+    h.close()
+    n_g, ms_g, fl_g = pd["gram"]
+    what = ("FP64 Gram pass (k_pass<PH_GRAM, N>), 4N + 2(N+2)^2 FP64 FLOPs per cand*K" if precision == "fp64" else
+            "FP64 column-sum pass (k_pass<PH_GRAM_SUMS, N>), 8N + 2 FP64 FLOPs per cand*K")
+    ach = fl_g / (ms_g * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": what, "unit": "TFLOP/s", "achieved": ach, "peak": PEAK_FP64,
+            "frac": ach / PEAK_FP64, "ms_per_pass": ms_g / max(n_g, 1),
+            "cand_k_per_s_per_pass": bn.candk_pass / (ms_g * 1e-3 / max(n_g, 1)),
+            "peak_note": "nominal GB300 FP64 rate 1.25 TFLOP/s (an FMA-chain probe measured 1.195)",
+            "per_kind_ms_one_evaluation": per_kind_ms(pd)}
+    return ({"value": v, "unit": UNIT, "ms_per_step": float(np.mean(r["times"])), "steps": steps,
+             "speedup_mixed_over_this": mixed_value / v, "roofline": roof}, out)
+
+
+# ------------------------------------------------------------------ main
+
 def main():
-    global WORKLOAD, TOPK, POLISH_ITERS
+    global WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -228,6 +523,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--configs", default="all", help="extra workloads: all, none or a comma list of "
+                    + ", ".join(EXTRA_CONFIGS))
     ap.add_argument("--iters", type=int, default=None, help="swarm generations (default: the workload's)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(SETTINGS))
     ap.add_argument("--kernel-case", type=int, default=0, metavar="S",
@@ -240,232 +538,153 @@ def main():
     args = ap.parse_args()
 
     WORKLOAD = args.workload
-    P_w, iters_w, TOPK, POLISH_ITERS = SETTINGS[WORKLOAD]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    configs = [] if args.configs == "none" else (list(EXTRA_CONFIGS) if args.configs == "all"
+                                                else [c for c in args.configs.split(",") if c])
 
     if args.impl == "reference":
         return reference_arm(args, rank, world)
     if args.kernel_case:
-        return kernel_case(args.kernel_case, args.precision, P_w, args.kernel_n)
+        return kernel_case(args.kernel_case, args.precision, SETTINGS[WORKLOAD][0], args.kernel_n)
 
-    # the oracle baseline runs first, in spawned processes, before any CUDA call
-    cpu = None
+    # the oracle baselines run first, in spawned processes, before any CUDA call
+    cpu, cpu_tab = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(quick=False)
+        cpu = cpu_baseline(WORKLOAD, quick=False)
+        if "tabulated_16384_k4096" in configs:
+            cpu_tab = cpu_baseline("tabulated_16384_k4096", quick=False)
 
     import torch
     import torch.distributed as dist
-    from oracle import dls  # noqa: F401  (only for the fit-agreement statistics below)
     from paper_2109_01928_gb300 import debyefit as D
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", init_method="env://", device_id=dev)
-
     red = RankReduce(world, dev)
-    barrier, max_over_ranks, sum_over_ranks = red.barrier, red.max, red.sum
 
-    b = replica_workload(WORKLOAD, rank)
-    b.P = P_w
-    iters = iters_w if args.iters is None else args.iters
-    S = b.S
-    nmax = b.n_max
-    tt = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
-    offsets_d = tt(b.offsets, torch.int64)
-    omega_d = tt(b.omega)
-    # target synthesis (Eqs. 4-6) on the device, once, outside the timed region
-    with D.Handle("fp64") as hs:
-        noise = (tt(b.noise_re), tt(b.noise_im)) if b.noise_re is not None else (None, None)
-        eps_re_d, eps_im_d = D.debye_synth_targets(hs, offsets_d, omega_d, tt(b.model, torch.int32),
-                                                    tt(b.params), tt(b.pole_offsets, torch.int64),
-                                                    tt(b.pole_tau), tt(b.pole_deps), *noise)
-        D.debye_sync(hs)
-    sp = D.Spectra(offsets_d, omega_d, eps_re_d, eps_im_d, tt(b.n_poles, torch.int32), tt(b.lo), tt(b.hi),
-                   np.ascontiguousarray(b.offsets, np.int64), np.ascontiguousarray(b.n_poles, np.int32))
+    bn = Bench(D, torch, dev, WORKLOAD, seed=rank, b=replica_workload(WORKLOAD, rank))
+    if args.iters is not None:
+        bn.iters = args.iters
+    b = bn.b
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
-
-    def fit_once(h, out=None, spx=None):
-        return D.debye_fit_batch(h, spx or sp, P=b.P, iters=iters, seed=rank, polish_topk=TOPK,
-                                 polish_iters=POLISH_ITERS, n_max=nmax, out=out)
-
-    def timed_steps(h, steps, warmup, host_io=False):
-        """Per-step CUDA-event times (ms) and cand*K per step; L2 flushed between steps."""
-        out = None
-        for _ in range(warmup):
-            out = fit_once(h, out)
-        torch.cuda.synchronize()
-        times, evals = [], []
-        pinned = None
-        if host_io:
-            pinned = {k: torch.as_tensor(v).pin_memory() for k, v in (
-                ("offsets", np.ascontiguousarray(b.offsets, np.int64)), ("omega", b.omega),
-                ("eps_re", eps_re_d.cpu().numpy()), ("eps_im", eps_im_d.cpu().numpy()),
-                ("n_poles", np.ascontiguousarray(b.n_poles, np.int32)), ("lo", b.lo), ("hi", b.hi))}
-            dev_in = {k: torch.empty_like(v, device=dev) for k, v in pinned.items()}
-            res_host = {k: torch.empty(s, dtype=torch.float64).pin_memory()
-                        for k, s in (("eps_inf", (S,)), ("d_eps", (S, nmax)), ("tau", (S, nmax)),
-                                     ("final_cost", (S,)))}
-        barrier()
-        torch.cuda.synchronize()
-        D.debye_launch_count(h, reset=True)
-        for _ in range(steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            if host_io:
-                for k in pinned:
-                    dev_in[k].copy_(pinned[k], non_blocking=True)
-                spx = D.Spectra(dev_in["offsets"], dev_in["omega"], dev_in["eps_re"], dev_in["eps_im"],
-                                dev_in["n_poles"], dev_in["lo"], dev_in["hi"], sp.offsets_host,
-                                sp.n_poles_host)
-                out = fit_once(h, out, spx)
-                for k in res_host:
-                    res_host[k].copy_(out[k], non_blocking=True)
-            else:
-                out = fit_once(h, out)
-            e1.record()
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
-            evals.append(out["evals"].item())
-        barrier()
-        torch.cuda.synchronize()
-        timed_steps.launches = D.debye_launch_count(h)
-        h2d = sum(v.numel() * v.element_size() for v in pinned.values()) if host_io else 0
-        d2h = sum(v.numel() * v.element_size() for v in res_host.values()) if host_io else 0
-        return times, evals, out, h2d, d2h
 
     hm = D.Handle("mixed")
     # pick the work layout on this batch before timing (project autotuner)
-    th_tune = torch.as_tensor(W.population(b, b.P, seed=2), device=dev)
-    tuned = D.debye_autotune(hm, sp, th_tune)
-    del th_tune
+    tuned = D.debye_autotune(hm, bn.sp, bn.population(2))
     with ClockSampler(local) as clk:
-        times, evals, out_mixed, _, _ = timed_steps(hm, args.steps, args.warmup)
+        rm = timed_fits(bn, hm, args.steps, args.warmup, flush, red.barrier)
     clocks = clk.summary()
-    t_total = max_over_ranks(sum(times) * 1e-3)
-    work = sum_over_ranks(sum(evals))
-    value = work / t_total
-    launches = timed_steps.launches
+    value = red.sum(sum(rm["evals"])) / red.max(sum(rm["times"]) * 1e-3)
+    out_mixed = host_out(rm["out"])
 
     # end to end through the C ABI with host buffers (pinned H2D in, D2H of the result)
-    e_times, e_evals, _, h2d, d2h = timed_steps(hm, max(1, args.steps // 2), 1, host_io=True)
-    e2e_value = sum_over_ranks(sum(e_evals)) / max_over_ranks(sum(e_times) * 1e-3)
+    re2e = timed_fits(bn, hm, max(1, args.steps // 2), 1, flush, red.barrier, host_io=True)
+    e2e_value = red.sum(sum(re2e["evals"])) / red.max(sum(re2e["times"]) * 1e-3)
 
     # live kernel timing of one step (events on the launching stream; graph capture off)
-    D.debye_profile_enable(hm, True)
-    fit_once(hm, out_mixed)
-    torch.cuda.synchronize()
-    prof = D.debye_profile_read(hm)
-    D.debye_profile_enable(hm, False)
-    kind = max(("gram", "refine", "sums"), key=lambda k: prof[k][1])
-    n_l, ms_l, fl = prof[kind]
-    achieved = fl / (ms_l * 1e-3) / 1e12 if ms_l > 0 else 0.0
-    peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = load_traffic(kind)
-    # F(N) = 4N + 2(N+2)^2 per cand*K (basis + unique Gram products), averaged over the batch
-    fN = float(np.sum(b.K * b.P * (4 * b.n_poles + 2 * (b.n_poles + 2.0) ** 2)) / np.sum(b.K * b.P))
-    step_fp32 = value / world * fN / 1e12
+    prof = profile(D, hm, lambda: bn.fit(hm, rm["out"]))
+    roof = roofline_mixed(bn, prof, "sums_mixed_1024")
+    roof["per_kind_ms"] = per_kind_ms(prof)
+    roof["step_frac"] = value / world * bn.alg_flops_pass / bn.candk_pass / 1e12 / PEAK_FP32
 
     # one batched evaluation of the whole population vs one launch sequence per spectrum
     batching = None
     if not args.no_fp64 and world == 1:
-        th_pop = torch.as_tensor(W.population(b, b.P, seed=1), device=dev)
+        th_pop = bn.population(1)
         per_spec = []
-        for s in range(S):
+        for s in range(b.S):
             a_, c_ = int(b.offsets[s]), int(b.offsets[s + 1])
-            per_spec.append((D.Spectra(tt(np.array([0, c_ - a_]), torch.int64), omega_d[a_:c_], eps_re_d[a_:c_],
-                                       eps_im_d[a_:c_], tt(b.n_poles[s:s + 1], torch.int32), tt(b.lo[s:s + 1]),
-                                       tt(b.hi[s:s + 1]), np.array([0, c_ - a_], np.int64),
+            per_spec.append((D.Spectra(bn.tt(np.array([0, c_ - a_]), torch.int64), bn.omega_d[a_:c_],
+                                       bn.eps_re_d[a_:c_], bn.eps_im_d[a_:c_], bn.tt(b.n_poles[s:s + 1], torch.int32),
+                                       bn.tt(b.lo[s:s + 1]), bn.tt(b.hi[s:s + 1]), np.array([0, c_ - a_], np.int64),
                                        np.ascontiguousarray(b.n_poles[s:s + 1], np.int32)),
                              th_pop[s:s + 1].contiguous()))
         batching = {}
         for prec in ("mixed", "fp64"):
             with D.Handle(prec) as hb:
-                D.debye_eval_population(hb, sp, th_pop)        # warm-up (workspaces)
+                D.debye_eval_population(hb, bn.sp, th_pop)        # warm-up (workspaces)
                 for spx, thx in per_spec[:4]:
                     D.debye_eval_population(hb, spx, thx)
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
-                D.debye_eval_population(hb, sp, th_pop)
+                D.debye_eval_population(hb, bn.sp, th_pop)
                 e1.record()
                 torch.cuda.synchronize()
                 t_batched = e0.elapsed_time(e1)
-                t0 = time.perf_counter()
                 e0.record()
                 for spx, thx in per_spec:
                     D.debye_eval_population(hb, spx, thx)
                 e1.record()
                 torch.cuda.synchronize()
                 t_each = e0.elapsed_time(e1)
-            candk = float(b.P * b.K.sum())
             batching[prec] = {"batched_ms": t_batched, "per_spectrum_ms": t_each,
-                              "batched_candK_per_s": candk / (t_batched * 1e-3),
-                              "per_spectrum_candK_per_s": candk / (t_each * 1e-3)}
+                              "batched_candK_per_s": bn.candk_pass / (t_batched * 1e-3),
+                              "per_spectrum_candK_per_s": bn.candk_pass / (t_each * 1e-3)}
 
-    # the plain FP64 GPU evaluator on the same workload, and agreement of the fitted spectra
-    fp64 = None
+    # the FP64 GPU evaluators on the same fit: the plain method (direct Gram pass) and the Gram
+    # from FP64 column sums; their rooflines, and the agreement of the fitted spectra
+    fp64, fp64_sums = None, None
     if not args.no_fp64:
-        hd = D.Handle("fp64")
-        th_tune = torch.as_tensor(W.population(b, b.P, seed=2), device=dev)
-        D.debye_autotune(hd, sp, th_tune)
-        del th_tune
-        d_times, d_evals, out_fp64, _, _ = timed_steps(hd, 1, 1)
-        d_value = sum_over_ranks(sum(d_evals)) / max_over_ranks(sum(d_times) * 1e-3)
-        from oracle import models as om
-        rr, better = [], 0
-        for s in range(S):
-            a, c = b.offsets[s], b.offsets[s + 1]
-            N = int(b.n_poles[s])
-            em = om.multi_debye(b.omega[a:c], out_mixed["eps_inf"][s].item(),
-                                out_mixed["d_eps"][s, :N].cpu().numpy(), out_mixed["tau"][s, :N].cpu().numpy())
-            ed = om.multi_debye(b.omega[a:c], out_fp64["eps_inf"][s].item(),
-                                out_fp64["d_eps"][s, :N].cpu().numpy(), out_fp64["tau"][s, :N].cpu().numpy())
-            rr.append(float(np.linalg.norm(em - ed) / np.linalg.norm(ed)))
-            better += out_mixed["final_cost"][s].item() <= out_fp64["final_cost"][s].item() * (1 + 1e-6)
-        rr = np.array(rr)
-        fp64 = {"value": d_value, "unit": UNIT, "ms_per_step": sum(d_times) / len(d_times),
-                "speedup_mixed_over_fp64": value / d_value,
-                "fit_agreement": {"median_rel_rms": float(np.median(rr)),
-                                  "frac_rel_rms_le_1e-4": float(np.mean(rr <= 1e-4)),
-                                  "frac_mixed_cost_le_fp64": better / S}}
-        hd.close()
-
+        b.extra["_re"] = (bn.eps_re_d.cpu().numpy(), bn.eps_im_d.cpu().numpy())
+        fp64, out_fp64 = fp64_arm(D, torch, bn, "fp64", args.fp64_steps, flush, red, value)
+        fp64["fit_agreement"] = fit_agreement(b, out_mixed, out_fp64)
+        # noise floor of the criterion: the FP64 fit against itself with the damping moved by 1e-9
+        lam = D.default_options().lam_search * (1 + CTL_REL)
+        with D.Handle("fp64", lam_search=lam, lam_final=lam) as hc:
+            out_ctl = host_out(bn.fit(hc))
+        ctl = fit_agreement(b, out_ctl, out_fp64)
+        fp64["fit_agreement"]["fp64_control"] = {
+            "what": f"the FP64 fit with lam_search = lam_final = 1e-3 (1 + {CTL_REL:g}) against the FP64 fit: "
+                    "the same criteria, showing how many spectra a 1e-9 change of the problem moves past them",
+            **{k: ctl[k] for k in ("n_fail_both", "worst_cost_ratio", "frac_rel_rms_le_1e-4", "median_rel_rms")}}
+        fp64_sums, out_sums = fp64_arm(D, torch, bn, "fp64_sums", args.fp64_steps, flush, red, value)
+        fp64_sums["fit_agreement_vs_fp64"] = {
+            k: v for k, v in fit_agreement(b, out_sums, out_fp64).items() if k != "fit_error_vs_target"}
     hm.close()
+
+    extra = {}
+    if rank == 0 and world == 1:
+        if "single_hn_k50" in configs:
+            extra["single_hn_k50"] = config_single_hn(D, torch, dev, flush, 10)
+        if "hn_256_k2000" in configs:
+            extra["hn_256_k2000"] = config_hn256(D, torch, dev, flush, 3)
+        if "tabulated_16384_k4096" in configs:
+            del bn, flush
+            torch.cuda.empty_cache()
+            flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+            extra["tabulated_16384_k4096"] = config_tabulated(D, torch, dev, flush)
+            if cpu_tab:
+                extra["tabulated_16384_k4096"]["cpu_baseline"] = cpu_tab
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": sum(times) / len(times), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(rm["times"])), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded HN/CC/CD/Jonscher/CRIM spectra, targets synthesised on the device)",
-        "config": {"workload": workload_desc(b, iters),
+        "config": {"workload": workload_desc(b, bn.iters),
                    "precision": "mixed (float-float column sums, exact Gram identity, FP32 factor refined "
                                 "in float-float)",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches,
-        "autotune": {"cands_per_block": tuned},
-        "roofline": {"bound": "alu", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if peak else None, "traffic": traffic,
-                     "passes": n_l, "ms_per_pass": ms_l / max(n_l, 1),
-                     "pass_note": "one pass = the concurrent launches of the pass kernel for every "
-                                  "pole count (one kernel per N on forked streams), timed fork to join; "
-                                  "full-population passes only (the line search's masked passes are "
-                                  "timed under *_masked)",
-                     "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz",
-                     "step_fp32_tflops": step_fp32, "step_fp32_frac": step_fp32 / peak,
-                     "per_kind_ms": {k: v[1] for k, v in prof.items()}},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": re2e["h2d"],
+                "d2h_bytes_per_step": re2e["d2h"]},
+        "gpu_launches": rm["launches"],
+        "autotune": tuned,
+        "roofline": roof,
         "cpu_baseline": cpu,
         "fp64_plain": fp64,
+        "fp64_sums": fp64_sums,
         "eval_batching": batching,
+        "configs": extra,
     }
     print(json.dumps(line))
     if world > 1:
@@ -498,9 +717,10 @@ def kernel_case(S: int, precision: str, P: int, n_poles: int = 0):
 
 def workload_desc(b, iters) -> str:
     """The timed workload, as both arms name it in `config`."""
+    P, _, topk, pit = SETTINGS[WORKLOAD]
     return (f"{WORKLOAD}: {b.S} spectra, K {int(b.K.min())}-{int(b.K.max())} (sum {int(b.K.sum())}), "
-            f"N {int(b.n_poles.min())}-{int(b.n_poles.max())}, P={b.P}, {iters} swarm generations after the "
-            f"first, top-{TOPK} x {POLISH_ITERS} L-BFGS polish")
+            f"N {int(b.n_poles.min())}-{int(b.n_poles.max())}, P={P}, {iters} swarm generations after the "
+            f"first, top-{topk} x {pit} L-BFGS polish")
 
 
 def reference_arm(args, rank, world):
@@ -509,13 +729,14 @@ def reference_arm(args, rank, world):
         return
     cores = os.cpu_count() or 1
     times, work = [], []
+    used = cores
     for i in range(args.warmup + args.steps):
-        r, w, t = oracle_rate(max(cores, 4), 2, cores, seed=i)
+        r, w, t, used = oracle_rate(WORKLOAD, max(cores, 4), 2, cores, seed=i)
         if i >= args.warmup:
             times.append(t)
             work.append(w)
     value = sum(work) / sum(times)
-    cpu = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+    cpu = {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
            "sample": f"per step {max(cores, 4)} seeded spectra of {WORKLOAD}, P={SETTINGS[WORKLOAD][0]}, "
                      f"2 swarm generations"}
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -524,7 +745,7 @@ def reference_arm(args, rank, world):
                       "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                       "config": {"workload": workload_desc(W.workload(WORKLOAD), SETTINGS[WORKLOAD][1]),
                                  "precision": "FP64 oracle (numpy, host cores)",
-                                 "sample": cpu["sample"], "parallelism": f"{cores} host processes"},
+                                 "sample": cpu["sample"], "parallelism": f"{used} host processes"},
                       "cpu_baseline": cpu,
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 

@@ -30,7 +30,11 @@
  *     work-list bound violated) are recorded in a device status word and returned
  *     by the next debye_sync().
  *   - A candidate whose damped normal matrix is not positive definite gets cost
- *     +inf; that is a result, not a call error.
+ *     +inf, weights and gradient 0, and counts in the optional per-spectrum
+ *     n_failed output; that is a result, not a call error. With lam_search > 0 the
+ *     damped matrix G + lam diag(G) is positive definite for every finite theta
+ *     (diag(G) > 0 for Debye columns), so in practice a candidate fails only for a
+ *     non-finite theta or with lam_search = 0.
  *   - Calls on one handle must not overlap in time (one host thread at a time);
  *     different handles are independent.
  */
@@ -58,6 +62,9 @@ extern "C" {
 #define DEBYE_PREC_FP64  0    /* FP64 basis, Gram, solve and residual */
 #define DEBYE_PREC_MIXED 1    /* float-float column sums of the Debye basis, exact Gram identity,
                                  FP32 factor refined in float-float */
+#define DEBYE_PREC_FP64_SUMS 2 /* FP64 throughout, the Gram from FP64 column sums by the exact
+                                 identity (no O(K N^2) Gram pass), then the FP64 solve and
+                                 residual passes of DEBYE_PREC_FP64 */
 
 #define DEBYE_MAX_POLES 20    /* largest N accepted */
 
@@ -83,7 +90,7 @@ typedef struct debye_ctx* debye_handle;
 
 /* Solver options. debye_default_options() fills the documented defaults. */
 typedef struct {
-  int32_t precision;      /* DEBYE_PREC_FP64 or DEBYE_PREC_MIXED (default MIXED) */
+  int32_t precision;      /* DEBYE_PREC_FP64, DEBYE_PREC_MIXED (default) or DEBYE_PREC_FP64_SUMS */
   int32_t refine_steps;   /* FP64 precision: residual passes with refinement after the first
                              solve, 1..4 (default 1); the mixed path refines on its small
                              float-float system instead and ignores it */
@@ -95,7 +102,9 @@ typedef struct {
   int32_t lbfgs_m;        /* L-BFGS history pairs, 1..8 (default 8) */
   int32_t lbfgs_max_trials; /* backtracking halvings per iteration, 1..40 (default 20) */
   double  lbfgs_c1;       /* Armijo constant (default 1e-4) */
-  int32_t cands_per_block;/* candidates per thread block, 32..128, multiple of 32; 0 = autotune */
+  int32_t cands_per_block;/* candidates per thread block of full populations, 1..128 with
+                             cands_per_block x lanes (lanes_per_candidate, 1 if 0) a
+                             multiple of 32 and at most 128; 0 = autotune / 64 */
   int32_t use_graphs;     /* capture the generation and polish loops in CUDA graphs (default 1) */
   double  de_f_lo;        /* differential evolution: scale factor F ~ U[de_f_lo, de_f_hi) drawn */
   double  de_f_hi;        /*   once per generation; 0 <= lo <= hi <= 2 (default 0.5, 1.0) */
@@ -110,6 +119,10 @@ typedef struct {
                              candidates per SM). Results agree to rounding either way.
                              debye_eval_population_noalloc always takes one thread per
                              candidate. */
+  int32_t lanes_per_candidate; /* lanes that share one candidate's frequency samples in the
+                             pass kernels of full populations (a warp or more of
+                             candidates per spectrum): 0 = autotune / 1, else 1..32, a
+                             power of two */
 } debye_options;
 
 /* A ragged batch of S spectra, CSR over frequency (all device memory unless _host). */
@@ -134,8 +147,14 @@ typedef struct {
   int32_t  polish_topk;   /* personal bests polished per spectrum, 0..min(P,64) */
   int32_t  polish_iters;  /* L-BFGS iterations per polished candidate, >= 0 */
   double*  trace;         /* optional [S][iters+1] device: global-best cost per generation */
-  double*  evals;         /* optional [1] device: candidate evaluations x K performed */
+  double*  evals;         /* optional [1] device: candidate evaluations x K, counted as a
+                             sequential search evaluates them (the swarm's populations; per
+                             polish iteration the trials of a backtracking line search up to
+                             the accepted one, not the speculative step lengths after it) */
   int32_t  method;        /* DEBYE_SEARCH_PSO (0), DEBYE_SEARCH_DE or DEBYE_SEARCH_DA */
+  int32_t* n_failed;      /* optional [S] device, caller-initialised: incremented once per
+                             evaluated candidate of spectrum s (search, polish and final
+                             re-solve) whose damped normal matrix is not positive definite */
 } debye_search;
 
 /* Fill *opt with the defaults listed above. */
@@ -166,14 +185,19 @@ int debye_synth_targets(debye_handle h, int64_t S, const int64_t* offsets, const
  * the damped least-squares weights at damping lam_search, the sign flip of
  * negative d_eps, and cost = ||A x_hat - b||^2 + lam sum_j G_jj x_hat_j^2 over the
  * stacked real/imaginary rows. cost [S][P]; weights [S][P][n_max+1] or NULL.
- * n_max >= max_s N_s. */
+ * n_max >= max_s N_s. n_failed [S] (device, caller-initialised, or NULL) is
+ * incremented once per candidate of spectrum s whose damped normal matrix is not
+ * positive definite (its cost is +inf and its weights 0). */
 int debye_eval_population(debye_handle h, const debye_spectra* spectra, int32_t P, int32_t n_max,
-                          const double* theta, double* cost, double* weights, cudaStream_t stream);
+                          const double* theta, double* cost, double* weights, int32_t* n_failed,
+                          cudaStream_t stream);
 
 /* Cost (as debye_eval_population) and its exact gradient d cost / d theta
- * (variable projection, including the flipped case), grad [S][P][n_max]. */
+ * (variable projection, including the flipped case), grad [S][P][n_max];
+ * n_failed as for debye_eval_population (the gradient of a failed candidate is 0). */
 int debye_cost_grad(debye_handle h, const debye_spectra* spectra, int32_t P, int32_t n_max,
-                    const double* theta, double* cost, double* grad, cudaStream_t stream);
+                    const double* theta, double* cost, double* grad, int32_t* n_failed,
+                    cudaStream_t stream);
 
 /* Whole fit (Sec. III-B, IV): seeded particle swarm, differential evolution or
  * dual annealing over log10(tau) with DLS weights, projected L-BFGS polish of
@@ -199,7 +223,7 @@ int debye_fit_batch(debye_handle h, const debye_spectra* spectra, const debye_se
  * ragged batch; spectra that found their N leave before the next wave (the call
  * synchronises its work stream once per wave). Outputs as debye_fit_batch
  * (d_eps, tau [S][n_max], zero beyond the chosen N) plus frac_err [S] (percent)
- * and n_chosen [S]. search->trace must be NULL. */
+ * and n_chosen [S]. search->trace and search->n_failed must be NULL. */
 int debye_fit_auto(debye_handle h, const debye_spectra* spectra, const debye_search* search,
                    int32_t n_max, double threshold, int32_t wave, double* eps_inf, double* d_eps,
                    double* tau, double* final_cost, double* frac_err, int32_t* n_chosen,
@@ -240,14 +264,18 @@ int debye_eval_population_noalloc(const debye_options* opt, const debye_spectra*
                                   int32_t n_max, const double* theta, double* cost, double* weights,
                                   char* err, int32_t err_len, cudaStream_t stream);
 
-/* Work-layout autotuner. Times debye_eval_population on the caller's batch
- * (theta as for that call, cost [S][P] is overwritten) for every candidates-
- * per-block choice (32, 64, 96, 128) and keeps the fastest for this handle; it
- * is used by later calls whose options leave cands_per_block at 0 (auto).
- * cache_path (may be NULL) is a text file of "key | choice" lines keyed by the
- * device's SM count, precision, S, P, n_max and sample count: a cached choice
- * is reused without timing, a new one is appended. *chosen (may be NULL)
- * receives the choice. Synchronises `stream`. */
+/* Work-layout autotuner, for two shapes. Full populations: times
+ * debye_eval_population on the caller's batch (theta as for that call, cost
+ * [S][P] is overwritten) for every (candidates per block, lanes per candidate)
+ * in {(32,1), (64,1), (96,1), (128,1), (32,2), (64,2), (32,4)}. The polish's
+ * accepted points: times debye_cost_grad on the first min(P, 8) candidates of
+ * every spectrum for (cb, lanes) in {(16,4), (8,8), (4,16), (2,32), (32,4),
+ * (16,8), (8,16), (4,32)}. The fastest of each is kept for this handle and used
+ * by later calls whose options leave cands_per_block and lanes_per_candidate at
+ * 0. cache_path (may be NULL) is a text file of "key | cb lanes polish_cb
+ * polish_lanes" lines keyed by the device's SM count, precision, S, P, n_max and
+ * sample count: a cached choice is reused without timing, a new one is appended.
+ * chosen (may be NULL) receives the four numbers. Synchronises `stream`. */
 int debye_autotune(debye_handle h, const debye_spectra* spectra, int32_t P, int32_t n_max,
                    const double* theta, double* cost, const char* cache_path, int32_t* chosen,
                    cudaStream_t stream);

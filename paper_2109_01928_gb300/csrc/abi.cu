@@ -100,6 +100,9 @@ int debye_ctx::prof_collect() {
 // renormalisation, ||r||^2 and the eps_inf column).
 static double flops_per_cand_k(int phase, int N) {
   if (phase == PH_GRAM) return 4.0 * N + 2.0 * (N + 2) * (N + 2);
+  // FP64 column sums: per sample omega^2 and omega eps'' (2), per pole omega^2 tau^2 + 1
+  // (FMA), the reciprocal, S += re and two FMAs (8, the reciprocal counted as 1)
+  if (phase == PH_GRAM_SUMS) return 8.0 * N + 2.0;
   if (phase == PH_REFINE) return 13.0 * N + 5.0;
   // column sums: FP32 operations per (sample, pole) of the float-float sequence in the
   // squared form (FMA = 2): 54, and 103 with the derivative sums
@@ -111,6 +114,7 @@ static double flops_per_cand_k(int phase, int N) {
 // Profiling kind of a pass of `phase`, restricted by an activity mask or not.
 static int pass_kind(int phase, bool masked) {
   if (phase == PH_SUMS || phase == PH_SUMSG) return masked ? DEBYE_KERNEL_SUMS_MASKED : DEBYE_KERNEL_SUMS;
+  if (phase == PH_GRAM_SUMS) return masked ? DEBYE_KERNEL_GRAM_MASKED : DEBYE_KERNEL_GRAM;
   return masked ? DEBYE_KERNEL_GRAM_MASKED + phase : phase;
 }
 
@@ -250,25 +254,24 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
   // that the pole counts' launches run concurrently and fill the GPU together.
   // Kernel timing brackets the whole pass (fork to join) with events on st: its
   // duration is that of the pass as it runs, and its FLOPs those of every bucket.
-  auto per_bucket = [&](int phase) -> int {
+  // body(b, ab, stream) launches bucket b's work (ab: the arguments restricted to its
+  // units) for every non-empty bucket below b_hi; kind >= 0 times the whole fork-join.
+  // The buckets are launched from the most poles down: the block scheduler starts the
+  // kernels' blocks in launch order, so the longest-running blocks start first and the
+  // short ones fill in behind them instead of forming the pass's tail.
+  auto fork_buckets = [&](int kind, double flops, int b_hi, auto body) -> int {
     int first = -1, n_nonempty = 0;
-    for (int b = 0; b < N_BUCKETS; ++b)
+    for (int b = b_hi - 1; b >= 0; --b)
       if (g.begin[b + 1] > g.begin[b]) {
         if (first < 0) first = b;
         ++n_nonempty;
       }
     if (!n_nonempty) return DEBYE_OK;
     ProfEntry pe;
-    if (prof_on) {
-      double fl = 0.0;
-      if (!a.active)
-        for (const Unit& x : g.units)
-          fl += (double)(x.q1 - x.q0) * (double)(x.k1 - x.k0) * flops_per_cand_k(phase, x.N);
-      prof_begin(pass_kind(phase, a.active != nullptr), fl, st, pe);
-    }
+    if (prof_on && kind >= 0) prof_begin(kind, flops, st, pe);
     const bool fork = n_nonempty > 1;
     if (fork) cudaEventRecord(ev_fork, st);
-    for (int b = 0; b < N_BUCKETS; ++b) {
+    for (int b = b_hi - 1; b >= 0; --b) {
       const int n = g.begin[b + 1] - g.begin[b];
       if (!n) continue;
       cudaStream_t bs = st;
@@ -279,16 +282,28 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
       EvalArgs ab = a;
       ab.units = a.units + g.begin[b];
       ab.n_units = n;
-      const int grid = std::max(1, std::min(n, sms * 16));
-      launch_pass(b + 1, phase, ab, grid, cb * a.ks, bs);
-      ++launches;
+      body(b, ab, bs);
       if (bs != st) {
         cudaEventRecord(ev_join[b], bs);
         cudaStreamWaitEvent(st, ev_join[b], 0);
       }
     }
-    if (prof_on) prof_end(pe, st);
+    if (prof_on && kind >= 0) prof_end(pe, st);
     return check_launch("pass");
+  };
+  auto pass_flops = [&](int phase) {
+    double fl = 0.0;
+    if (prof_on && !a.active)
+      for (const Unit& x : g.units) fl += (double)(x.q1 - x.q0) * (double)(x.k1 - x.k0) * flops_per_cand_k(phase, x.N);
+    return fl;
+  };
+  auto launch_bucket_pass = [&](int phase, int b, const EvalArgs& ab, cudaStream_t bs) {
+    launch_pass(b + 1, phase, ab, std::max(1, std::min(ab.n_units, sms * 16)), cb * a.ks, bs);
+    ++launches;
+  };
+  auto per_bucket = [&](int phase) -> int {
+    return fork_buckets(pass_kind(phase, a.active != nullptr), pass_flops(phase), N_BUCKETS,
+                        [&](int b, const EvalArgs& ab, cudaStream_t bs) { launch_bucket_pass(phase, b, ab, bs); });
   };
   auto timed = [&](int kind, auto launch) {
     ProfEntry pe;
@@ -303,19 +318,50 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
   if (a.ks < 1 || a.ks > 32 || (a.ks & (a.ks - 1)) || cb * a.ks > MAX_BLOCK)
     return fail(DEBYE_EINTERNAL, "bad work layout (%d candidates x %d lanes)", cb, a.ks);
   const int gblock = warp_round(cb);
+  auto grid_solve = [&](int n) { return std::max(1, std::min(n, sms * 32)); };
   if (mixed) {
     // one float-float column-sum pass (with the derivative sums when the gradient is
     // wanted), then weights, cost and gradient from the exact Gram identity of the
-    // Debye columns (k_solve_sums)
-    if ((rc = per_bucket(grad ? PH_SUMSG : PH_SUMS))) return rc;
+    // Debye columns. With the thread-per-candidate solve, buckets up to SOLVE_N_MAX
+    // poles solve in a per-N kernel (systems in registers) launched right after the
+    // bucket's pass on the bucket's stream; the other buckets take the general
+    // kernel after the join, and the warp-per-candidate solve runs after it. With
+    // kernel timing on, the per-N solves run after the timed pass, timed on their own.
+    const int ph = grad ? PH_SUMSG : PH_SUMS, sph = grad ? PH_SOLVEG : PH_SOLVE;
     const bool by_warp = solve_sums_by_warp(a.sc.Q, opt.solve_lanes, sms);
-    timed(DEBYE_KERNEL_SOLVE, [&] {
-      if (by_warp) launch_solve_sums_warp(a, cost, weights, grad, cb, sms, st);
-      else launch_solve_sums(a, cost, weights, grad, gblock, sms, st);
-    });
+    const int nb_n = by_warp ? 0 : SOLVE_N_MAX;   // buckets with a per-N solve
+    auto solve_bucket = [&](int b, const EvalArgs& ab, cudaStream_t bs) {
+      if (b >= nb_n) return;
+      EvalArgs as = ab;
+      as.out_cost = cost;
+      as.out_weights = weights;
+      as.out_grad = grad;
+      launch_pass(b + 1, sph, as, grid_solve(ab.n_units), gblock, bs);
+      ++launches;
+    };
+    if (!prof_on) {
+      rc = fork_buckets(-1, 0.0, N_BUCKETS, [&](int b, const EvalArgs& ab, cudaStream_t bs) {
+        launch_bucket_pass(ph, b, ab, bs);
+        solve_bucket(b, ab, bs);
+      });
+    } else {
+      rc = per_bucket(ph);
+      if (!rc) rc = fork_buckets(DEBYE_KERNEL_SOLVE, 0.0, nb_n, solve_bucket);
+    }
+    if (rc) return rc;
+    const int u0 = g.begin[nb_n], rest = g.begin[N_BUCKETS] - u0;
+    if (rest) {
+      EvalArgs ar = a;
+      ar.units = a.units + u0;
+      ar.n_units = rest;
+      timed(DEBYE_KERNEL_SOLVE, [&] {
+        if (by_warp) launch_solve_sums_warp(ar, cost, weights, grad, cb, sms, st);
+        else launch_solve_sums(ar, cost, weights, grad, gblock, sms, st);
+      });
+    }
     return check_launch("column-sum solve");
   }
-  if ((rc = per_bucket(PH_GRAM))) return rc;
+  if ((rc = per_bucket(opt.precision == DEBYE_PREC_FP64_SUMS ? PH_GRAM_SUMS : PH_GRAM))) return rc;
   timed(DEBYE_KERNEL_SOLVE, [&] { launch_solve(a, gblock, sms, st); });
   if ((rc = check_launch("solve"))) return rc;
   for (int it = 0; it < steps; ++it) {
@@ -336,7 +382,7 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
 // Common path of debye_eval_population / debye_cost_grad.
 static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n_max,
                       const double* theta, double* cost, double* weights, double* grad,
-                      cudaStream_t st) {
+                      int32_t* n_failed, cudaStream_t st) {
   if (!h) return DEBYE_EINVAL;
   h->err.clear();
   if (P < 1) return h->fail(DEBYE_EINVAL, "P = %d < 1", P);
@@ -356,7 +402,12 @@ static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_
     qe[s] = (int32_t)((s + 1) * P);
   }
   int cb, ks;
-  choose_layout(P, pl.S * (int64_t)P, h->sms, h->opt.cands_per_block, h->tuned_cb, &cb, &ks);
+  if (h->layout_override.cb > 0) {
+    cb = h->layout_override.cb;
+    ks = h->layout_override.ks;
+  } else {
+    choose_layout(P, pl.S * (int64_t)P, h->sms, h->forced(), h->tuned, &cb, &ks);
+  }
   UnitGroups g;
   build_units(pl, qb, qe, cb, g);
   if ((rc = h->upload_units(g, h->ws_units, st))) return rc;
@@ -376,6 +427,7 @@ static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_
   a.h0 = (const double*)h->ws_h0.p;
   a.bb = a.h0 + pl.S;
   a.active = nullptr;
+  a.n_failed = n_failed;
   a.ks = ks;
   a.lam = h->opt.lam_search;
   a.status = h->d_status;
@@ -423,6 +475,7 @@ void debye_default_options(debye_options* o) {
   o->da_t0 = 5230.0;
   o->da_qa = -5.0;
   o->solve_lanes = 0;
+  o->lanes_per_candidate = 0;
 }
 
 int debye_fit_init(debye_handle* out, const debye_options* opt) {
@@ -431,19 +484,26 @@ int debye_fit_init(debye_handle* out, const debye_options* opt) {
   debye_options o;
   if (opt) o = *opt;
   else debye_default_options(&o);
-  if (o.precision != DEBYE_PREC_FP64 && o.precision != DEBYE_PREC_MIXED) return DEBYE_EINVAL;
+  if (o.precision != DEBYE_PREC_FP64 && o.precision != DEBYE_PREC_MIXED && o.precision != DEBYE_PREC_FP64_SUMS)
+    return DEBYE_EINVAL;
   if (o.refine_steps < 1 || o.refine_steps > 4) return DEBYE_EINVAL;
   if (!(o.lam_search >= 0.0) || !(o.lam_final >= 0.0)) return DEBYE_EINVAL;
   if (o.lbfgs_m < 1 || o.lbfgs_m > 8) return DEBYE_EINVAL;
   if (o.lbfgs_max_trials < 1 || o.lbfgs_max_trials > 40) return DEBYE_EINVAL;
-  if (o.cands_per_block != 0 &&
-      (o.cands_per_block < 32 || o.cands_per_block > MAX_BLOCK || o.cands_per_block % 32))
-    return DEBYE_EINVAL;
+  if (o.cands_per_block < 0 || o.cands_per_block > MAX_BLOCK) return DEBYE_EINVAL;
   if (!(o.de_f_lo >= 0.0) || !(o.de_f_hi >= o.de_f_lo) || !(o.de_f_hi <= 2.0)) return DEBYE_EINVAL;
   if (!(o.de_cr >= 0.0) || !(o.de_cr <= 1.0)) return DEBYE_EINVAL;
   if (o.de_strategy != DEBYE_DE_RAND1 && o.de_strategy != DEBYE_DE_BEST1) return DEBYE_EINVAL;
   if (!(o.da_t0 > 0.0) || !(o.da_t0 < 1e300) || !(o.da_qa < 1.0) || !(o.da_qa > -1e6)) return DEBYE_EINVAL;
   if (o.solve_lanes != 0 && o.solve_lanes != 1 && o.solve_lanes != 32) return DEBYE_EINVAL;
+  if (o.lanes_per_candidate != 0 &&
+      (o.lanes_per_candidate < 1 || o.lanes_per_candidate > 32 || (o.lanes_per_candidate & (o.lanes_per_candidate - 1))))
+    return DEBYE_EINVAL;
+  // a pass block (candidates x lanes) is whole warps, at most MAX_BLOCK threads
+  if (o.cands_per_block &&
+      (o.cands_per_block * std::max(o.lanes_per_candidate, 1) > MAX_BLOCK ||
+       (o.cands_per_block * std::max(o.lanes_per_candidate, 1)) % 32))
+    return DEBYE_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -478,14 +538,15 @@ int debye_fit_destroy(debye_handle h) {
 }
 
 int debye_eval_population(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n_max,
-                          const double* theta, double* cost, double* weights, cudaStream_t st) {
-  return eval_entry(h, sp, P, n_max, theta, cost, weights, nullptr, st);
+                          const double* theta, double* cost, double* weights, int32_t* n_failed,
+                          cudaStream_t st) {
+  return eval_entry(h, sp, P, n_max, theta, cost, weights, nullptr, n_failed, st);
 }
 
 int debye_cost_grad(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n_max,
-                    const double* theta, double* cost, double* grad, cudaStream_t st) {
+                    const double* theta, double* cost, double* grad, int32_t* n_failed, cudaStream_t st) {
   if (h && !grad) return h->fail(DEBYE_EINVAL, "grad is NULL");
-  return eval_entry(h, sp, P, n_max, theta, cost, nullptr, grad, st);
+  return eval_entry(h, sp, P, n_max, theta, cost, nullptr, grad, n_failed, st);
 }
 
 int debye_synth_targets(debye_handle h, int64_t S, const int64_t* offsets, const double* omega,
@@ -527,12 +588,25 @@ int debye_autotune(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n
   if (!h) return DEBYE_EINVAL;
   h->err.clear();
   if (!sp || !theta || !cost) return h->fail(DEBYE_EINVAL, "spectra, theta or cost is NULL");
+  if (P < 1 || n_max < 1 || n_max > NMAX) return h->fail(DEBYE_EINVAL, "P < 1 or n_max outside 1..%d", NMAX);
   char key[160];
   int64_t nsamp = 0;
   if (sp->offsets_host && sp->S > 0) nsamp = sp->offsets_host[sp->S];
   snprintf(key, sizeof(key), "sms=%d prec=%d S=%lld P=%d nmax=%d samples=%lld", h->sms, h->opt.precision,
            (long long)sp->S, P, n_max, (long long)nsamp);
-  if (cache_path) {  // "key | cb" lines
+  auto valid = [](Layout l, bool full) {
+    const bool pow2 = l.ks >= 1 && l.ks <= 32 && (l.ks & (l.ks - 1)) == 0;
+    return pow2 && l.cb >= 1 && l.cb * l.ks <= MAX_BLOCK && (!full || l.cb % 32 == 0);
+  };
+  auto report = [&]() {
+    if (chosen) {
+      chosen[0] = h->tuned.cb;
+      chosen[1] = h->tuned.ks;
+      chosen[2] = h->tuned_polish.cb;
+      chosen[3] = h->tuned_polish.ks;
+    }
+  };
+  if (cache_path) {  // "key | cb ks polish_cb polish_ks" lines
     if (FILE* f = fopen(cache_path, "r")) {
       char line[256];
       while (fgets(line, sizeof(line), f)) {
@@ -541,56 +615,92 @@ int debye_autotune(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n
         *bar = '\0';
         std::string k(line);
         while (!k.empty() && k.back() == ' ') k.pop_back();
-        if (k == key) {
-          const int cb = atoi(bar + 1);
-          if (cb >= 32 && cb <= MAX_BLOCK && cb % 32 == 0) {
-            h->tuned_cb = cb;
-            if (chosen) *chosen = cb;
-            fclose(f);
-            return DEBYE_OK;
-          }
+        Layout full, pol;
+        if (k == key && sscanf(bar + 1, "%d %d %d %d", &full.cb, &full.ks, &pol.cb, &pol.ks) == 4 &&
+            valid(full, true) && valid(pol, false)) {
+          h->tuned = full;
+          h->tuned_polish = pol;
+          report();
+          fclose(f);
+          return DEBYE_OK;
         }
       }
       fclose(f);
     }
   }
-  const int saved = h->opt.cands_per_block;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     cudaGetLastError();
     return h->fail(DEBYE_ECUDA, "event creation failed");
   }
-  int best = 0;
-  float best_ms = 0.f;
-  int rc = DEBYE_OK;
-  for (int cb = 32; cb <= MAX_BLOCK && rc == DEBYE_OK; cb += 32) {
-    h->opt.cands_per_block = cb;
-    rc = debye_eval_population(h, sp, P, n_max, theta, cost, nullptr, st);   // warm-up
-    if (rc) break;
-    float ms = 0.f;
+  // time one evaluation (after a warm-up) of the given layout; eval() runs it
+  auto time_layout = [&](Layout l, auto eval, float* ms) -> int {
+    h->layout_override = l;
+    int rc = eval();
+    float tot = 0.f;
     for (int rep = 0; rep < 2 && rc == DEBYE_OK; ++rep) {
       cudaEventRecord(e0, st);
-      rc = debye_eval_population(h, sp, P, n_max, theta, cost, nullptr, st);
+      rc = eval();
       cudaEventRecord(e1, st);
       cudaEventSynchronize(e1);
       float t = 0.f;
       cudaEventElapsedTime(&t, e0, e1);
-      ms += t;
+      tot += t;
     }
-    if (rc == DEBYE_OK && (best == 0 || ms < best_ms)) {
-      best = cb;
+    h->layout_override = Layout{};
+    *ms = tot;
+    return rc;
+  };
+  int rc = DEBYE_OK;
+  // full population: the caller's batch, cost only (the swarm's evaluations)
+  Layout best_full, best_pol;
+  float best_ms = 0.f;
+  static const Layout full_set[] = {{32, 1}, {64, 1}, {96, 1}, {128, 1}, {32, 2}, {64, 2}, {32, 4}};
+  for (const Layout& l : full_set) {
+    float ms = 0.f;
+    rc = time_layout(l, [&] { return debye_eval_population(h, sp, P, n_max, theta, cost, nullptr, nullptr, st); },
+                     &ms);
+    if (rc) break;
+    if (!best_full.cb || ms < best_ms) {
+      best_full = l;
       best_ms = ms;
+    }
+  }
+  // the polish's accepted points: the first T = min(P, 8) candidates of every spectrum with
+  // their gradient, over a range of lane splits
+  const int T = std::min(P, 8);
+  if (rc == DEBYE_OK && sp->S > 0) {
+    void *pt = nullptr, *pc = nullptr, *pg = nullptr;
+    const size_t row = sizeof(double) * (size_t)n_max;
+    if (!(rc = h->named("tune.theta", row * T * sp->S, &pt)) && !(rc = h->named("tune.cost", sizeof(double) * T * sp->S, &pc)) &&
+        !(rc = h->named("tune.grad", row * T * sp->S, &pg))) {
+      cudaError_t e = cudaMemcpy2DAsync(pt, row * T, theta, row * P, row * T, sp->S, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) rc = h->fail(DEBYE_ECUDA, "autotune copy: %s", cudaGetErrorString(e));
+    }
+    static const Layout pol_set[] = {{16, 4}, {8, 8}, {4, 16}, {2, 32}, {32, 4}, {16, 8}, {8, 16}, {4, 32}};
+    best_ms = 0.f;
+    for (const Layout& l : pol_set) {
+      if (rc) break;
+      float ms = 0.f;
+      rc = time_layout(l, [&] {
+        return debye_cost_grad(h, sp, T, n_max, (const double*)pt, (double*)pc, (double*)pg, nullptr, st);
+      }, &ms);
+      if (rc) break;
+      if (!best_pol.cb || ms < best_ms) {
+        best_pol = l;
+        best_ms = ms;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  h->opt.cands_per_block = saved;
   if (rc) return rc;
-  h->tuned_cb = best;
-  if (chosen) *chosen = best;
+  h->tuned = best_full;
+  h->tuned_polish = best_pol;
+  report();
   if (cache_path) {
     if (FILE* f = fopen(cache_path, "a")) {
-      fprintf(f, "%s | %d\n", key, best);
+      fprintf(f, "%s | %d %d %d %d\n", key, best_full.cb, best_full.ks, best_pol.cb, best_pol.ks);
       fclose(f);
     }
   }

@@ -138,6 +138,7 @@ extern "C" int debye_fit_auto(debye_handle h, const debye_spectra* sp, const deb
   h->err.clear();
   if (!sp || !se) return h->fail(DEBYE_EINVAL, "spectra or search is NULL");
   if (se->trace) return h->fail(DEBYE_EINVAL, "search->trace is not supported by debye_fit_auto");
+  if (se->n_failed) return h->fail(DEBYE_EINVAL, "search->n_failed is not supported by debye_fit_auto");
   if (se->P < 1 || se->P > 32768) return h->fail(DEBYE_EINVAL, "P = %d outside 1..32768", se->P);
   if (se->iters < 0 || se->polish_iters < 0) return h->fail(DEBYE_EINVAL, "iters < 0 or polish_iters < 0");
   if (se->polish_topk < 0 || se->polish_topk > 64) return h->fail(DEBYE_EINVAL, "polish_topk outside 0..64");

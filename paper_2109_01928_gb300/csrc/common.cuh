@@ -21,7 +21,15 @@ constexpr int NPACK_MAX = NMAX1 * (NMAX1 + 1) / 2;
 // Packed lower-triangular index of (I, J), J <= I.
 __host__ __device__ constexpr int pk(int I, int J) { return I * (I + 1) / 2 + J; }
 
-enum Phase { PH_GRAM = 0, PH_REFINE = 1, PH_GRAD = 2, PH_SUMS = 3, PH_SUMSG = 4 };
+enum Phase { PH_GRAM = 0, PH_REFINE = 1, PH_GRAD = 2, PH_SUMS = 3, PH_SUMSG = 4,
+             // mixed precision: weights, cost (and gradient) from a bucket's column sums,
+             // one thread per candidate, the pole count fixed at compile time
+             PH_SOLVE = 5, PH_SOLVEG = 6,
+             // FP64 column sums and the Gram from the partial-fraction identity (FP64 path)
+             PH_GRAM_SUMS = 7 };
+// Largest pole count with a compile-time (register-resident) column-sum solve;
+// larger ones use the general kernel.
+constexpr int SOLVE_N_MAX = 12;
 // The column sums with the derivative sums (eval.cuh, sums_sq_unit) sweep the
 // samples once for up to this many poles (14 registers per pole) and twice, about
 // N/2 poles each, above it; the cost-only sums (8 registers per pole) always sweep
@@ -67,8 +75,13 @@ struct EvalArgs {
   const double* h0;        // [S] sum_k eps'_k
   const double* bb;        // [S] b^T b = sum_k eps'_k^2 + eps''_k^2
   const uint8_t* active;   // [Q] optional candidate mask (nullptr: all)
+  int32_t* n_failed;       // [S] optional: +1 per evaluated candidate whose damped matrix is not
+                           //   positive definite (its cost is +inf)
   int32_t ks;              // lanes per candidate in the pass kernels (power of two <= 32)
   double lam;
+  double* out_cost;        // PH_SOLVE / PH_SOLVEG outputs: cost [Q], weights [Q][nmax+1] or
+  double* out_weights;     //   nullptr, gradient [Q][nmax] (PH_SOLVEG)
+  double* out_grad;
   Scratch sc;
   int* status;             // device status word
 };
@@ -76,6 +89,12 @@ struct EvalArgs {
 // ------------------------------------------------------------------ status word
 __device__ __forceinline__ void set_status(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
+}
+
+// Record the outcome of candidate q's factorisation (spectrum s).
+__device__ __forceinline__ void record_fail(const EvalArgs& a, int q, int s, bool ok) {
+  a.sc.fail[q] = ok ? 0 : 1;
+  if (!ok && a.n_failed) atomicAdd(&a.n_failed[s], 1);
 }
 
 // ------------------------------------------------------------------ float-float helpers

@@ -138,6 +138,65 @@ __device__ __forceinline__ void gram_unit(const EvalArgs& a, const Unit& u) {
 
 }
 
+// ------------------------------------------------------------------ Gram from FP64 column sums
+// The FP64 path's Gram G and h = A^T b by the partial-fraction identity of the Debye
+// columns (the mixed path's algebra, in plain FP64): the pass sums, per pole,
+//   S_i = sum_k re_i(k),   h_i = sum_k re_i(k) eps'_k + tau_i sum_k re_i(k) (omega_k eps''_k)
+// (im = omega tau re) with re = 1/(1 + omega^2 tau^2), and writes the packed Gram
+//   G_00 = K, G_i0 = G_ii = S_i, G_ij = (tau_i S_i + tau_j S_j) / (tau_i + tau_j)
+// in gram_unit's layout, so the FP64 solve, residual passes and finish follow unchanged
+// (the cost comes from the residual pass, free of the cancellation of b^T b - x^T h).
+template <int N>
+__device__ __forceinline__ void gram_sums_unit(const EvalArgs& a, const Unit& u) {
+  const Lane ln = lane_of(a, u, false);
+  const int q = ln.act ? ln.q : u.q0;
+  const double* th = a.theta + (int64_t)q * a.sc.nmax;
+  const int64_t Q = a.sc.Q;
+  const int64_t kbeg = u.k0 + ln.slice;
+  const int64_t kend = ln.act ? u.k1 : kbeg;
+  double tau[N], t2[N], sv[N], av[N], bv[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    tau[i] = ln.act ? exp10(th[i]) : 0.0;
+    t2[i] = tau[i] * tau[i];
+    sv[i] = av[i] = bv[i] = 0.0;
+  }
+#pragma unroll 1
+  for (int64_t k = kbeg; k < kend; k += ln.ks) {
+    const double w = __ldg(&a.omega[k]);
+    const double er = __ldg(&a.eps_re[k]);
+    const double wei = w * __ldg(&a.eps_im[k]);
+    const double w2 = w * w;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const double r = 1.0 / fma(w2, t2[i], 1.0);
+      sv[i] += r;
+      av[i] = fma(r, er, av[i]);
+      bv[i] = fma(r, wei, bv[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    sv[i] = group_sum(sv[i], ln.ks);
+    av[i] = group_sum(av[i], ln.ks);
+    bv[i] = group_sum(bv[i], ln.ks);
+  }
+  if (!(ln.act && ln.slice == 0)) return;
+  double* G = a.sc.G;
+  const int hb = (a.sc.nmax + 1) * (a.sc.nmax + 2) / 2;
+  G[(int64_t)pk(0, 0) * Q + q] = (double)(u.k1 - u.k0);
+  G[(int64_t)hb * Q + q] = a.h0[u.s];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    G[(int64_t)pk(i + 1, 0) * Q + q] = sv[i];
+    G[(int64_t)pk(i + 1, i + 1) * Q + q] = sv[i];
+    G[(int64_t)(hb + 1 + i) * Q + q] = av[i] + tau[i] * bv[i];
+#pragma unroll
+    for (int j = 0; j < i; ++j)
+      G[(int64_t)pk(i + 1, j + 1) * Q + q] = (tau[i] * sv[i] + tau[j] * sv[j]) / (tau[i] + tau[j]);
+  }
+}
+
 // ------------------------------------------------------------------ residual pass
 // Reads the weights x (FP64) of candidate q, writes rt[0] = ||b - A x||^2 and
 // rt[1 + j] = (A^T (b - A x))_j, j = 0..N.
@@ -427,6 +486,7 @@ __device__ __forceinline__ void grad_unit(const EvalArgs& a, const Unit& u) {
 template <int PH, int N>
 __device__ __forceinline__ void run_phase(const EvalArgs& a, const Unit& u) {
   if constexpr (PH == PH_GRAM) gram_unit<N>(a, u);
+  else if constexpr (PH == PH_GRAM_SUMS) gram_sums_unit<N>(a, u);
   else if constexpr (PH == PH_REFINE) refine_unit<N>(a, u);
   else if constexpr (PH == PH_SUMS) sums_sq_unit<N, false>(a, u);
   else if constexpr (PH == PH_SUMSG) sums_sq_unit<N, true>(a, u);

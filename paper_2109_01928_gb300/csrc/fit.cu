@@ -18,7 +18,9 @@ using namespace debyefit;
 
 namespace {
 
-constexpr int POLISH_R = 4;  // step lengths evaluated per line search round
+// Line search of the polish: the full step is evaluated first (with its gradient);
+// a line that rejects it evaluates POLISH_R further step lengths per backtracking round.
+constexpr int POLISH_R = 8;
 
 struct GraphGuard {
   cudaGraph_t g = nullptr;
@@ -85,7 +87,7 @@ int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, in
   if (Q > ((int64_t)1 << 31) - 1) return h->fail(DEBYE_EINVAL, "S*P exceeds 2^31-1");
   if ((rc = h->prep_spectra(sp, pl, st))) return rc;
   int cb, ks;
-  choose_layout(P, Q, h->sms, h->opt.cands_per_block, h->tuned_cb, &cb, &ks);
+  choose_layout(P, Q, h->sms, h->forced(), h->tuned, &cb, &ks);
   const bool mixed = h->opt.precision == DEBYE_PREC_MIXED;
   const int nmax = n_max;
 
@@ -165,6 +167,7 @@ int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, in
   ea.lam = h->opt.lam_search;
   ea.ks = ks;
   ea.status = h->d_status;
+  ea.n_failed = se->n_failed;
   const int steps = h->opt.refine_steps;
 
   // generation 0: initial positions (the same for both methods), evaluation, bests
@@ -259,9 +262,16 @@ int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, in
       ab[s] = (int32_t)(s * T);
       ae[s] = (int32_t)((s + 1) * T);
     }
-    int cbp, ksp, cba, ksa;
-    choose_layout((int64_t)T * pa.R, pl.S * T * pa.R, h->sms, h->opt.cands_per_block, h->tuned_cb, &cbp, &ksp);
-    choose_layout(T, pl.S * T, h->sms, h->opt.cands_per_block, h->tuned_cb, &cba, &ksa);
+    // trial steps: one work unit per line (its R step lengths), so that a unit whose line
+    // has stopped searching exits at once and an active one has no idle candidates
+    int cba, ksa;
+    const int cbp = pa.R, ksp = MAX_BLOCK / pa.R;
+    if (h->tuned_polish.cb > 0) {   // debye_autotune's choice for this shape
+      cba = h->tuned_polish.cb;
+      ksa = h->tuned_polish.ks;
+    } else {
+      choose_layout(T, pl.S * T, h->sms, h->forced(), h->tuned, &cba, &ksa);
+    }
     UnitGroups gp, ga;
     build_units(pl, pb, pe, cbp, gp);
     build_units(pl, ab, ae, cba, ga);
@@ -292,21 +302,25 @@ int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, in
       launch_add_scalar(se->evals, add, st); ++h->launches;
     }
     if ((rc = h->check_launch("polish start"))) return rc;
-    const int rounds = (pa.max_trials + pa.R - 1) / pa.R;
+    const int rounds = (pa.max_trials - 1 + pa.R - 1) / pa.R;
     rc = repeat(h, se->polish_iters, st, [&]() -> int {
       launch_polish_dir(pa, sp->n_poles, sp->lo, sp->hi, h->sms, st); ++h->launches;
-      for (int r = 0; r < rounds; ++r) {
-        // Armijo needs only costs: the trial steps are evaluated without gradients
-        int e = h->run_eval(ep, gp, mixed, h->eval_steps(false), pa.tcost, nullptr, nullptr, h->sb_polish.g1,
-                            cbp, st);
-        if (e) return e;
-        launch_polish_accept(pa, sp->n_poles, sp->lo, sp->hi, sp->offsets, h->sms, st); ++h->launches;
-      }
-      // cost and gradient at the accepted points, then the L-BFGS update
+      // the full step of every line, with its gradient (most lines accept it)
       int e = h->run_eval(eg, ga, mixed, h->eval_steps(true), pa.acost, nullptr, pa.agrad, h->sb_polish_acc.g1,
                           cba, st);
       if (e) return e;
-      launch_polish_take(pa, sp->n_poles, sp->offsets, h->sms, st); ++h->launches;
+      launch_polish_first(pa, sp->n_poles, sp->lo, sp->hi, sp->offsets, h->sms, st); ++h->launches;
+      for (int r = 0; r < rounds; ++r) {
+        // Armijo needs only costs: the backtracking steps are evaluated without gradients
+        e = h->run_eval(ep, gp, mixed, h->eval_steps(false), pa.tcost, nullptr, nullptr, h->sb_polish.g1, cbp, st);
+        if (e) return e;
+        launch_polish_accept(pa, sp->n_poles, sp->lo, sp->hi, sp->offsets, h->sms, st); ++h->launches;
+      }
+      // cost and gradient at the points accepted by backtracking, then the L-BFGS update
+      e = h->run_eval(eg, ga, mixed, h->eval_steps(true), pa.acost, nullptr, pa.agrad, h->sb_polish_acc.g1, cba,
+                      st);
+      if (e) return e;
+      launch_polish_take(pa, sp->n_poles, h->sms, st); ++h->launches;
       return h->check_launch("polish iteration");
     });
     if (rc) return rc;
@@ -327,7 +341,7 @@ int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, in
     fe[s] = (int32_t)(s + 1);
   }
   int cbf, ksf;
-  choose_layout(1, S, h->sms, 0, 0, &cbf, &ksf);
+  choose_layout(1, S, h->sms, Layout{}, Layout{}, &cbf, &ksf);
   UnitGroups gf;
   build_units(pl, fb, fe, cbf, gf);
   if ((rc = h->upload_units(gf, h->named_bufs["fin.units"], st))) return rc;

@@ -5,6 +5,7 @@
 
 #include "launch.h"
 #include "solve.cuh"
+#include "solve_sums.cuh"
 
 namespace debyefit {
 
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(256) k_solve(EvalArgs a) {
         ok = ok && isfinite(x0[i]);
       }
     }
-    a.sc.fail[q] = ok ? 0 : 1;
+    record_fail(a, q, u.s, ok);
     if (!ok) continue;
     const int npk = n * (n + 1) / 2;
     for (int e = 0; e < npk; ++e) Lg[(int64_t)e * Q + q] = L[e];
@@ -231,219 +232,6 @@ __global__ void __launch_bounds__(256) k_finish(EvalArgs a, int final_step, doub
     }
     if (weights) {
       for (int j = 0; j < nm1; ++j) weights[(int64_t)q * nm1 + j] = (j < n) ? x[j] + e[j] : 0.0;
-    }
-  }
-}
-
-// ------------------------------------------------------------------ cost from column sums (mixed)
-// For the Debye columns c_i = 1/(1 + j w tau_i), partial fractions give
-//   Re(c_i conj c_j) = (tau_i Re c_i + tau_j Re c_j) / (tau_i + tau_j),
-// so the pole block of the Gram follows from the column sums S_i = sum_k re_i(k):
-//   G_ij = (tau_i S_i + tau_j S_j) / (tau_i + tau_j),  G_ii = S_i  (re^2 + im^2 = re),
-// and G_0i = S_i, G_00 = K for the eps_inf column. With h = A^T b and b^T b, the
-// damped weights solve M x = h (M = G + lam diag G), and for the flipped x_hat
-//   cost(x_hat) = b^T b - 2 x_hat^T h + x_hat^T M x_hat
-// exactly. M, h, b^T b and the products with M are float-float (the subtraction
-// loses the digits of b^T b / cost, about 4: float-float keeps ~9 of the ~13
-// digits it carries); x comes from an FP32 Cholesky factor of the scaled M and
-// refinement steps with the float-float residual h - M x.
-constexpr int SUMS_REFINE = 2;       // refinement steps with the gradient (x and the adjoint w)
-// Cost-only evaluations take one step: the scaled damped matrix C + lam I has unit
-// diagonal, so kappa <= (n + lam) / lam (2e4 at n = 21, lam = 1e-3) and after one
-// step the weights carry about (kappa 2^-24)^2 = 1.4e-6 relative error, which
-// reaches a flipped candidate's cost at first order; two steps are ~2e-9.
-constexpr int SUMS_REFINE_COST = 1;
-
-__device__ __forceinline__ ff gram_ff(int i, int j, const ff* tau, const ff* S, ff kk) {
-  if (i == 0 && j == 0) return kk;
-  if (i == 0) return S[j - 1];
-  if (j == 0 || i == j) return S[i - 1];
-  const ff num = ff_sum(ff_prod(tau[i - 1], S[i - 1]), ff_prod(tau[j - 1], S[j - 1]));
-  return ff_quot(num, ff_sum(tau[i - 1], tau[j - 1]));
-}
-
-// (M v)_i in float-float, M = G + lam diag G. Every entry is formed where it is
-// used (once per product, serving both of its rows) rather than kept per
-// candidate: the kernel is bound by latency and local memory, not arithmetic.
-__device__ __forceinline__ void mvec_ff(int n, const ff* tau, const ff* S, ff kk, ff one_lam, const ff* v,
-                                        ff* out) {
-  for (int i = 0; i < n; ++i) out[i] = ff{0.f, 0.f};
-  for (int i = 0; i < n; ++i) {
-    for (int j = 0; j < i; ++j) {
-      const ff g = gram_ff(i, j, tau, S, kk);
-      out[i] = ff_sum(out[i], ff_prod(g, v[j]));
-      out[j] = ff_sum(out[j], ff_prod(g, v[i]));
-    }
-    out[i] = ff_sum(out[i], ff_prod(ff_prod(gram_ff(i, i, tau, S, kk), one_lam), v[i]));
-  }
-}
-
-// FP32 Cholesky L L^T of the scaled damped matrix, with 1 / L_jj stored on the
-// diagonal so that the solves multiply instead of dividing.
-__device__ __forceinline__ bool cholesky_rdiag(float* L, int n) {
-  for (int j = 0; j < n; ++j) {
-    float s = L[pk(j, j)];
-    for (int k = 0; k < j; ++k) s = __fmaf_rn(-L[pk(j, k)], L[pk(j, k)], s);
-    if (!(s > 0.f) || !isfinite(s)) return false;
-    const float inv = __frsqrt_rn(s);
-    L[pk(j, j)] = inv;
-    for (int i = j + 1; i < n; ++i) {
-      float v = L[pk(i, j)];
-      for (int k = 0; k < j; ++k) v = __fmaf_rn(-L[pk(i, k)], L[pk(j, k)], v);
-      L[pk(i, j)] = __fmul_rn(v, inv);
-    }
-  }
-  return true;
-}
-
-// v <- (L L^T)^-1 v for the factor of cholesky_rdiag
-__device__ __forceinline__ void llt_solve_rdiag(const float* L, float* v, int n) {
-  for (int i = 0; i < n; ++i) {
-    float s = v[i];
-    for (int k = 0; k < i; ++k) s = __fmaf_rn(-L[pk(i, k)], v[k], s);
-    v[i] = __fmul_rn(s, L[pk(i, i)]);
-  }
-  for (int i = n - 1; i >= 0; --i) {
-    float s = v[i];
-    for (int k = i + 1; k < n; ++k) s = __fmaf_rn(-L[pk(k, i)], v[k], s);
-    v[i] = __fmul_rn(s, L[pk(i, i)]);
-  }
-}
-
-// M^-1 rhs through the FP32 factor L of the scaled M (scaling dinv = diag(G)^-1/2),
-// refined `steps` times against the float-float M.
-__device__ __forceinline__ bool refined_solve(int n, const float* L, const float* dinv, const ff* tau, const ff* S,
-                                              ff kk, ff one_lam, const ff* rhs, ff* x, ff* r, float* v, int steps) {
-  bool ok = true;
-  for (int i = 0; i < n; ++i) x[i] = ff{0.f, 0.f};
-  for (int it = 0; it <= steps && ok; ++it) {
-    // r = rhs - M x (the first step has x = 0), dx = M^-1 r through the FP32 factor
-    if (it == 0) {
-      for (int i = 0; i < n; ++i) r[i] = rhs[i];
-    } else {
-      mvec_ff(n, tau, S, kk, one_lam, x, r);
-      for (int i = 0; i < n; ++i) r[i] = ff_sum(rhs[i], ff_neg(r[i]));
-    }
-    for (int i = 0; i < n; ++i) v[i] = __fmul_rn(r[i].h, dinv[i]);
-    llt_solve_rdiag(L, v, n);
-    for (int i = 0; i < n; ++i) {
-      x[i] = ff_sum(x[i], ff{__fmul_rn(v[i], dinv[i]), 0.f});
-      ok = ok && isfinite(x[i].h);
-    }
-  }
-  return ok;
-}
-
-// Cost (and, with grad, its derivative in theta) from the column sums. The
-// gradient of cost(x_hat) = b^T b - 2 x_hat^T h + x_hat^T M x_hat, x_hat = s * x*
-// (s the signs of the flip), x* = M^-1 h, is (variable projection with an
-// adjoint for the flip)
-//   d cost / d theta_i = -2 x_hat_i E_i + x_hat^T M_i x_hat + 2 (w_i E_i - w^T M_i x*),
-//   w = M^-1 (s * (M x_hat - h)),
-// with M_i = dM / d theta_i nonzero in row and column i only:
-//   (M_i)_{i0} = D_i,  (M_i)_{ii} = (1 + lam) D_i,
-//   (M_i)_{ij} = tau_i D_i / (tau_i + tau_j) + ln10 tau_i tau_j (S_i - S_j) / (tau_i + tau_j)^2
-// (the derivative of G_ij = (tau_i S_i + tau_j S_j)/(tau_i + tau_j), d tau_i = ln10 tau_i).
-__global__ void __launch_bounds__(256) k_solve_sums(EvalArgs a, double* cost, double* weights, double* grad) {
-  const int64_t Q = a.sc.Q;
-  const int nmax = a.sc.nmax, nm1 = nmax + 1;
-  for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
-    const Unit u = a.units[ui];
-    const int q = u.q0 + (int)threadIdx.x;
-    if (q >= u.q1 || (a.active && !a.active[q])) continue;
-    const int N = u.N, n = N + 1;
-    ff tau[NMAX], S[NMAX], hv[NMAX1], x[NMAX1], r[NMAX1];
-    float L[NPACK_MAX], dinv[NMAX1], v[NMAX1];
-    for (int i = 0; i < N; ++i) {
-      tau[i] = ff_of(a.sc.x[(int64_t)i * Q + q]);   // 10^theta_i from the column-sum pass
-      S[i] = ff_of(a.sc.G[(int64_t)i * Q + q]);
-      hv[i + 1] = ff_of(a.sc.G[(int64_t)(N + i) * Q + q]);
-    }
-    hv[0] = ff_of(a.h0[u.s]);
-    const ff kk = ff_of((double)(u.k1 - u.k0));
-    const ff one_lam = ff_of(1.0 + a.lam);
-    // FP32 Cholesky of the Marquardt-scaled damped matrix (unit diagonal + lam)
-    for (int i = 0; i < n; ++i) dinv[i] = __frsqrt_rn(gram_ff(i, i, tau, S, kk).h);   // diag(G)^-1/2
-    for (int i = 0; i < n; ++i) {
-      for (int j = 0; j < i; ++j) L[pk(i, j)] = __fmul_rn(__fmul_rn(gram_ff(i, j, tau, S, kk).h, dinv[i]), dinv[j]);
-      L[pk(i, i)] = (float)(1.0 + a.lam);
-    }
-    bool ok = cholesky_rdiag(L, n);
-    if (ok) ok = refined_solve(n, L, dinv, tau, S, kk, one_lam, hv, x, r, v, grad ? SUMS_REFINE : SUMS_REFINE_COST);
-    a.sc.fail[q] = ok ? 0 : 1;
-    if (!ok) {
-      if (cost) cost[q] = INFINITY;
-      if (weights)
-        for (int j = 0; j < nm1; ++j) weights[(int64_t)q * nm1 + j] = 0.0;
-      if (grad)
-        for (int j = 0; j < nmax; ++j) grad[(int64_t)q * nmax + j] = 0.0;
-      continue;
-    }
-    // sign flip of negative d_eps (Sec. III-B), then the exact quadratic cost
-    float sgn[NMAX1];
-    for (int i = 0; i < n; ++i) {
-      sgn[i] = (i > 0 && x[i].h < 0.f) ? -1.f : 1.f;
-      if (sgn[i] < 0.f) x[i] = ff_neg(x[i]);
-    }
-    mvec_ff(n, tau, S, kk, one_lam, x, r);   // r = M x_hat
-    ff c = ff_of(a.bb[u.s]);
-    for (int i = 0; i < n; ++i) {
-      c = ff_sum(c, ff_neg(ff_prod(ff{__fmul_rn(2.f, x[i].h), __fmul_rn(2.f, x[i].l)}, hv[i])));
-      c = ff_sum(c, ff_prod(x[i], r[i]));
-    }
-    double cv = ff_dbl(c);
-    if (!isfinite(cv)) cv = INFINITY;
-    if (cv < 0.0) cv = 0.0;
-    if (cost) cost[q] = cv;
-    if (weights)
-      for (int j = 0; j < nm1; ++j) weights[(int64_t)q * nm1 + j] = j < n ? ff_dbl(x[j]) : 0.0;
-    if (!grad) continue;
-    // adjoint w = M^-1 (s * (M x_hat - h)); r becomes its right-hand side
-    ff w[NMAX1], rw[NMAX1];
-    for (int i = 0; i < n; ++i) {
-      r[i] = ff_sum(r[i], ff_neg(hv[i]));
-      if (sgn[i] < 0.f) r[i] = ff_neg(r[i]);
-    }
-    if (!refined_solve(n, L, dinv, tau, S, kk, one_lam, r, w, rw, v, SUMS_REFINE)) {
-      for (int j = 0; j < nmax; ++j) grad[(int64_t)q * nmax + j] = 0.0;
-      continue;
-    }
-    const ff ln10 = ff_of(2.302585092994046);
-    for (int i = 0; i < nmax; ++i) {
-      if (i >= N) {
-        grad[(int64_t)q * nmax + i] = 0.0;
-        continue;
-      }
-      const int I = i + 1;
-      const ff Di = ff_of(a.sc.G[(int64_t)(2 * N + i) * Q + q]);
-      const ff Ei = ff_of(a.sc.G[(int64_t)(3 * N + i) * Q + q]);
-      // row i of M_i against x_hat, w and x* (x*_j = s_j x_hat_j), off the diagonal
-      ff ax = ff_prod(Di, x[0]), aw = ff_prod(Di, w[0]), as = ax;
-      for (int j = 0; j < N; ++j) {
-        if (j == i) continue;
-        const ff rr = ff_quot(ff{1.f, 0.f}, ff_sum(tau[i], tau[j]));
-        const ff t1 = ff_prod(ff_prod(tau[i], Di), rr);
-        const ff t2 = ff_prod(ff_prod(ff_prod(ln10, ff_prod(tau[i], tau[j])), ff_sum(S[i], ff_neg(S[j]))),
-                              ff_prod(rr, rr));
-        const ff row = ff_sum(t1, t2);
-        const ff xs = sgn[j + 1] < 0.f ? ff_neg(x[j + 1]) : x[j + 1];
-        ax = ff_sum(ax, ff_prod(row, x[j + 1]));
-        aw = ff_sum(aw, ff_prod(row, w[j + 1]));
-        as = ff_sum(as, ff_prod(row, xs));
-      }
-      const ff diag = ff_prod(Di, one_lam);
-      const ff xhI = x[I], wI = w[I];
-      const ff xsI = sgn[I] < 0.f ? ff_neg(xhI) : xhI;
-      // x_hat^T M_i x_hat = 2 x_hat_i ax + diag x_hat_i^2;  w^T M_i x* = w_i as + x*_i aw + diag w_i x*_i
-      ff gsum = ff_neg(ff_prod(ff{__fmul_rn(2.f, xhI.h), __fmul_rn(2.f, xhI.l)}, Ei));
-      gsum = ff_sum(gsum, ff_prod(ff{__fmul_rn(2.f, xhI.h), __fmul_rn(2.f, xhI.l)}, ax));
-      gsum = ff_sum(gsum, ff_prod(diag, ff_prod(xhI, xhI)));
-      ff adj = ff_prod(wI, Ei);
-      adj = ff_sum(adj, ff_neg(ff_prod(wI, as)));
-      adj = ff_sum(adj, ff_neg(ff_prod(xsI, aw)));
-      adj = ff_sum(adj, ff_neg(ff_prod(diag, ff_prod(wI, xsI))));
-      gsum = ff_sum(gsum, ff{__fmul_rn(2.f, adj.h), __fmul_rn(2.f, adj.l)});
-      grad[(int64_t)q * nmax + i] = ff_dbl(gsum);
     }
   }
 }
@@ -616,7 +404,7 @@ __global__ void __launch_bounds__(WARP_SOLVE_MAX_WARPS * 32) k_solve_sums_warp(E
       bool ok = warp_cholesky(m, n1, n, r);
       ff x{0.f, 0.f};
       if (ok) ok = warp_refined_solve(m, n1, n, r, hv, x, grad ? SUMS_REFINE : SUMS_REFINE_COST);
-      if (r == 0) a.sc.fail[q] = ok ? 0 : 1;
+      if (r == 0) record_fail(a, q, u.s, ok);
       if (!ok) {
         if (cost && r == 0) cost[q] = INFINITY;
         if (weights && r < nm1) weights[(int64_t)q * nm1 + r] = 0.0;
@@ -794,7 +582,7 @@ static int grid_for(int n_units, int sms, int per_sm) {
 // 32 blocks per SM keeps enough warps resident to hide that memory's latency.
 void launch_solve_sums(const EvalArgs& a, double* cost, double* weights, double* grad, int block, int sms,
                        cudaStream_t st) {
-  if (a.n_units) k_solve_sums<<<grid_for(a.n_units, sms, 32), block, 0, st>>>(a, cost, weights, grad);
+  if (a.n_units) k_solve_sums_t<0, -1><<<grid_for(a.n_units, sms, 32), block, 0, st>>>(a, cost, weights, grad);
 }
 
 bool solve_sums_by_warp(int64_t Q, int lanes, int sms) {

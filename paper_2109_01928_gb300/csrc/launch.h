@@ -14,26 +14,30 @@ constexpr int N_BUCKETS = NMAX;
 constexpr int MAX_BLOCK = 128; // largest pass block (candidates x lanes)
 __host__ __device__ constexpr int bucket_of(int N) { return N - 1; }
 
+// A work layout: candidates per unit (cb) and lanes per candidate (ks); 0 = unset.
+struct Layout {
+  int cb = 0, ks = 0;
+};
+
 // Work layout for spectra with `per_spectrum` candidates each, `total` in the
 // batch: `cb` candidates per unit and `ks` lanes per candidate. A population
-// that fills the GPU (about 2048 resident threads per SM) gets one lane per
-// candidate, `tuned` (debye_autotune's choice, 0 = 64) candidates per unit; a
-// smaller batch (the polish's trial steps and accepted points, the final
-// re-solve, small fits) splits each candidate over ks = 2..32 lanes, sized so
-// that the batch fills the GPU and a 64-thread block holds candidates of one
-// spectrum. `forced` > 0 (the caller's cands_per_block) fixes cb with one lane
-// per candidate whenever a spectrum has at least a warp of candidates.
-inline void choose_layout(int64_t per_spectrum, int64_t total, int sms, int forced, int tuned, int* cb,
+// that fills the GPU (about 2048 resident threads per SM) is a full population:
+// `tuned` (debye_autotune's choice; unset: 64 candidates, one lane each), with
+// `forced` (the caller's cands_per_block / lanes_per_candidate options) taking
+// precedence field by field; a forced block size alone means one lane per
+// candidate, and cb is cut so that cb x ks <= MAX_BLOCK. A forced block size also
+// makes any batch with at least a warp of candidates per spectrum a full
+// population. A smaller batch (the polish's accepted points, the final re-solve,
+// small fits) splits each candidate over ks = 2..32 lanes, sized so that the batch
+// fills the GPU and a 64-thread block holds candidates of one spectrum.
+inline void choose_layout(int64_t per_spectrum, int64_t total, int sms, Layout forced, Layout tuned, int* cb,
                           int* ks) {
   const int64_t target = (int64_t)std::max(sms, 1) * 2048;
-  if (forced > 0 && per_spectrum >= 32) {
-    *cb = forced;
-    *ks = 1;
-    return;
-  }
-  if (per_spectrum >= 32 && 2 * total >= target) {
-    *cb = tuned > 0 ? tuned : 64;
-    *ks = 1;
+  if (per_spectrum >= 32 && (forced.cb > 0 || 2 * total >= target)) {
+    int c = forced.cb > 0 ? forced.cb : (tuned.cb > 0 ? tuned.cb : 64);
+    int k = forced.ks > 0 ? forced.ks : (forced.cb > 0 ? 1 : (tuned.ks > 0 ? tuned.ks : 1));
+    *ks = k;
+    *cb = std::max(1, std::min(c, MAX_BLOCK / k));
     return;
   }
   int p2 = 1;

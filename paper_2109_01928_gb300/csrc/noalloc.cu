@@ -144,8 +144,8 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
   debye_options opt;
   if (opt_in) opt = *opt_in;
   else debye_default_options(&opt);
-  if (opt.precision != DEBYE_PREC_FP64 && opt.precision != DEBYE_PREC_MIXED)
-    return fail_msg(DEBYE_EINVAL, err, err_len, "precision must be DEBYE_PREC_FP64 or DEBYE_PREC_MIXED");
+  if (opt.precision != DEBYE_PREC_FP64 && opt.precision != DEBYE_PREC_MIXED && opt.precision != DEBYE_PREC_FP64_SUMS)
+    return fail_msg(DEBYE_EINVAL, err, err_len, "precision must be DEBYE_PREC_FP64, _MIXED or _FP64_SUMS");
   if (opt.refine_steps < 1 || opt.refine_steps > 4 || !(opt.lam_search >= 0.0))
     return fail_msg(DEBYE_EINVAL, err, err_len, "refine_steps outside 1..4 or negative lam_search");
   if (!sp) return fail_msg(DEBYE_EINVAL, err, err_len, "spectra is NULL");
@@ -164,16 +164,23 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
   // the carving below): 8 B per candidate and 16 B per spectrum at the very least.
   if (Q > (int64_t)(SCRATCH_BYTES / sizeof(double)) || S > (int64_t)(SCRATCH_BYTES / (2 * sizeof(double))))
     return fail_msg(DEBYE_EINVAL, err, err_len, "batch needs more than the allocation-free scratch");
-  if (opt.cands_per_block != 0 &&
-      (opt.cands_per_block < 32 || opt.cands_per_block > MAX_BLOCK || opt.cands_per_block % 32))
-    return fail_msg(DEBYE_EINVAL, err, err_len, "cands_per_block");
+  if (opt.lanes_per_candidate != 0 && (opt.lanes_per_candidate < 1 || opt.lanes_per_candidate > 32 ||
+                                       (opt.lanes_per_candidate & (opt.lanes_per_candidate - 1))))
+    return fail_msg(DEBYE_EINVAL, err, err_len, "lanes_per_candidate");
+  {
+    const int blk = opt.cands_per_block * std::max(opt.lanes_per_candidate, 1);
+    if (opt.cands_per_block < 0 || (opt.cands_per_block && (blk > MAX_BLOCK || blk % 32)))
+      return fail_msg(DEBYE_EINVAL, err, err_len,
+                      "cands_per_block x lanes_per_candidate must be a multiple of 32, at most 128");
+  }
   int cb, ks;
   int sms_l = 1, dev_l = 0;
   cudaGetDevice(&dev_l);
   cudaDeviceGetAttribute(&sms_l, cudaDevAttrMultiProcessorCount, dev_l);
   // one lane per candidate for populations of a warp or more (as large batches get), so
   // the number of work units stays small
-  choose_layout(P, (int64_t)1 << 40, sms_l, opt.cands_per_block, 0, &cb, &ks);
+  choose_layout(P, (int64_t)1 << 40, sms_l, Layout{opt.cands_per_block, opt.lanes_per_candidate}, Layout{}, &cb,
+                &ks);
   const int64_t* offs = sp->offsets_host;
   if (offs[0] != 0) return fail_msg(DEBYE_EINVAL, err, err_len, "offsets[0] must be 0");
 
@@ -290,7 +297,7 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
     per_bucket(PH_SUMS);
     launch_solve_sums(a, cost, weights, nullptr, warp_round(cb), sms, st);
   } else {
-    per_bucket(PH_GRAM);
+    per_bucket(opt.precision == DEBYE_PREC_FP64_SUMS ? PH_GRAM_SUMS : PH_GRAM);
     launch_solve(a, warp_round(cb), sms, st);
     for (int it = 0; it < opt.refine_steps; ++it) {
       per_bucket(PH_REFINE);

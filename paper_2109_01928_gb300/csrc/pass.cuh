@@ -2,10 +2,12 @@
 #pragma once
 #include "eval.cuh"
 #include "launch.h"
+#include "solve_sums.cuh"
 
 namespace debyefit {
 
-// The column-sum passes (PH_SUMS, PH_SUMSG) are the mixed-precision path; the
+// The column-sum passes (PH_SUMS, PH_SUMSG) and the per-N column-sum solves
+// (PH_SOLVE, PH_SOLVEG, N <= SOLVE_N_MAX) are the mixed-precision path; the
 // Gram, residual and gradient passes the FP64 path.
 template <int N>
 void launch_pass_n(int phase, const EvalArgs& a, int grid, int block, cudaStream_t st) {
@@ -19,7 +21,16 @@ void launch_pass_n(int phase, const EvalArgs& a, int grid, int block, cudaStream
     case PH_SUMS: k_pass<PH_SUMS, N, N, MAXT, MB_SUMS><<<grid, block, 0, st>>>(a); break;
     case PH_SUMSG: k_pass<PH_SUMSG, N, N, MAXT, 1><<<grid, block, 0, st>>>(a); break;
     case PH_GRAM: k_pass<PH_GRAM, N, N, MAXT, 1><<<grid, block, 0, st>>>(a); break;
+    case PH_GRAM_SUMS: k_pass<PH_GRAM_SUMS, N, N, MAXT, 1><<<grid, block, 0, st>>>(a); break;
     case PH_REFINE: k_pass<PH_REFINE, N, N, MAXT, 1><<<grid, block, 0, st>>>(a); break;
+    case PH_SOLVE:
+    case PH_SOLVEG:
+      if constexpr (N <= SOLVE_N_MAX) {   // one thread per candidate (block = candidates per unit)
+        const size_t smem = solve_smem_per_thread(N) * block;   // <= 46.6 KB (N = 12, 128 threads)
+        if (phase == PH_SOLVE) k_solve_sums_t<N, 0><<<grid, block, smem, st>>>(a, a.out_cost, a.out_weights, nullptr);
+        else k_solve_sums_t<N, 1><<<grid, block, smem, st>>>(a, a.out_cost, a.out_weights, a.out_grad);
+      }
+      break;
     default: k_pass<PH_GRAD, N, N, MAXT, 1><<<grid, block, 0, st>>>(a); break;
   }
 }

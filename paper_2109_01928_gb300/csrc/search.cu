@@ -455,8 +455,40 @@ __global__ void k_polish_dir(PolishArgs pa, const int32_t* n_poles, const double
     } else {
       for (int d = 0; d < N; ++d) dir[d] = -q[d];
     }
-    pa.t0[l] = 0;
-    write_trials(pa, l, N, lo_[s], hi_[s]);
+    // the full step t = 0 is evaluated first, with its gradient, in the accepted-point slot;
+    // the backtracking rounds start at t = 1 if it fails
+    for (int d = 0; d < nmax; ++d) {
+      double v = 0.0;
+      if (d < N) v = fmin(fmax(pa.th[l * nmax + d] + dir[d], lo_[s]), hi_[s]);
+      pa.ath[l * nmax + d] = v;
+    }
+    pa.aactive[l] = 1;
+    pa.t0[l] = 1;
+  }
+}
+
+// Armijo test of the full step (evaluated with its gradient in the accepted-point
+// slot): accepted, the line's cost and gradient are ready for the update; rejected,
+// the backtracking trials t = 1 .. R of the first round are written.
+__global__ void k_polish_first(PolishArgs pa, const int32_t* n_poles, const double* lo_, const double* hi_,
+                               const int64_t* offsets) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < pa.L;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    if (!pa.aactive[l]) continue;
+    pa.aactive[l] = 0;
+    const int64_t s = l / pa.T;
+    const int N = n_poles[s];
+    const int nmax = pa.nmax;
+    if (pa.evals) atomicAdd(pa.evals, (double)(offsets[s + 1] - offsets[s]));
+    double gs = 0.0;
+    for (int d = 0; d < N; ++d) gs = fma(pa.g[l * nmax + d], pa.ath[l * nmax + d] - pa.th[l * nmax + d], gs);
+    if (pa.acost[l] <= pa.f[l] + pa.c1 * gs) {
+      pa.acc[l] = 1;
+    } else if (pa.t0[l] >= pa.max_trials) {
+      pa.done[l] = 1;
+    } else {
+      write_trials(pa, l, N, lo_[s], hi_[s]);
+    }
   }
 }
 
@@ -481,7 +513,10 @@ __global__ void k_polish_accept(PolishArgs pa, const int32_t* n_poles, const dou
         gs = fma(pa.g[l * nmax + d], pa.tth[q * nmax + d] - pa.th[l * nmax + d], gs);
       if (pa.tcost[q] <= pa.f[l] + pa.c1 * gs) hit = t;
     }
-    if (pa.evals && n_active) atomicAdd(pa.evals, (double)n_active * (double)(offsets[s + 1] - offsets[s]));
+    // the trials a sequential backtracking search evaluates: up to and including the first
+    // acceptable one (the speculative trials after it are not counted)
+    const int counted = hit >= 0 ? hit + 1 : n_active;
+    if (pa.evals && counted) atomicAdd(pa.evals, (double)counted * (double)(offsets[s + 1] - offsets[s]));
     for (int t = 0; t < pa.R; ++t) pa.active[l * pa.R + t] = 0;
     if (hit >= 0) {
       const int64_t q = l * pa.R + hit;
@@ -498,15 +533,14 @@ __global__ void k_polish_accept(PolishArgs pa, const int32_t* n_poles, const dou
 
 // L-BFGS update with the accepted point's cost and gradient: history pair
 // (s, y) kept only when s^T y > eps y^T y (oldest pair dropped when full).
-__global__ void k_polish_take(PolishArgs pa, const int32_t* n_poles, const int64_t* offsets) {
+__global__ void k_polish_take(PolishArgs pa, const int32_t* n_poles) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < pa.L;
        l += (int64_t)gridDim.x * blockDim.x) {
-    if (!pa.aactive[l]) continue;
+    if (!pa.acc[l]) continue;
     pa.aactive[l] = 0;
     const int64_t s = l / pa.T;
     const int N = n_poles[s];
     const int nmax = pa.nmax, m = pa.m;
-    if (pa.evals) atomicAdd(pa.evals, (double)(offsets[s + 1] - offsets[s]));
     double sv[NMAX], yv[NMAX];
     for (int d = 0; d < N; ++d) {
       sv[d] = pa.ath[l * nmax + d] - pa.th[l * nmax + d];
@@ -634,13 +668,16 @@ void launch_polish_dir(const PolishArgs& pa, const int32_t* n_poles, const doubl
                        int sms, cudaStream_t st) {
   k_polish_dir<<<g1d(pa.L, sms), 128, 0, st>>>(pa, n_poles, lo, hi);
 }
+void launch_polish_first(const PolishArgs& pa, const int32_t* n_poles, const double* lo, const double* hi,
+                         const int64_t* offsets, int sms, cudaStream_t st) {
+  k_polish_first<<<g1d(pa.L, sms), 128, 0, st>>>(pa, n_poles, lo, hi, offsets);
+}
 void launch_polish_accept(const PolishArgs& pa, const int32_t* n_poles, const double* lo, const double* hi,
                           const int64_t* offsets, int sms, cudaStream_t st) {
   k_polish_accept<<<g1d(pa.L, sms), 128, 0, st>>>(pa, n_poles, lo, hi, offsets);
 }
-void launch_polish_take(const PolishArgs& pa, const int32_t* n_poles, const int64_t* offsets, int sms,
-                        cudaStream_t st) {
-  k_polish_take<<<g1d(pa.L, sms), 128, 0, st>>>(pa, n_poles, offsets);
+void launch_polish_take(const PolishArgs& pa, const int32_t* n_poles, int sms, cudaStream_t st) {
+  k_polish_take<<<g1d(pa.L, sms), 128, 0, st>>>(pa, n_poles);
 }
 void launch_pick_best(const SwarmArgs& a, const PolishArgs& pa, double* out_theta, int sms, cudaStream_t st) {
   k_pick_best<<<g1d(a.S, sms), 256, 0, st>>>(a, pa, out_theta);

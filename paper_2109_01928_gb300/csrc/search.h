@@ -33,7 +33,7 @@ struct SwarmArgs {
 struct PolishArgs {
   int64_t L;       // lines = S * T
   int32_t T;       // lines per spectrum
-  int32_t R;       // trial step lengths evaluated per round
+  int32_t R;       // trial step lengths per backtracking round (after the full step)
   int32_t nmax, m, max_trials;
   double c1;
   double* th;      // [L][nmax] current point
@@ -43,9 +43,9 @@ struct PolishArgs {
   double* hs;      // [L][m][nmax] history s (oldest first)
   double* hy;      // [L][m][nmax] history y
   int32_t* hcount; // [L]
-  int32_t* t0;     // [L] first trial index of the current round
+  int32_t* t0;     // [L] first trial index of the next backtracking round
   int32_t* done;   // [L] line finished (no acceptable step or non-finite)
-  int32_t* acc;    // [L] step accepted in this iteration
+  int32_t* acc;    // [L] step accepted in this iteration (acost, agrad at ath ready after the last evaluation)
   double* tth;     // [L*R][nmax] trial points
   double* tcost;   // [L*R]
   uint8_t* active; // [L*R] trial needs evaluation
@@ -53,7 +53,7 @@ struct PolishArgs {
   double* ath;     // [L][nmax] accepted point
   double* acost;   // [L]
   double* agrad;   // [L][nmax]
-  uint8_t* aactive;// [L] line has an accepted point to take
+  uint8_t* aactive;// [L] ath needs a cost + gradient evaluation (the full step, or a later accepted trial)
   double* evals;   // [1] or nullptr
 };
 
@@ -72,10 +72,11 @@ void launch_polish_start(const PolishArgs& pa, int sms, cudaStream_t st);
 void launch_polish_take0(const PolishArgs& pa, int sms, cudaStream_t st);
 void launch_polish_dir(const PolishArgs& pa, const int32_t* n_poles, const double* lo, const double* hi,
                        int sms, cudaStream_t st);
+void launch_polish_first(const PolishArgs& pa, const int32_t* n_poles, const double* lo, const double* hi,
+                         const int64_t* offsets, int sms, cudaStream_t st);
 void launch_polish_accept(const PolishArgs& pa, const int32_t* n_poles, const double* lo, const double* hi,
                           const int64_t* offsets, int sms, cudaStream_t st);
-void launch_polish_take(const PolishArgs& pa, const int32_t* n_poles, const int64_t* offsets, int sms,
-                        cudaStream_t st);
+void launch_polish_take(const PolishArgs& pa, const int32_t* n_poles, int sms, cudaStream_t st);
 void launch_pick_best(const SwarmArgs& a, const PolishArgs& pa, double* out_theta, int sms, cudaStream_t st);
 void launch_assemble(int64_t S, int nmax, const int32_t* n_poles, const double* theta, const double* weights,
                      const double* cost, double* eps_inf, double* d_eps, double* tau, double* final_cost,

@@ -27,6 +27,8 @@ DEBYE_ENOTFINITE = -6
 DEBYE_EBOUNDS = -7
 PREC_FP64 = 0
 PREC_MIXED = 1
+PREC_FP64_SUMS = 2
+PRECISIONS = {"mixed": PREC_MIXED, "fp64": PREC_FP64, "fp64_sums": PREC_FP64_SUMS}
 SEARCH_PSO = 0
 SEARCH_DE = 1
 SEARCH_DA = 2
@@ -51,7 +53,7 @@ class Options(ctypes.Structure):
                 ("cands_per_block", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
                 ("de_f_lo", ctypes.c_double), ("de_f_hi", ctypes.c_double), ("de_cr", ctypes.c_double),
                 ("de_strategy", ctypes.c_int32), ("da_t0", ctypes.c_double), ("da_qa", ctypes.c_double),
-                ("solve_lanes", ctypes.c_int32)]
+                ("solve_lanes", ctypes.c_int32), ("lanes_per_candidate", ctypes.c_int32)]
 
 
 class SpectraC(ctypes.Structure):
@@ -64,7 +66,8 @@ class SpectraC(ctypes.Structure):
 class SearchC(ctypes.Structure):
     _fields_ = [("P", ctypes.c_int32), ("iters", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("polish_topk", ctypes.c_int32), ("polish_iters", ctypes.c_int32),
-                ("trace", ctypes.c_void_p), ("evals", ctypes.c_void_p), ("method", ctypes.c_int32)]
+                ("trace", ctypes.c_void_p), ("evals", ctypes.c_void_p), ("method", ctypes.c_int32),
+                ("n_failed", ctypes.c_void_p)]
 
 
 _lib = None
@@ -86,9 +89,9 @@ def lib() -> ctypes.CDLL:
     L.debye_fit_destroy.argtypes = [_VP]
     L.debye_synth_targets.argtypes = [_VP, ctypes.c_int64] + [_VP] * 11 + [_VP]
     L.debye_eval_population.argtypes = [_VP, ctypes.POINTER(SpectraC), ctypes.c_int32, ctypes.c_int32,
-                                        _VP, _VP, _VP, _VP]
+                                        _VP, _VP, _VP, _VP, _VP]
     L.debye_cost_grad.argtypes = [_VP, ctypes.POINTER(SpectraC), ctypes.c_int32, ctypes.c_int32,
-                                  _VP, _VP, _VP, _VP]
+                                  _VP, _VP, _VP, _VP, _VP]
     L.debye_fit_batch.argtypes = [_VP, ctypes.POINTER(SpectraC), ctypes.POINTER(SearchC), ctypes.c_int32,
                                   _VP, _VP, _VP, _VP, _VP]
     L.debye_fit_auto.argtypes = [_VP, ctypes.POINTER(SpectraC), ctypes.POINTER(SearchC), ctypes.c_int32,
@@ -100,7 +103,7 @@ def lib() -> ctypes.CDLL:
     L.debye_profile_enable.argtypes = [_VP, ctypes.c_int32]
     L.debye_launch_count.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]
     L.debye_autotune.argtypes = [_VP, ctypes.POINTER(SpectraC), ctypes.c_int32, ctypes.c_int32, _VP, _VP,
-                                 ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32), _VP]
+                                 ctypes.c_char_p, _VP, _VP]
     L.debye_eval_population_noalloc.argtypes = [ctypes.POINTER(Options), ctypes.POINTER(SpectraC),
                                                 ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP,
                                                 ctypes.c_char_p, ctypes.c_int32, _VP]
@@ -146,11 +149,11 @@ def default_options() -> Options:
 
 
 class Handle:
-    """debye_handle with its options (precision 'mixed' or 'fp64')."""
+    """debye_handle with its options (precision 'mixed', 'fp64' or 'fp64_sums')."""
 
     def __init__(self, precision: str = "mixed", **opts):
         o = default_options()
-        o.precision = {"mixed": PREC_MIXED, "fp64": PREC_FP64}[precision]
+        o.precision = PRECISIONS[precision]
         for k, v in opts.items():
             setattr(o, k, v)
         self.options = o
@@ -240,8 +243,10 @@ def debye_synth_targets(h: Handle, offsets, omega, model, params, pole_offsets=N
 
 
 def debye_eval_population(h: Handle, sp: Spectra, theta, weights: bool = False, n_max: int | None = None,
-                          cost=None, weights_out=None, stream=None):
-    """Cost [S, P] (and weights [S, P, n_max+1]) of the population theta [S, P, n_max]."""
+                          cost=None, weights_out=None, n_failed=None, stream=None):
+    """Cost [S, P] (and weights [S, P, n_max+1]) of the population theta [S, P, n_max].
+    n_failed: optional int32 [S] device tensor, incremented per candidate whose damped
+    matrix is not positive definite."""
     import torch
     S, P, nm = theta.shape
     n_max = _check_n_max(theta, n_max)
@@ -252,12 +257,12 @@ def debye_eval_population(h: Handle, sp: Spectra, theta, weights: bool = False, 
         weights_out = torch.empty((S, P, n_max + 1), dtype=torch.float64, device=theta.device)
     c = sp.c()
     h.check(lib().debye_eval_population(h.ptr, ctypes.byref(c), P, n_max, _ptr(theta), _ptr(cost),
-                                        _ptr(weights_out) if weights else None, _stream(stream)))
+                                        _ptr(weights_out) if weights else None, _ptr(n_failed), _stream(stream)))
     return (cost, weights_out) if weights else cost
 
 
-def debye_cost_grad(h: Handle, sp: Spectra, theta, cost=None, grad=None, stream=None):
-    """Cost [S, P] and d cost / d theta [S, P, n_max]."""
+def debye_cost_grad(h: Handle, sp: Spectra, theta, cost=None, grad=None, n_failed=None, stream=None):
+    """Cost [S, P] and d cost / d theta [S, P, n_max] (n_failed as for debye_eval_population)."""
     import torch
     S, P, nm = theta.shape
     if cost is None:
@@ -266,15 +271,16 @@ def debye_cost_grad(h: Handle, sp: Spectra, theta, cost=None, grad=None, stream=
         grad = torch.empty_like(theta)
     c = sp.c()
     h.check(lib().debye_cost_grad(h.ptr, ctypes.byref(c), P, nm, _ptr(theta), _ptr(cost), _ptr(grad),
-                                  _stream(stream)))
+                                  _ptr(n_failed), _stream(stream)))
     return cost, grad
 
 
 def debye_fit_batch(h: Handle, sp: Spectra, P: int, iters: int, seed: int = 0, polish_topk: int = 8,
                     polish_iters: int = 50, n_max: int | None = None, trace: bool = False, stream=None,
-                    out=None, method: str = "pso"):
+                    out=None, method: str = "pso", n_failed: bool = False):
     """Whole fit of every spectrum: dict of eps_inf [S], d_eps [S, n_max], tau [S, n_max],
-    final_cost [S], evals (candidate evaluations x K) and optionally trace [S, iters+1].
+    final_cost [S], evals (candidate evaluations x K), optionally trace [S, iters+1] and
+    n_failed [S] (int32: candidates whose damped matrix was not positive definite).
     method: "pso" (particle swarm), "de" (differential evolution) or "da" (dual annealing)."""
     import torch
     dev = sp.omega.device
@@ -288,8 +294,12 @@ def debye_fit_batch(h: Handle, sp: Spectra, P: int, iters: int, seed: int = 0, p
                "evals": torch.zeros(1, dtype=torch.float64, device=dev)}
         if trace:
             out["trace"] = torch.empty((S, iters + 1), dtype=torch.float64, device=dev)
+        if n_failed:
+            out["n_failed"] = torch.zeros(S, dtype=torch.int32, device=dev)
+    elif "n_failed" in out:
+        out["n_failed"].zero_()
     srch = SearchC(P, iters, seed, polish_topk, polish_iters, _ptr(out.get("trace")), _ptr(out["evals"]),
-                   {"pso": SEARCH_PSO, "de": SEARCH_DE, "da": SEARCH_DA}[method])
+                   {"pso": SEARCH_PSO, "de": SEARCH_DE, "da": SEARCH_DA}[method], _ptr(out.get("n_failed")))
     c = sp.c()
     h.check(lib().debye_fit_batch(h.ptr, ctypes.byref(c), ctypes.byref(srch), n_max, _ptr(out["eps_inf"]),
                                   _ptr(out["d_eps"]), _ptr(out["tau"]), _ptr(out["final_cost"]),
@@ -312,7 +322,7 @@ def debye_fit_auto(h: Handle, sp: Spectra, P: int, iters: int, seed: int = 0, po
            "frac_err": torch.empty(S, **f64), "n_chosen": torch.empty(S, dtype=torch.int32, device=dev),
            "evals": torch.zeros(1, **f64)}
     srch = SearchC(P, iters, seed, polish_topk, polish_iters, None, _ptr(out["evals"]),
-                   {"pso": SEARCH_PSO, "de": SEARCH_DE, "da": SEARCH_DA}[method])
+                   {"pso": SEARCH_PSO, "de": SEARCH_DE, "da": SEARCH_DA}[method], None)
     c = sp.c()
     h.check(lib().debye_fit_auto(h.ptr, ctypes.byref(c), ctypes.byref(srch), n_max, float(threshold), wave,
                                  _ptr(out["eps_inf"]), _ptr(out["d_eps"]), _ptr(out["tau"]),
@@ -338,7 +348,7 @@ def debye_eval_population_noalloc(sp: Spectra, theta, precision: str = "mixed", 
     S, P, nm = theta.shape
     n_max = _check_n_max(theta, n_max)
     o = options if options is not None else default_options()
-    o.precision = {"mixed": PREC_MIXED, "fp64": PREC_FP64}[precision]
+    o.precision = PRECISIONS[precision]
     if cost is None:
         cost = torch.empty((S, P), dtype=torch.float64, device=theta.device)
     if weights and weights_out is None:
@@ -353,17 +363,19 @@ def debye_eval_population_noalloc(sp: Spectra, theta, precision: str = "mixed", 
     return (cost, weights_out) if weights else cost
 
 
-def debye_autotune(h: Handle, sp: Spectra, theta, cache_path: str | None = None, stream=None) -> int:
-    """Time the candidates-per-block choices on this batch and keep the fastest for h."""
+def debye_autotune(h: Handle, sp: Spectra, theta, cache_path: str | None = None, stream=None) -> dict:
+    """Time the work layouts on this batch and keep the fastest for h: returns
+    {"cands_per_block", "lanes_per_candidate"} of full populations and
+    {"polish_cands_per_block", "polish_lanes_per_candidate"} of the polish's accepted points."""
     import torch
     S, P, nm = theta.shape
     cost = torch.empty((S, P), dtype=torch.float64, device=theta.device)
-    chosen = ctypes.c_int32(0)
+    chosen = (ctypes.c_int32 * 4)()
     c = sp.c()
     h.check(lib().debye_autotune(h.ptr, ctypes.byref(c), P, nm, _ptr(theta), _ptr(cost),
-                                 cache_path.encode() if cache_path else None, ctypes.byref(chosen),
-                                 _stream(stream)))
-    return chosen.value
+                                 cache_path.encode() if cache_path else None, chosen, _stream(stream)))
+    return {"cands_per_block": chosen[0], "lanes_per_candidate": chosen[1],
+            "polish_cands_per_block": chosen[2], "polish_lanes_per_candidate": chosen[3]}
 
 
 def debye_launch_count(h: Handle, reset: bool = False) -> int:

@@ -44,11 +44,13 @@ def test_init_rejects_bad_options(lib):
     o.refine_steps = 0
     h = ctypes.c_void_p()
     assert lib.debye_fit_init(ctypes.byref(h), ctypes.byref(o)) == D.DEBYE_EINVAL
-    o = D.default_options()
-    o.cands_per_block = 48
-    assert lib.debye_fit_init(ctypes.byref(h), ctypes.byref(o)) == D.DEBYE_EINVAL
+    for cb, lanes in ((48, 0), (129, 0), (16, 1), (64, 4), (3, 8)):   # not whole warps, or > 128 threads
+        o = D.default_options()
+        o.cands_per_block, o.lanes_per_candidate = cb, lanes
+        assert lib.debye_fit_init(ctypes.byref(h), ctypes.byref(o)) == D.DEBYE_EINVAL, (cb, lanes)
     for field, bad in (("de_cr", 1.5), ("de_f_lo", -0.1), ("de_f_hi", 0.25), ("de_strategy", 2),
-                       ("da_t0", 0.0), ("da_qa", 1.0), ("solve_lanes", 2), ("solve_lanes", 16)):
+                       ("da_t0", 0.0), ("da_qa", 1.0), ("solve_lanes", 2), ("solve_lanes", 16),
+                       ("lanes_per_candidate", 3), ("lanes_per_candidate", 64)):
         o = D.default_options()
         setattr(o, field, bad)
         assert lib.debye_fit_init(ctypes.byref(h), ctypes.byref(o)) == D.DEBYE_EINVAL
@@ -57,7 +59,8 @@ def test_init_rejects_bad_options(lib):
 
 def test_null_handle_calls(lib):
     assert lib.debye_fit_destroy(None) == D.DEBYE_OK
-    assert lib.debye_eval_population(None, None, 1, 1, None, None, None, None) == D.DEBYE_EINVAL
+    assert lib.debye_eval_population(None, None, 1, 1, None, None, None, None, None) == D.DEBYE_EINVAL
+    assert lib.debye_cost_grad(None, None, 1, 1, None, None, None, None, None) == D.DEBYE_EINVAL
     assert lib.debye_sync(None, None) == D.DEBYE_EINVAL
     assert lib.debye_version().startswith(b"debyefit")
 
@@ -78,6 +81,7 @@ int main(void) {
          offsetof(debye_search, method));
   printf("%zu %zu %zu\n", offsetof(debye_options, da_t0), offsetof(debye_options, da_qa),
          offsetof(debye_options, solve_lanes));
+  printf("%zu\n", offsetof(debye_search, n_failed));
   return 0;
 }
 ''')
@@ -102,3 +106,4 @@ int main(void) {
     assert vals[10] == D.SearchC.method.offset
     assert vals[11] == D.Options.da_t0.offset and vals[12] == D.Options.da_qa.offset
     assert vals[13] == D.Options.solve_lanes.offset
+    assert vals[14] == D.SearchC.n_failed.offset

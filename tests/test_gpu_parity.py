@@ -16,14 +16,14 @@ from oracle import dls, fit, models, varpro
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-COST_TOL = {"fp64": 1e-10, "mixed": 1e-5}
-GRAD_TOL = {"fp64": 1e-8, "mixed": 1e-4}
+COST_TOL = {"fp64": 1e-10, "fp64_sums": 1e-10, "mixed": 1e-5}
+GRAD_TOL = {"fp64": 1e-8, "fp64_sums": 1e-8, "mixed": 1e-4}
 # Weights, relative to the largest weight of the candidate. The cost is stationary
 # in the weights, the weights are not: FP64 carries the Cholesky solve's rounding
 # (~1e-13 of the scale at the damped condition number kappa <= (n + lam)/lam);
 # mixed precision the FP32 factor's error after one refinement step,
 # (kappa 2^-24)^2 ~ 1.6e-6 at n = 21, lam = 1e-3.
-WEIGHT_TOL = {"fp64": 1e-10, "mixed": 1e-5}
+WEIGHT_TOL = {"fp64": 1e-10, "fp64_sums": 1e-10, "mixed": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -82,7 +82,7 @@ def test_synth_matches_oracle(D):
 
 # the mixed path's small-system solve in both forms: one thread per candidate
 # (solve_lanes 1) and one warp per candidate (32, the default at these sizes)
-PREC_LANES = [("fp64", 0), ("mixed", 1), ("mixed", 32)]
+PREC_LANES = [("fp64", 0), ("fp64_sums", 0), ("mixed", 1), ("mixed", 32)]
 
 
 @pytest.mark.parametrize("prec,lanes", PREC_LANES)
@@ -106,6 +106,39 @@ def test_eval_population_ragged(D, prec, lanes):
         assert np.all(w[s, :, b.n_poles[s] + 1:] == 0)
 
 
+@pytest.mark.parametrize("cb", [32, 128])
+def test_eval_one_lane_per_candidate_every_n(D, cb):
+    # a forced block size gives one lane per candidate (the full-population layout): the
+    # column-sum solve then runs per pole count with the system in registers for N up to
+    # 12, and in the general kernel above; costs, weights and gradients for N = 1..20
+    b = ragged_batch()
+    re, im = models.synthesize(b)
+    th = W.population(b, 70, seed=9)
+    ref, wref = oracle_costs(b, re, im, th)
+    sp = spectra_for(D, b, re, im)
+    with D.Handle("mixed", cands_per_block=cb) as h:
+        cost, w = D.debye_eval_population(h, sp, torch.as_tensor(th, device="cuda"), weights=True)
+        cost2, grad = D.debye_cost_grad(h, sp, torch.as_tensor(th, device="cuda"))
+        D.debye_sync(h)
+    cost, w, cost2, grad = cost.cpu().numpy(), w.cpu().numpy(), cost2.cpu().numpy(), grad.cpu().numpy()
+    assert (np.abs(cost - ref) / ref).max() <= COST_TOL["mixed"]
+    assert (np.abs(cost2 - ref) / ref).max() <= COST_TOL["mixed"]
+    assert (np.abs(w - wref) / np.abs(wref).max(axis=2, keepdims=True)).max() <= WEIGHT_TOL["mixed"]
+    checked = 0
+    for s in range(b.S):
+        a, c = b.offsets[s], b.offsets[s + 1]
+        N = int(b.n_poles[s])
+        assert np.all(w[s, :, N + 1:] == 0) and np.all(grad[s, :, N:] == 0)
+        for p in range(0, 70, 7):
+            x = wref[s, p, :N + 1]
+            if np.min(np.abs(x[1:])) < 1e-6 * np.abs(x).max():
+                continue
+            _, gref = varpro.cost_grad(b.omega[a:c], re[a:c], im[a:c], th[s, p, :N])
+            assert np.linalg.norm(grad[s, p, :N] - gref) <= GRAD_TOL["mixed"] * np.linalg.norm(gref), (s, p)
+            checked += 1
+    assert checked >= 100
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("cb", [32, 96, 128])
 def test_eval_block_sizes(D, prec, cb):
@@ -118,7 +151,7 @@ def test_eval_block_sizes(D, prec, cb):
     assert (np.abs(cost.cpu().numpy() - ref) / ref).max() <= COST_TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64_sums", "mixed"])
 def test_eval_full_size_sampled(D, prec):
     # the 1024-spectrum workload at full population, checked on a seeded sample
     b = W.workload("mixed_1024")
@@ -200,12 +233,43 @@ def test_autotune_then_eval(D, tmp_path):
     ref, _ = oracle_costs(b, re, im, th.cpu().numpy())
     cache = str(tmp_path / "tune.txt")
     with D.Handle("mixed") as h:
-        cb = D.debye_autotune(h, sp, th, cache_path=cache)
-        assert cb in (32, 64, 96, 128)
-        assert D.debye_autotune(h, sp, th, cache_path=cache) == cb     # served from the cache
+        t = D.debye_autotune(h, sp, th, cache_path=cache)
+        assert (t["cands_per_block"], t["lanes_per_candidate"]) in FULL_LAYOUTS
+        assert (t["polish_cands_per_block"], t["polish_lanes_per_candidate"]) in POLISH_LAYOUTS
+        assert D.debye_autotune(h, sp, th, cache_path=cache) == t     # served from the cache
         cost = D.debye_eval_population(h, sp, th).cpu().numpy()
+        out = D.debye_fit_batch(h, sp, P=96, iters=3, polish_topk=8, polish_iters=3)   # tuned polish layout
+        D.debye_sync(h)
     assert (np.abs(cost - ref) / ref).max() <= COST_TOL["mixed"]
     assert open(cache).read().count("|") == 1
+    assert torch.isfinite(out["final_cost"]).all()
+
+
+# the layouts debye_autotune chooses from: full populations and the polish's accepted points
+FULL_LAYOUTS = [(32, 1), (64, 1), (96, 1), (128, 1), (32, 2), (64, 2), (32, 4)]
+POLISH_LAYOUTS = [(16, 4), (8, 8), (4, 16), (2, 32), (32, 4), (16, 8), (8, 16), (4, 32)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_eval_every_tuned_layout(D, prec):
+    # every (candidates per block, lanes per candidate) the autotuner may pick, forced
+    # through the options on a batch of N = 1..20 with 40 candidates per spectrum:
+    # costs, and with the polish layouts the gradient too, against the oracle
+    b = W.mixed_batch(S=10, seed=19, P=40, K_range=(20, 400), N_range=(1, 20))
+    b.n_poles[:] = [1, 2, 3, 5, 8, 9, 12, 13, 17, 20]
+    re, im = models.synthesize(b)
+    th = W.population(b, 40, seed=7)
+    ref, _ = oracle_costs(b, re, im, th)
+    sp = spectra_for(D, b, re, im)
+    tt = torch.as_tensor(th, device="cuda")
+    for cb, ks in FULL_LAYOUTS + POLISH_LAYOUTS:
+        with D.Handle(prec, cands_per_block=cb, lanes_per_candidate=ks) as h:
+            cost = D.debye_eval_population(h, sp, tt).cpu().numpy()
+            if (cb, ks) in POLISH_LAYOUTS:
+                c2, g = D.debye_cost_grad(h, sp, tt)
+                assert (np.abs(c2.cpu().numpy() - ref) / ref).max() <= COST_TOL[prec], (cb, ks)
+            D.debye_sync(h)
+        assert (np.abs(cost - ref) / ref).max() <= COST_TOL[prec], (cb, ks)
 
 
 def test_duplicate_tau_and_tiny_k(D):
@@ -218,6 +282,47 @@ def test_duplicate_tau_and_tiny_k(D):
         with D.Handle(prec, solve_lanes=lanes) as h:
             cost = D.debye_eval_population(h, spectra_for(D, b, re, im), torch.as_tensor(th, device="cuda"))
         assert (np.abs(cost.cpu().numpy() - ref) / ref).max() <= COST_TOL[prec], (prec, lanes)
+
+
+@pytest.mark.parametrize("prec,lanes", PREC_LANES + [("mixed", 1)])
+def test_failure_counter(D, prec, lanes):
+    # a candidate whose damped matrix is not positive definite gets cost +inf and counts
+    # once in its spectrum's n_failed: with the default damping that happens only for
+    # non-finite theta (one in five candidates here); spectra with K = 1..3 samples,
+    # whose undamped Gram is singular, and exactly repeated poles do not fail
+    with_cb = {"cands_per_block": 32} if (prec, lanes) == ("mixed", 1) else {}
+    for b in (W.mixed_batch(S=3, seed=5, P=40, K_range=(1, 3), N_range=(2, 4)),
+              W.mixed_batch(S=3, seed=6, P=40, K_range=(40, 200), N_range=(2, 9))):
+        re, im = models.synthesize(b)
+        th = W.population(b, 40, seed=2)
+        th[:, 1::5, 1] = th[:, 1::5, 0]          # exactly repeated pole
+        th[:, ::5, 0] = np.nan
+        sp = spectra_for(D, b, re, im)
+        tt = torch.as_tensor(th, device="cuda")
+        with D.Handle(prec, solve_lanes=lanes, **with_cb) as h:
+            nf = torch.zeros(b.S, dtype=torch.int32, device="cuda")
+            cost, w = D.debye_eval_population(h, sp, tt, weights=True, n_failed=nf)
+            nf2 = torch.zeros(b.S, dtype=torch.int32, device="cuda")
+            cost2, grad = D.debye_cost_grad(h, sp, tt, n_failed=nf2)
+            D.debye_sync(h)
+        cost, w, cost2, grad = cost.cpu().numpy(), w.cpu().numpy(), cost2.cpu().numpy(), grad.cpu().numpy()
+        bad = np.zeros(th.shape[:2], bool)
+        bad[:, ::5] = True
+        assert np.all(np.isinf(cost[bad])) and np.all(np.isfinite(cost[~bad]))
+        assert np.all(np.isinf(cost2[bad])) and np.all(np.isfinite(cost2[~bad]))
+        np.testing.assert_array_equal(nf.cpu().numpy(), bad.sum(axis=1))
+        np.testing.assert_array_equal(nf2.cpu().numpy(), bad.sum(axis=1))
+        assert np.all(w[bad] == 0) and np.all(grad[bad] == 0) and np.all(np.isfinite(grad))
+        ref, _ = oracle_costs(b, re, im, np.where(np.isnan(th), 0.0, th))
+        assert (np.abs(cost[~bad] - ref[~bad]) / ref[~bad]).max() <= COST_TOL[prec]
+    # a whole fit counts nothing on regular spectra
+    b = W.mixed_batch(S=3, seed=7, P=32, K_range=(40, 120), N_range=(2, 5))
+    re, im = models.synthesize(b)
+    with D.Handle(prec, solve_lanes=lanes) as h:
+        out = D.debye_fit_batch(h, spectra_for(D, b, re, im), P=32, iters=5, polish_topk=2, polish_iters=3,
+                                n_failed=True)
+        D.debye_sync(h)
+    assert out["n_failed"].dtype == torch.int32 and int(out["n_failed"].sum()) == 0
 
 
 def test_input_errors(D):
@@ -327,10 +432,11 @@ def fitted(om, eps_inf, d_eps, tau):
     return models.multi_debye(om, eps_inf, d_eps, tau)
 
 
-def test_fit_fp64_swarm_trace_matches_oracle(D):
+@pytest.mark.parametrize("prec", ["fp64", "fp64_sums"])
+def test_fit_fp64_swarm_trace_matches_oracle(D, prec):
     b = W.single_hn()
     re, im = models.synthesize(b)
-    with D.Handle("fp64") as h:
+    with D.Handle(prec) as h:
         out = D.debye_fit_batch(h, spectra_for(D, b, re, im), P=64, iters=100, seed=0, polish_topk=0,
                                 trace=True)
         D.debye_sync(h)
@@ -343,7 +449,7 @@ def test_fit_fp64_swarm_trace_matches_oracle(D):
     assert out["evals"].item() == 64 * 101 * 50
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64_sums", "mixed"])
 def test_fit_with_polish_matches_oracle(D, prec):
     # Every spectrum: the fitted spectrum within 1e-4 relative RMS of the oracle's,
     # or a final cost at most the oracle's x (1 + 1e-6). FP64 follows the oracle's
@@ -364,7 +470,7 @@ def test_fit_with_polish_matches_oracle(D, prec):
         e_gpu = fitted(b.omega[a:c], out["eps_inf"][s].item(), out["d_eps"][s, :N].cpu().numpy(),
                        out["tau"][s, :N].cpu().numpy())
         gcost = out["final_cost"][s].item()
-        if prec == "fp64":
+        if prec != "mixed":
             r = fit_oracle(b, re, im, s, 64, 60, 8, 40)
             assert fitcheck.agree(e_gpu, gcost, fit.fitted_eps(b.omega[a:c], r), r["cost_final"]), \
                 (s, dls.rel_rms(e_gpu, fit.fitted_eps(b.omega[a:c], r)), gcost, r["cost_final"])
@@ -378,6 +484,31 @@ def test_fit_with_polish_matches_oracle(D, prec):
         assert np.all(np.diff(out["tau"][s, :N].cpu().numpy()) >= 0)
     print(prec, how)
     assert how.count("strict") >= b.S // 2, how
+
+
+def test_polish_evaluation_count_matches_oracle(D):
+    # FP64, the polish started from the seeded initial population (no swarm updates) for
+    # three L-BFGS iterations: every Armijo decision is a real descent test (far above
+    # rounding), so the GPU's line searches make the oracle's sequential decisions, and
+    # the evaluation count (population, polish start, and per iteration the trials up
+    # to the accepted one) is the oracle's x K. Once a polish has converged, its Armijo
+    # decisions compare costs equal to the last bits and no longer follow the oracle's.
+    b = W.mixed_batch(S=5, seed=33, P=32, K_range=(50, 200), N_range=(2, 6))
+    re, im = models.synthesize(b)
+    with D.Handle("fp64") as h:
+        out = D.debye_fit_batch(h, spectra_for(D, b, re, im), P=32, iters=0, seed=0, polish_topk=8,
+                                polish_iters=3)
+        D.debye_sync(h)
+    expect = 0
+    for s in range(b.S):
+        a, c = b.offsets[s], b.offsets[s + 1]
+        r = fit_oracle(b, re, im, s, 32, 0, 8, 3)
+        expect += r["n_evals"] * (c - a)
+        N = int(b.n_poles[s])
+        e_gpu = fitted(b.omega[a:c], out["eps_inf"][s].item(), out["d_eps"][s, :N].cpu().numpy(),
+                       out["tau"][s, :N].cpu().numpy())
+        assert dls.rel_rms(e_gpu, fit.fitted_eps(b.omega[a:c], r)) <= 1e-8
+    assert out["evals"].item() == expect, (out["evals"].item(), expect)
 
 
 # ---------------------------------------------------------------- differential evolution

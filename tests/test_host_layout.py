@@ -17,16 +17,16 @@ HARNESS = r'''
 int main() {
   const long long per[] = {1, 2, 3, 7, 8, 16, 31, 32, 33, 64, 100, 256, 4096};
   const long long tot[] = {1, 100, 8192, 32768, 262144, 1LL << 20, 1LL << 40};
-  const int forced[] = {0, 32, 128};
-  const int tuned[] = {0, 64, 128};
+  const debyefit::Layout forced[] = {{0, 0}, {32, 0}, {128, 0}, {32, 4}, {0, 2}, {8, 16}};
+  const debyefit::Layout tuned[] = {{0, 0}, {64, 1}, {128, 1}, {64, 2}, {32, 4}};
   for (long long p : per)
     for (long long t : tot)
-      for (int f : forced)
-        for (int u : tuned) {
+      for (const auto& f : forced)
+        for (const auto& u : tuned) {
           if (t < p) continue;
           int cb = 0, ks = 0;
           debyefit::choose_layout(p, t, 152, f, u, &cb, &ks);
-          std::printf("%lld %lld %d %d %d %d\n", p, t, f, u, cb, ks);
+          std::printf("%lld %lld %d %d %d %d %d %d\n", p, t, f.cb, f.ks, u.cb, u.ks, cb, ks);
         }
   std::printf("MAX_BLOCK %d\n", debyefit::MAX_BLOCK);
   return 0;
@@ -53,15 +53,15 @@ def layouts(tmp_path_factory):
 
 def test_layout_invariants(layouts):
     rows, max_block = layouts
-    assert len(rows) > 500
+    assert len(rows) > 1500
     target = 152 * 2048
-    for p, t, f, u, cb, ks in rows:
-        assert ks in (1, 2, 4, 8, 16, 32), (p, t, f, u, cb, ks)
-        assert cb >= 1 and cb * ks <= max_block, (p, t, f, u, cb, ks)
-        if f > 0 and p >= 32:
-            assert (cb, ks) == (f, 1)
-        elif p >= 32 and 2 * t >= target:
-            assert ks == 1 and cb == (u if u > 0 else 64)
+    for p, t, fc, fk, uc, uk, cb, ks in rows:
+        assert ks in (1, 2, 4, 8, 16, 32), (p, t, fc, fk, uc, uk, cb, ks)
+        assert cb >= 1 and cb * ks <= max_block, (p, t, fc, fk, uc, uk, cb, ks)
+        if p >= 32 and (fc > 0 or 2 * t >= target):       # full population
+            want_ks = fk if fk else (1 if fc else (uk if uk else 1))
+            want_cb = fc if fc else (uc if uc else 64)
+            assert (cb, ks) == (min(want_cb, max_block // want_ks), want_ks), (p, t, fc, fk, uc, uk, cb, ks)
         else:
             assert cb * ks == 64 or (cb == 1 and ks == 32)   # a 64-thread block (or one 32-lane candidate)
 
@@ -69,8 +69,8 @@ def test_layout_invariants(layouts):
 def test_small_batches_get_more_lanes(layouts):
     rows, _ = layouts
     by = {}
-    for p, t, f, u, cb, ks in rows:
-        if f == 0 and u == 0:
+    for p, t, fc, fk, uc, uk, cb, ks in rows:
+        if fc == fk == uc == uk == 0:
             by.setdefault(p, []).append((t, ks))
     for p, seq in by.items():
         seq.sort()

@@ -479,6 +479,90 @@ def test_pso_finds_quadratic_minimum():
     np.testing.assert_allclose(pbx[gi], target, atol=1e-4)
 
 
+def _recording(f):
+    """cost function that also records every population it evaluates"""
+    seen = []
+
+    def g(th):
+        seen.append((th.copy(), f(th)))
+        return seen[-1][1]
+    return g, seen
+
+
+def test_pso_initial_state_distribution():
+    # positions U[lo, hi], velocities U[-(hi - lo), hi - lo]: the first generation's
+    # positions x1 = clip(x0 + v1) with omega = 1, phi = 0 give v1 = v0 = x1 - x0 where
+    # unclipped; Kolmogorov-Smirnov against the two uniform laws (10^4 draws each)
+    from scipy import stats
+    lo, hi = -13.0, -5.0
+    f, seen = _recording(lambda th: np.zeros(th.shape[0]))
+    pso.pso(f, 4, lo, hi, 2500, 1, seed=3, omega=1.0, phi_p=0.0, phi_g=0.0)
+    x0, x1 = seen[0][0], seen[1][0]
+    assert stats.kstest(((x0 - lo) / (hi - lo)).ravel(), "uniform").pvalue > 1e-3
+    free = (x1 > lo) & (x1 < hi)
+    v = (x1 - x0)[free] / (hi - lo)
+    # v0 ~ U[-1, 1] conditioned on x0 + v0 staying inside: compare with the same
+    # conditioning applied to exact uniform draws
+    rs = np.random.default_rng(0)
+    u0 = rs.uniform(0, 1, 200000)
+    w0 = rs.uniform(-1, 1, 200000)
+    keep = (u0 + w0 > 0) & (u0 + w0 < 1)
+    assert stats.ks_2samp(v, w0[keep]).pvalue > 1e-3
+    assert abs(np.mean(free) - np.mean(keep)) < 0.02
+
+
+def test_pso_social_term_pulls_towards_the_global_best():
+    # omega = 0, phi_p = 0, phi_g = 1: v1 = r2 (g - x0) with r2 in [0, 1), so every
+    # particle lands on the segment from its start to the global best of generation 0
+    target = np.array([-9.0, -7.0, -11.0])
+    def f(th):
+        return np.sum((th - target) ** 2, axis=1)
+    rec, seen = _recording(f)
+    pso.pso(rec, 3, -13.0, -5.0, 64, 1, seed=5, omega=0.0, phi_p=0.0, phi_g=1.0)
+    (x0, c0), (x1, _) = seen[0], seen[1]
+    g = x0[int(np.argmin(c0))]
+    t = (x1 - x0) / np.where(g - x0 == 0, 1.0, g - x0)
+    assert np.all((t >= 0) & (t < 1) | (g - x0 == 0))
+    # and not towards the particle's own start (phi_p = 1, phi_g = 0: at generation 1
+    # the personal best is the start itself, so nothing moves)
+    rec2, seen2 = _recording(f)
+    pso.pso(rec2, 3, -13.0, -5.0, 64, 1, seed=5, omega=0.0, phi_p=1.0, phi_g=0.0)
+    np.testing.assert_array_equal(seen2[1][0], seen2[0][0])
+
+
+def test_pso_inertia_and_clipping():
+    # omega = 1, phi = 0: straight lines with the initial velocity, clipped to the box;
+    # a particle stays at a bound while its velocity points outwards
+    rec, seen = _recording(lambda th: np.zeros(th.shape[0]))
+    pso.pso(rec, 2, -13.0, -5.0, 50, 6, seed=7, omega=1.0, phi_p=0.0, phi_g=0.0)
+    xs = np.array([x for x, _ in seen])
+    assert xs.min() >= -13.0 and xs.max() <= -5.0
+    v0 = xs[1] - xs[0]
+    for k in range(1, len(xs)):
+        expect = np.clip(xs[0] + k * v0, -13.0, -5.0)   # exact where no clip happened before
+        inside = np.all([(xs[0] + j * v0 > -13.0) & (xs[0] + j * v0 < -5.0) for j in range(1, k)], axis=0) \
+            if k > 1 else np.ones_like(v0, bool)
+        np.testing.assert_allclose(xs[k][inside], expect[inside], rtol=0, atol=1e-12)
+    assert np.any(xs == -13.0) and np.any(xs == -5.0)
+
+
+def test_pso_trace_is_running_minimum_of_all_costs():
+    # synchronous update, personal best replaced only on a strictly lower cost: the
+    # global best after each generation is the lowest cost evaluated so far, and each
+    # personal best is the lowest cost its particle has seen
+    rs = np.random.default_rng(4)
+    A = rs.standard_normal((3, 3))
+    def f(th):
+        d = th + 9.0
+        return np.einsum("pi,ij,pj->p", d, A @ A.T, d) + np.sin(5 * th).sum(axis=1)
+    rec, seen = _recording(f)
+    pbx, pbc, gi, trace = pso.pso(rec, 3, -13.0, -5.0, 40, 30, seed=2)
+    costs = np.array([c for _, c in seen])
+    np.testing.assert_array_equal(trace, np.minimum.accumulate(costs.min(axis=1)))
+    np.testing.assert_array_equal(pbc, costs.min(axis=0))
+    assert pbc[gi] == costs.min()
+
+
 def test_lbfgs_box_quadratic_and_bound():
     Q = np.array([[3.0, 1.0], [1.0, 2.0]])
     c = np.array([-9.0, -8.0])
