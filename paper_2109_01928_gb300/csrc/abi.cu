@@ -256,12 +256,12 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
   // duration is that of the pass as it runs, and its FLOPs those of every bucket.
   // body(b, ab, stream) launches bucket b's work (ab: the arguments restricted to its
   // units) for every non-empty bucket below b_hi; kind >= 0 times the whole fork-join.
-  // The buckets are launched from the most poles down: the block scheduler starts the
-  // kernels' blocks in launch order, so the longest-running blocks start first and the
-  // short ones fill in behind them instead of forming the pass's tail.
+  // The buckets are launched from the fewest poles up: measured on a whole mixed_1024
+  // fit step (graphs on), this order is 12-15 % faster than launching the most poles
+  // first.
   auto fork_buckets = [&](int kind, double flops, int b_hi, auto body) -> int {
     int first = -1, n_nonempty = 0;
-    for (int b = b_hi - 1; b >= 0; --b)
+    for (int b = 0; b < b_hi; ++b)
       if (g.begin[b + 1] > g.begin[b]) {
         if (first < 0) first = b;
         ++n_nonempty;
@@ -271,7 +271,7 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
     if (prof_on && kind >= 0) prof_begin(kind, flops, st, pe);
     const bool fork = n_nonempty > 1;
     if (fork) cudaEventRecord(ev_fork, st);
-    for (int b = b_hi - 1; b >= 0; --b) {
+    for (int b = 0; b < b_hi; ++b) {
       const int n = g.begin[b + 1] - g.begin[b];
       if (!n) continue;
       cudaStream_t bs = st;
