@@ -570,6 +570,7 @@ def main():
     if args.iters is not None:
         bn.iters = args.iters
     b = bn.b
+    desc = workload_desc(b, bn.iters)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
     hm = D.Handle("mixed")
@@ -670,7 +671,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": float(np.mean(rm["times"])), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded HN/CC/CD/Jonscher/CRIM spectra, targets synthesised on the device)",
-        "config": {"workload": workload_desc(b, bn.iters),
+        "config": {"workload": desc,
                    "precision": "mixed (float-float column sums, exact Gram identity, FP32 factor refined "
                                 "in float-float)",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
