@@ -253,6 +253,93 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
 
 }
 
+// ------------------------------------------------------------------ sample staging (bulk copies)
+// The column-sum pass reads, for every sample of a unit's spectrum, the two float4
+// records {(omega 2^-30)^2, eps', omega eps''} (high and low float-float parts);
+// every lane of the block reads the same samples. They are staged in shared memory
+// in chunks of STAGE_SAMPLES by the Tensor Memory Accelerator (cp.async.bulk, a
+// plain global -> shared copy completing on an mbarrier), double-buffered: thread 0
+// issues chunk c + 1 while the block computes on chunk c. Every record is 16 bytes
+// and 16-byte aligned, as the bulk copy requires.
+//
+// Every wait on an mbarrier is bounded (STAGE_WAIT_CYCLES of clock64): a wait that
+// runs out records DEBYE_ETIMEOUT, the block agrees on it (__syncthreads_or), waits
+// again, bounded, for its own copies still in flight, and leaves the kernel.
+constexpr int STAGE_SAMPLES = 256;
+constexpr long long STAGE_WAIT_CYCLES = 1ll << 31;   // about 1 s at the maximum SM clock
+
+struct Stage {
+  float4* hi;        // [2][STAGE_SAMPLES]
+  float4* lo;        // [2][STAGE_SAMPLES]
+  uint64_t* bar;     // [2] one mbarrier per buffer
+  uint32_t fills0, fills1;     // completed phases of each buffer (the same in every thread)
+  bool pending0, pending1;     // a copy into the buffer has been issued and not yet waited for
+  __device__ __forceinline__ uint32_t& fills(int b) { return b ? fills1 : fills0; }
+  __device__ __forceinline__ bool& pending(int b) { return b ? pending1 : pending0; }
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void stage_init(Stage& st, float4* buf, uint64_t* bar) {
+  st.hi = buf;
+  st.lo = buf + 2 * STAGE_SAMPLES;
+  st.bar = bar;
+  st.fills0 = st.fills1 = 0;
+  st.pending0 = st.pending1 = false;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar + b)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+// Thread 0: copy samples k .. k + n - 1 of both record arrays into buffer b.
+__device__ __forceinline__ void stage_issue(const EvalArgs& a, Stage& st, int b, int64_t k, int n) {
+  if (threadIdx.x == 0) {
+    const uint32_t bytes = (uint32_t)n * (uint32_t)sizeof(float4);
+    const uint32_t bar = smem_addr(st.bar + b);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier generic reads of the buffer
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2u * bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(st.hi + b * STAGE_SAMPLES)), "l"(a.kq32 + k), "r"(bytes), "r"(bar) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(st.lo + b * STAGE_SAMPLES)), "l"(a.kqff + k), "r"(bytes), "r"(bar) : "memory");
+  }
+  st.pending(b) = true;
+}
+
+// Wait (bounded) until buffer b's current phase has completed.
+__device__ __forceinline__ bool stage_wait_one(Stage& st, int b) {
+  const uint32_t bar = smem_addr(st.bar + b), parity = st.fills(b) & 1u;
+  const long long t0 = clock64();
+  uint32_t done = 0;
+  while (true) {
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done || clock64() - t0 > STAGE_WAIT_CYCLES) break;
+  }
+  if (done) {
+    st.fills(b) += 1;
+    st.pending(b) = false;
+  }
+  return done != 0;
+}
+
+// Buffer b ready in every thread; false (the block agreeing) if a wait ran out.
+__device__ __forceinline__ bool stage_wait(const EvalArgs& a, Stage& st, int b) {
+  const bool ok = stage_wait_one(st, b);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) set_status(a.status, DEBYE_ETIMEOUT);
+    for (int c = 0; c < 2; ++c)
+      if (st.pending(c)) stage_wait_one(st, c);   // the block's own copies in flight
+    return false;
+  }
+  return true;
+}
+
 // ------------------------------------------------------------------ column-sum pass (mixed)
 // For the mixed evaluation from column sums (k_solve_sums): per candidate, in
 // float-float,
@@ -281,12 +368,9 @@ __device__ __forceinline__ void refine_unit(const EvalArgs& a, const Unit& u) {
 //
 // One sweep over the samples for poles P0 .. P0 + C - 1 of an N-pole candidate:
 template <int N, int P0, int C, bool GRAD>
-__device__ __forceinline__ void sums_sq_sweep(const EvalArgs& a, const Unit& u, const Lane& ln, int q) {
+__device__ __forceinline__ bool sums_sq_sweep(const EvalArgs& a, const Unit& u, const Lane& ln, int q, Stage& st) {
   const double* th = a.theta + (int64_t)q * a.sc.nmax + P0;
   const int64_t Q = a.sc.Q;
-  const int64_t kbeg = u.k0 + ln.slice;
-  const int64_t kend = ln.act ? u.k1 : kbeg;
-  const int64_t step = ln.ks;
   constexpr int CG = GRAD ? C : 1;
   float t2h[C], t2l[C], sh[C], sl[C], ah[C], al[C], ch[C], cl[C];
   float uh[CG], ul[CG], vh_[CG], vl_[CG], wh[CG], wl[CG];
@@ -307,14 +391,28 @@ __device__ __forceinline__ void sums_sq_sweep(const EvalArgs& a, const Unit& u, 
     uh[i] = 1.f;
     ul[i] = vh_[i] = vl_[i] = wh[i] = wl[i] = 0.f;
   }
-  const int64_t k0s = kbeg < u.k1 ? kbeg : u.k0;
-  float4 vhn = __ldg(&a.kq32[k0s]), vln = __ldg(&a.kqff[k0s]);
+  const int64_t nk = u.k1 - u.k0;
+  const int nch = (int)((nk + STAGE_SAMPLES - 1) / STAGE_SAMPLES);
+  auto chunk_len = [&](int64_t c0) { return (int)(nk - c0 < STAGE_SAMPLES ? nk - c0 : STAGE_SAMPLES); };
+  if (nch > 0) stage_issue(a, st, 0, u.k0, chunk_len(0));
 #pragma unroll 1
-  for (int64_t k = kbeg; k < kend; k += step) {
+  for (int c = 0; c < nch; ++c) {
+    const int b = c & 1;
+    const int64_t c0 = (int64_t)c * STAGE_SAMPLES;
+    if (c + 1 < nch)   // buffer b ^ 1 was released by the barrier that ended chunk c - 1
+      stage_issue(a, st, b ^ 1, u.k0 + c0 + STAGE_SAMPLES, chunk_len(c0 + STAGE_SAMPLES));
+    if (!stage_wait(a, st, b)) return false;
+    const int cnt = chunk_len(c0);
+    const float4* bh = st.hi + b * STAGE_SAMPLES;
+    const float4* bl = st.lo + b * STAGE_SAMPLES;
+    const int jend = ln.act ? cnt : 0;
+    float4 vhn = bh[ln.slice < jend ? ln.slice : 0], vln = bl[ln.slice < jend ? ln.slice : 0];
+#pragma unroll 1
+  for (int j = ln.slice; j < jend; j += ln.ks) {
     const float4 vh = vhn, vl = vln;
-    if (k + step < kend) {   // next sample in flight during this one
-      vhn = __ldg(&a.kq32[k + step]);
-      vln = __ldg(&a.kqff[k + step]);
+    if (j + ln.ks < jend) {   // next sample's records in flight during this one
+      vhn = bh[j + ln.ks];
+      vln = bl[j + ln.ks];
     }
 #pragma unroll
     for (int i = 0; i < C; ++i) {
@@ -347,6 +445,8 @@ __device__ __forceinline__ void sums_sq_sweep(const EvalArgs& a, const Unit& u, 
         ff_add_prod(wh[i], wl[i], qh, ql, vh.z, vl.z);               // u omega eps''
       }
     }
+  }
+    __syncthreads();   // the whole block is done with buffer b
   }
 #pragma unroll
   for (int i = 0; i < C; ++i) {
@@ -381,20 +481,24 @@ __device__ __forceinline__ void sums_sq_sweep(const EvalArgs& a, const Unit& u, 
       }
     }
   }
+  return true;
 }
 
 // With GRAD, more than SQUARED_CHUNK_GRAD poles take two sweeps of about N/2 poles
-// each (14 registers per pole); the cost-only sums (8 per pole) sweep once.
+// each (14 registers per pole); the cost-only sums (8 per pole) sweep once. A unit
+// without any active candidate (a masked evaluation) is skipped by the whole block.
+// Returns false if a wait for staged samples ran out (the block then stops).
 template <int N, bool GRAD>
-__device__ __forceinline__ void sums_sq_unit(const EvalArgs& a, const Unit& u) {
+__device__ __forceinline__ bool sums_sq_unit(const EvalArgs& a, const Unit& u, Stage& st) {
   const Lane ln = lane_of(a, u, false);
+  if (!__syncthreads_or(ln.act)) return true;
   const int q = ln.act ? ln.q : u.q0;
   if constexpr (!GRAD || N <= SQUARED_CHUNK_GRAD) {
-    sums_sq_sweep<N, 0, N, GRAD>(a, u, ln, q);
+    return sums_sq_sweep<N, 0, N, GRAD>(a, u, ln, q, st);
   } else {
     constexpr int C1 = (N + 1) / 2;
-    sums_sq_sweep<N, 0, C1, GRAD>(a, u, ln, q);
-    sums_sq_sweep<N, C1, N - C1, GRAD>(a, u, ln, q);
+    if (!sums_sq_sweep<N, 0, C1, GRAD>(a, u, ln, q, st)) return false;
+    return sums_sq_sweep<N, C1, N - C1, GRAD>(a, u, ln, q, st);
   }
 }
 
@@ -488,8 +592,6 @@ __device__ __forceinline__ void run_phase(const EvalArgs& a, const Unit& u) {
   if constexpr (PH == PH_GRAM) gram_unit<N>(a, u);
   else if constexpr (PH == PH_GRAM_SUMS) gram_sums_unit<N>(a, u);
   else if constexpr (PH == PH_REFINE) refine_unit<N>(a, u);
-  else if constexpr (PH == PH_SUMS) sums_sq_unit<N, false>(a, u);
-  else if constexpr (PH == PH_SUMSG) sums_sq_unit<N, true>(a, u);
   else grad_unit<N>(a, u);
 }
 
@@ -505,6 +607,24 @@ __device__ __forceinline__ void dispatch_n(const EvalArgs& a, const Unit& u) {
 // pole counts compiled into this kernel (the library launches one N per kernel). At most MAXT threads per block; MINB
 // resident blocks of that size bound the registers per thread (128 x 3: 168
 // registers, 12 warps per SM with 64-thread blocks).
+// The column-sum pass (PH_SUMS, PH_SUMSG) of pole count N: one block per unit
+// (grid-stride over the unit list), the unit's samples staged by bulk copies.
+template <int N, bool GRAD, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_pass_sums(EvalArgs a) {
+  __shared__ __align__(128) float4 stage_buf[4 * STAGE_SAMPLES];
+  __shared__ __align__(8) uint64_t stage_bar[2];
+  Stage st;
+  stage_init(st, stage_buf, stage_bar);
+  for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {
+    const Unit u = a.units[ui];
+    if (u.N != N) {
+      if (threadIdx.x == 0) set_status(a.status, DEBYE_EBOUNDS);
+      continue;
+    }
+    if (!sums_sq_unit<N, GRAD>(a, u, st)) return;
+  }
+}
+
 template <int PH, int LO, int HI, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) k_pass(EvalArgs a) {
   for (int ui = blockIdx.x; ui < a.n_units; ui += gridDim.x) {

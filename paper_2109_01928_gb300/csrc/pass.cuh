@@ -18,8 +18,8 @@ void launch_pass_n(int phase, const EvalArgs& a, int grid, int block, cudaStream
   constexpr int MB_SUMS = N <= 12 ? 3 : 1;
   constexpr int MAXT = N <= 12 ? 128 : 256;
   switch (phase) {
-    case PH_SUMS: k_pass<PH_SUMS, N, N, MAXT, MB_SUMS><<<grid, block, 0, st>>>(a); break;
-    case PH_SUMSG: k_pass<PH_SUMSG, N, N, MAXT, 1><<<grid, block, 0, st>>>(a); break;
+    case PH_SUMS: k_pass_sums<N, false, MAXT, MB_SUMS><<<grid, block, 0, st>>>(a); break;
+    case PH_SUMSG: k_pass_sums<N, true, MAXT, 1><<<grid, block, 0, st>>>(a); break;
     case PH_GRAM: k_pass<PH_GRAM, N, N, MAXT, 1><<<grid, block, 0, st>>>(a); break;
     case PH_GRAM_SUMS: k_pass<PH_GRAM_SUMS, N, N, MAXT, 1><<<grid, block, 0, st>>>(a); break;
     case PH_REFINE: k_pass<PH_REFINE, N, N, MAXT, 1><<<grid, block, 0, st>>>(a); break;
