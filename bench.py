@@ -68,6 +68,26 @@ def replica_workload(name: str, rank: int):
     return W.workload(name, seed=rank)
 
 
+def split_by_weight(b, world: int, P: int):
+    """Contiguous shards of one batch's spectra, one per rank, balanced by the cumulative
+    work weight P K_s (N_s + 2)^2 (spectra are independent: no exchange is needed, the
+    results are gathered on the host). Returns [world + 1] spectrum boundaries."""
+    w = P * b.K.astype(np.float64) * (b.n_poles.astype(np.float64) + 2.0) ** 2
+    c = np.concatenate([[0.0], np.cumsum(w)])
+    bounds = [0]
+    for r in range(1, world):
+        bounds.append(int(np.searchsorted(c, c[-1] * r / world, side="left")))
+    bounds.append(b.S)
+    return np.maximum.accumulate(np.array(bounds, dtype=np.int64))
+
+
+def split_workload(name: str, rank: int, world: int):
+    """Rank r's shard of the seed-0 batch (strong scaling: the total work is fixed)."""
+    b = W.workload(name, seed=0)
+    bounds = split_by_weight(b, world, SETTINGS[name][0])
+    return b.subset(np.arange(bounds[rank], bounds[rank + 1]))
+
+
 class RankReduce:
     """Barrier and max/sum over ranks (NCCL on the GPUs, gloo in the CPU tests); with
     one rank these are identities. No collective touches the fitted data."""
@@ -524,6 +544,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--split", action="store_true",
+                    help="with N > 1: split the one seed-0 batch across the ranks by work weight (strong "
+                         "scaling) instead of one replica batch per rank (weak scaling, the default)")
     ap.add_argument("--configs", default="all", help="extra workloads: all, none or a comma list of "
                     + ", ".join(EXTRA_CONFIGS))
     ap.add_argument("--iters", type=int, default=None, help="swarm generations (default: the workload's)")
@@ -566,7 +589,8 @@ def main():
         dist.init_process_group("nccl", init_method="env://", device_id=dev)
     red = RankReduce(world, dev)
 
-    bn = Bench(D, torch, dev, WORKLOAD, seed=rank, b=replica_workload(WORKLOAD, rank))
+    bsel = split_workload(WORKLOAD, rank, world) if args.split else replica_workload(WORKLOAD, rank)
+    bn = Bench(D, torch, dev, WORKLOAD, seed=0 if args.split else rank, b=bsel)
     if args.iters is not None:
         bn.iters = args.iters
     b = bn.b
@@ -669,12 +693,14 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(np.mean(rm["times"])), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "scaling": "strong" if args.split else "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded HN/CC/CD/Jonscher/CRIM spectra, targets synthesised on the device)",
         "config": {"workload": desc,
                    "precision": "mixed (float-float column sums, exact Gram identity, FP32 factor refined "
                                 "in float-float)",
-                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": (f"weight-balanced split of one batch x{world}" if args.split
+                                   else f"replicas x{world}")},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": re2e["h2d"],
                 "d2h_bytes_per_step": re2e["d2h"]},
