@@ -238,8 +238,8 @@ int debye_fit_auto(debye_handle h, const debye_spectra* spectra, const debye_sea
  * Computes what debye_eval_population computes (costs, and weights if `weights`
  * is not NULL) for the options in `opt` (NULL = defaults), without a handle. The
  * results agree with debye_eval_population's to rounding, within the parity
- * tolerances of the cost (relative 1e-10 with DEBYE_PREC_FP64, 1e-5 with
- * DEBYE_PREC_MIXED), not bit for bit: the two entry points may split a candidate's
+ * tolerances of the cost (relative 1e-10 with DEBYE_PREC_FP64 and
+ * DEBYE_PREC_FP64_SUMS, 1e-5 with DEBYE_PREC_MIXED), not bit for bit: the two entry points may split a candidate's
  * samples over different numbers of lanes, and the mixed-precision solve here is
  * always the one-thread-per-candidate kernel. It calls no cudaMalloc, cudaFree
  * or other allocating routine: all temporary data lives in one fixed scratch
