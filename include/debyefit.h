@@ -65,6 +65,16 @@ extern "C" {
 #define DEBYE_PREC_FP64_SUMS 2 /* FP64 throughout, the Gram from FP64 column sums by the exact
                                  identity (no O(K N^2) Gram pass), then the FP64 solve and
                                  residual passes of DEBYE_PREC_FP64 */
+#define DEBYE_PREC_MIXED_TABLE 3 /* DEBYE_PREC_MIXED with the column sums read from per-spectrum
+                                 Chebyshev tables: once per call, every spectrum's column sums
+                                 S(theta), a^T b(theta) and their theta derivatives are
+                                 evaluated (float-float pass) at Chebyshev nodes on segments of
+                                 0.2 decades over its box [lo, hi] and interpolated (12
+                                 coefficients per segment, ~1e-14 relative); each candidate's
+                                 sums then cost O(1) per pole instead of O(K). A theta outside
+                                 the box takes a direct FP64 sweep. Same solve and tolerances
+                                 as DEBYE_PREC_MIXED; needs hi - lo <= 200 decades.
+                                 debye_eval_population_noalloc takes the direct sums. */
 
 #define DEBYE_MAX_POLES 20    /* largest N accepted */
 
@@ -90,7 +100,8 @@ typedef struct debye_ctx* debye_handle;
 
 /* Solver options. debye_default_options() fills the documented defaults. */
 typedef struct {
-  int32_t precision;      /* DEBYE_PREC_FP64, DEBYE_PREC_MIXED (default) or DEBYE_PREC_FP64_SUMS */
+  int32_t precision;      /* DEBYE_PREC_FP64, DEBYE_PREC_MIXED (default), DEBYE_PREC_FP64_SUMS
+                             or DEBYE_PREC_MIXED_TABLE */
   int32_t refine_steps;   /* FP64 precision: residual passes with refinement after the first
                              solve, 1..4 (default 1); the mixed path refines on its small
                              float-float system instead and ignores it */
@@ -239,7 +250,8 @@ int debye_fit_auto(debye_handle h, const debye_spectra* spectra, const debye_sea
  * is not NULL) for the options in `opt` (NULL = defaults), without a handle. The
  * results agree with debye_eval_population's to rounding, within the parity
  * tolerances of the cost (relative 1e-10 with DEBYE_PREC_FP64 and
- * DEBYE_PREC_FP64_SUMS, 1e-5 with DEBYE_PREC_MIXED), not bit for bit: the two entry points may split a candidate's
+ * DEBYE_PREC_FP64_SUMS, 1e-5 with DEBYE_PREC_MIXED and DEBYE_PREC_MIXED_TABLE, whose
+ * column sums are taken directly here), not bit for bit: the two entry points may split a candidate's
  * samples over different numbers of lanes, and the mixed-precision solve here is
  * always the one-thread-per-candidate kernel. It calls no cudaMalloc, cudaFree
  * or other allocating routine: all temporary data lives in one fixed scratch
@@ -308,7 +320,9 @@ int debye_sync(debye_handle h, cudaStream_t stream);
 #define DEBYE_KERNEL_GRAD_MASKED   7
 #define DEBYE_KERNEL_SUMS          8
 #define DEBYE_KERNEL_SUMS_MASKED   9
-#define DEBYE_KERNEL_KINDS         10
+#define DEBYE_KERNEL_TABLE         10  /* DEBYE_PREC_MIXED_TABLE: table build (node pass, coefficients) */
+#define DEBYE_KERNEL_TABLE_EVAL    11  /* DEBYE_PREC_MIXED_TABLE: candidates' sums from the tables */
+#define DEBYE_KERNEL_KINDS         12
 
 /* Number of kernel launches the handle has enqueued (a CUDA-graph replay counts
  * each of its kernel nodes); reset != 0 sets the counter to zero afterwards. */

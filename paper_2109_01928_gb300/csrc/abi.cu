@@ -1,6 +1,7 @@
 // Host side of libdebyefit: handle, device workspaces, work-unit scheduling and
 // the C ABI entry points declared in include/debyefit.h.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -168,6 +169,90 @@ int debye_ctx::prep_spectra(const debye_spectra* sp, const Plan& pl, cudaStream_
               (float4*)ws_kf32.p, (float4*)ws_kff.p, (double*)ws_h0.p, d_status, sms, st);
   launches += (pl.n_samples > 0) + (pl.S > 0);
   return check_launch("prep");
+}
+
+// Column-sum tables (DEBYE_PREC_MIXED_TABLE). Spectrum s gets nseg_s = ceil((hi - lo) /
+// TAB_W) segments from its lower bound; its nseg_s TAB_NC Chebyshev nodes are the poles
+// of ceil(nseg_s TAB_NC / TAB_NODE_N) pseudo-candidates of TAB_NODE_N poles, whose column
+// sums (with the derivative sums) the float-float column-sum pass computes; the
+// coefficients follow by a discrete cosine transform of the node values in FP64.
+int debye_ctx::build_tables(const debye_spectra* sp, const Plan& pl, cudaStream_t st) {
+  if (opt.precision != DEBYE_PREC_MIXED_TABLE || pl.S == 0) return DEBYE_OK;
+  const int64_t S = pl.S;
+  std::vector<double> lo(S), hi(S);
+  cudaError_t e = cudaMemcpyAsync(lo.data(), sp->lo, sizeof(double) * S, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hi.data(), sp->hi, sizeof(double) * S, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(DEBYE_ECUDA, "reading the bounds: %s", cudaGetErrorString(e));
+  std::vector<int64_t> seg0(S);
+  std::vector<int32_t> nseg(S), qn0(S + 1);
+  int64_t segs = 0, qn = 0;
+  for (int64_t s = 0; s < S; ++s) {
+    const double span = (hi[s] - lo[s]) / TAB_W;
+    if (!(span > 0.0) || !(span <= (double)TAB_MAX_SEG))
+      return fail(DEBYE_EINVAL, "spectrum %lld: the column-sum tables need lo < hi <= lo + %g decades",
+                  (long long)s, TAB_MAX_SEG * TAB_W);
+    nseg[s] = std::max(1, (int)std::ceil(span));
+    seg0[s] = segs;
+    segs += nseg[s];
+    qn0[s] = (int32_t)qn;
+    qn += (nseg[s] * TAB_NC + TAB_NODE_N - 1) / TAB_NODE_N;
+    if (qn > ((int64_t)1 << 31) - 1) return fail(DEBYE_EINVAL, "column-sum tables: too many nodes");
+  }
+  qn0[S] = (int32_t)qn;
+  int rc;
+  void *d_seg0, *d_nseg, *d_qn0, *d_th, *d_G, *d_x, *d_coef;
+  if ((rc = named("tab.seg0", sizeof(int64_t) * S, &d_seg0)) || (rc = named("tab.nseg", sizeof(int32_t) * S, &d_nseg)) ||
+      (rc = named("tab.qn0", sizeof(int32_t) * (S + 1), &d_qn0)) ||
+      (rc = named("tab.theta", sizeof(double) * TAB_NODE_N * qn, &d_th)) ||
+      (rc = named("tab.G", sizeof(double) * TAB_NF * TAB_NODE_N * qn, &d_G)) ||
+      (rc = named("tab.x", sizeof(double) * TAB_NODE_N * qn, &d_x)) ||
+      (rc = named("tab.coef", sizeof(float2) * TAB_NF * TAB_NC * segs, &d_coef)))
+    return rc;
+  e = cudaMemcpyAsync(d_seg0, seg0.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_nseg, nseg.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_qn0, qn0.data(), sizeof(int32_t) * (S + 1), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(DEBYE_ECUDA, "uploading the table plan: %s", cudaGetErrorString(e));
+  // node pass: TAB_NODE_N poles per pseudo-candidate, 16 pseudo-candidates x 8 lanes per block
+  constexpr int CBN = 16, KSN = 8;
+  Plan pn = pl;
+  std::fill(pn.npol.begin(), pn.npol.end(), TAB_NODE_N);
+  std::vector<int32_t> qb(qn0.begin(), qn0.end() - 1), qe(qn0.begin() + 1, qn0.end());
+  UnitGroups gn;
+  build_units(pn, qb, qe, CBN, gn);
+  if ((rc = upload_units(gn, ws_tab_units, st))) return rc;   // synchronises: the host plan may go
+  EvalArgs an{};
+  an.units = (const Unit*)ws_tab_units.p;
+  an.n_units = (int)gn.units.size();
+  an.theta = (const double*)d_th;
+  an.kf32 = (const float4*)ws_kf32.p;
+  an.kff = (const float4*)ws_kff.p;
+  an.kq32 = an.kf32 + pl.n_samples;
+  an.kqff = an.kff + pl.n_samples;
+  an.omega = sp->omega;
+  an.eps_re = sp->eps_re;
+  an.eps_im = sp->eps_im;
+  an.ks = KSN;
+  an.lam = opt.lam_search;
+  an.sc.Q = qn;
+  an.sc.nmax = TAB_NODE_N;
+  an.sc.G = (double*)d_G;
+  an.sc.x = (double*)d_x;
+  an.status = d_status;
+  ProfEntry pe;
+  if (prof_on) prof_begin(DEBYE_KERNEL_TABLE, 0.0, st, pe);
+  launch_tab_nodes(S, (const int32_t*)d_qn0, (const int32_t*)d_nseg, sp->lo, (double*)d_th, sms, st);
+  if (an.n_units > 0)
+    launch_pass(TAB_NODE_N, PH_SUMSG, an, std::max(1, std::min(an.n_units, sms * 16)), CBN * KSN, st);
+  launch_tab_coef(S, (const int32_t*)d_qn0, (const int32_t*)d_nseg, (const int64_t*)d_seg0, (const double*)d_G, qn,
+                  (float2*)d_coef, sms, st);
+  if (prof_on) prof_end(pe, st);
+  launches += 3;
+  tab.coef = (const float2*)d_coef;
+  tab.seg0 = (const int64_t*)d_seg0;
+  tab.nseg = (const int32_t*)d_nseg;
+  tab.lo = sp->lo;
+  return check_launch("column-sum tables");
 }
 
 // Units over candidate ranges [qb[s], qe[s]) of each spectrum, grouped by pole
@@ -339,7 +424,12 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
       launch_pass(b + 1, sph, as, grid_solve(ab.n_units), gblock, bs);
       ++launches;
     };
-    if (!prof_on) {
+    if (opt.precision == DEBYE_PREC_MIXED_TABLE) {
+      // the sums of every candidate from the tables (one launch), then the solves
+      a.tab = tab;
+      timed(DEBYE_KERNEL_TABLE_EVAL, [&] { launch_tab_eval(a, grad != nullptr, sms, st); });
+      rc = fork_buckets(prof_on ? DEBYE_KERNEL_SOLVE : -1, 0.0, nb_n, solve_bucket);
+    } else if (!prof_on) {
       rc = fork_buckets(-1, 0.0, N_BUCKETS, [&](int b, const EvalArgs& ab, cudaStream_t bs) {
         launch_bucket_pass(ph, b, ab, bs);
         solve_bucket(b, ab, bs);
@@ -396,6 +486,7 @@ static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_
   if (pl.S == 0) return DEBYE_OK;
   if (!theta || !cost) return h->fail(DEBYE_EINVAL, "theta or cost is NULL");
   if ((rc = h->prep_spectra(sp, pl, st))) return rc;
+  if ((rc = h->build_tables(sp, pl, st))) return rc;
   std::vector<int32_t> qb(pl.S), qe(pl.S);
   for (int64_t s = 0; s < pl.S; ++s) {
     qb[s] = (int32_t)(s * P);
@@ -431,7 +522,7 @@ static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_
   a.ks = ks;
   a.lam = h->opt.lam_search;
   a.status = h->d_status;
-  const bool mixed = h->opt.precision == DEBYE_PREC_MIXED;
+  const bool mixed = h->mixed();
   return h->run_eval(a, g, mixed, h->eval_steps(grad != nullptr), cost, weights, grad, sb.g1, cb, st);
 }
 
@@ -484,7 +575,8 @@ int debye_fit_init(debye_handle* out, const debye_options* opt) {
   debye_options o;
   if (opt) o = *opt;
   else debye_default_options(&o);
-  if (o.precision != DEBYE_PREC_FP64 && o.precision != DEBYE_PREC_MIXED && o.precision != DEBYE_PREC_FP64_SUMS)
+  if (o.precision != DEBYE_PREC_FP64 && o.precision != DEBYE_PREC_MIXED && o.precision != DEBYE_PREC_FP64_SUMS &&
+      o.precision != DEBYE_PREC_MIXED_TABLE)
     return DEBYE_EINVAL;
   if (o.refine_steps < 1 || o.refine_steps > 4) return DEBYE_EINVAL;
   if (!(o.lam_search >= 0.0) || !(o.lam_final >= 0.0)) return DEBYE_EINVAL;

@@ -61,6 +61,25 @@ struct Scratch {
   int32_t* fail;    // [Q] non-zero: candidate's damped matrix not positive definite
 };
 
+// Per-spectrum Chebyshev tables of the column sums (DEBYE_PREC_MIXED_TABLE). Over the
+// spectrum's log10(tau) box [lo, lo + nseg TAB_W], each column sum of one Debye pole
+// is a function of theta alone: S = sum_k re_k, h = a_i^T b and their theta
+// derivatives. Every term 1 / (1 + w_k^2 tau^2) is analytic in the strip
+// |Im ln tau^2| < pi whatever the samples, so on segments of TAB_W decades a
+// Chebyshev interpolant of degree TAB_NC - 1 reaches the float-float sums' rounding.
+constexpr double TAB_W = 0.2;    // decades of log10(tau) per segment
+constexpr int TAB_NC = 12;       // Chebyshev coefficients per segment and function
+constexpr int TAB_NF = 4;        // functions: S, h, dS/dtheta, dh/dtheta
+constexpr int TAB_NODE_N = 20;   // nodes per pseudo-candidate of the table's node pass
+constexpr int TAB_MAX_SEG = 1000;   // segments per spectrum (a box of at most 200 decades)
+
+struct TabView {
+  const float2* coef;      // [sum_s nseg_s][TAB_NF][TAB_NC] coefficients (hi, lo), c_0 halved
+  const int64_t* seg0;     // [S] first segment of spectrum s
+  const int32_t* nseg;     // [S] segments of spectrum s
+  const double* lo;        // [S] table origin: the spectrum's lower bound
+};
+
 struct EvalArgs {
   const Unit* units;
   int32_t n_units;
@@ -83,6 +102,7 @@ struct EvalArgs {
   double* out_weights;     //   nullptr, gradient [Q][nmax] (PH_SOLVEG)
   double* out_grad;
   Scratch sc;
+  TabView tab;             // DEBYE_PREC_MIXED_TABLE: the spectra's column-sum tables
   int* status;             // device status word
 };
 

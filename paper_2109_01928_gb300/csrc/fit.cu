@@ -86,9 +86,10 @@ int fit_impl(debye_handle h, const debye_spectra* sp, const debye_search* se, in
   const int64_t Q = pl.S * (int64_t)P;
   if (Q > ((int64_t)1 << 31) - 1) return h->fail(DEBYE_EINVAL, "S*P exceeds 2^31-1");
   if ((rc = h->prep_spectra(sp, pl, st))) return rc;
+  if ((rc = h->build_tables(sp, pl, st))) return rc;   // once per fit: the samples do not change
   int cb, ks;
   choose_layout(P, Q, h->sms, h->forced(), h->tuned, &cb, &ks);
-  const bool mixed = h->opt.precision == DEBYE_PREC_MIXED;
+  const bool mixed = h->mixed();
   const int nmax = n_max;
 
   // ---- swarm state and evaluation plan

@@ -69,6 +69,8 @@ struct debye_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join[debyefit::N_BUCKETS] = {nullptr};
 
   debyefit::Buf ws_kf32, ws_kff, ws_h0, ws_units;
+  debyefit::Buf ws_tab_units;    // units of the column-sum tables' node pass
+  debyefit::TabView tab{};       // column-sum tables of the current call (DEBYE_PREC_MIXED_TABLE)
   debyefit::ScratchBufs sb_eval, sb_polish, sb_polish_acc, sb_final;
   std::map<std::string, debyefit::Buf> named_bufs;  // swarm / polish / result state
 
@@ -104,6 +106,11 @@ struct debye_ctx {
   int run_eval(debyefit::EvalArgs a, const debyefit::UnitGroups& g, bool mixed, int steps,
                double* cost, double* weights, double* grad, double* g1, int cb, cudaStream_t st);
   int eval_steps(bool with_grad) const;
+  // Mixed precision: column sums and the Gram identity (direct or tabulated sums).
+  bool mixed() const { return opt.precision == DEBYE_PREC_MIXED || opt.precision == DEBYE_PREC_MIXED_TABLE; }
+  // DEBYE_PREC_MIXED_TABLE: build every spectrum's column-sum tables (after
+  // prep_spectra) and point `tab` at them; a no-op for the other precisions.
+  int build_tables(const debye_spectra* sp, const debyefit::Plan& pl, cudaStream_t st);
   int named(const char* name, size_t bytes, void** out);
 
   void free_buf(debyefit::Buf& b) {
@@ -116,6 +123,7 @@ struct debye_ctx {
     free_buf(ws_kff);
     free_buf(ws_h0);
     free_buf(ws_units);
+    free_buf(ws_tab_units);
     for (debyefit::ScratchBufs* sb : {&sb_eval, &sb_polish, &sb_polish_acc, &sb_final}) {
       free_buf(sb->G);
       free_buf(sb->L);

@@ -144,8 +144,9 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
   debye_options opt;
   if (opt_in) opt = *opt_in;
   else debye_default_options(&opt);
-  if (opt.precision != DEBYE_PREC_FP64 && opt.precision != DEBYE_PREC_MIXED && opt.precision != DEBYE_PREC_FP64_SUMS)
-    return fail_msg(DEBYE_EINVAL, err, err_len, "precision must be DEBYE_PREC_FP64, _MIXED or _FP64_SUMS");
+  if (opt.precision != DEBYE_PREC_FP64 && opt.precision != DEBYE_PREC_MIXED && opt.precision != DEBYE_PREC_FP64_SUMS &&
+      opt.precision != DEBYE_PREC_MIXED_TABLE)
+    return fail_msg(DEBYE_EINVAL, err, err_len, "precision must be DEBYE_PREC_FP64, _MIXED, _FP64_SUMS or _MIXED_TABLE");
   if (opt.refine_steps < 1 || opt.refine_steps > 4 || !(opt.lam_search >= 0.0))
     return fail_msg(DEBYE_EINVAL, err, err_len, "refine_steps outside 1..4 or negative lam_search");
   if (!sp) return fail_msg(DEBYE_EINVAL, err, err_len, "spectra is NULL");
@@ -280,7 +281,7 @@ extern "C" int debye_eval_population_noalloc(const debye_options* opt_in, const 
   a.lam = opt.lam_search;
   a.sc = sc;
   a.status = status;
-  const bool mixed = opt.precision == DEBYE_PREC_MIXED;
+  const bool mixed = opt.precision == DEBYE_PREC_MIXED || opt.precision == DEBYE_PREC_MIXED_TABLE;   // direct sums
   auto per_bucket = [&](int phase) {
     for (int b = 0; b < N_BUCKETS; ++b) {
       const int n = begin[b + 1] - begin[b];

@@ -28,7 +28,9 @@ DEBYE_EBOUNDS = -7
 PREC_FP64 = 0
 PREC_MIXED = 1
 PREC_FP64_SUMS = 2
-PRECISIONS = {"mixed": PREC_MIXED, "fp64": PREC_FP64, "fp64_sums": PREC_FP64_SUMS}
+PREC_MIXED_TABLE = 3
+PRECISIONS = {"mixed": PREC_MIXED, "fp64": PREC_FP64, "fp64_sums": PREC_FP64_SUMS,
+              "mixed_table": PREC_MIXED_TABLE}
 SEARCH_PSO = 0
 SEARCH_DE = 1
 SEARCH_DA = 2
@@ -149,7 +151,7 @@ def default_options() -> Options:
 
 
 class Handle:
-    """debye_handle with its options (precision 'mixed', 'fp64' or 'fp64_sums')."""
+    """debye_handle with its options (precision 'mixed', 'fp64', 'fp64_sums' or 'mixed_table')."""
 
     def __init__(self, precision: str = "mixed", **opts):
         o = default_options()
@@ -336,7 +338,8 @@ def debye_sync(h: Handle, stream=None):
 
 
 KERNEL_KINDS = {"gram": 0, "refine": 1, "grad": 2, "solve": 3, "finish": 4, "gram_masked": 5,
-                "refine_masked": 6, "grad_masked": 7, "sums": 8, "sums_masked": 9}
+                "refine_masked": 6, "grad_masked": 7, "sums": 8, "sums_masked": 9, "table": 10,
+                "table_eval": 11}
 
 
 def debye_eval_population_noalloc(sp: Spectra, theta, precision: str = "mixed", weights: bool = False,

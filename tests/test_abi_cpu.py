@@ -28,6 +28,21 @@ def test_exports_every_declared_function(lib):
         assert hasattr(lib, n), f"{n} declared in include/debyefit.h but not exported"
 
 
+def header_defines(prefix):
+    import re
+    text = open(os.path.join(ROOT, "include", "debyefit.h")).read()
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (" + prefix + r"\w+)\s+(-?\d+)", text)}
+
+
+def test_binding_constants_match_header():
+    prec = header_defines("DEBYE_PREC_")
+    assert prec == {"DEBYE_PREC_" + k.upper(): v for k, v in D.PRECISIONS.items()}
+    kinds = header_defines("DEBYE_KERNEL_")
+    n = kinds.pop("DEBYE_KERNEL_KINDS")
+    assert kinds == {"DEBYE_KERNEL_" + k.upper(): v for k, v in D.KERNEL_KINDS.items()}
+    assert sorted(kinds.values()) == list(range(n))
+
+
 def test_default_options(lib):
     o = D.default_options()
     assert o.precision == D.PREC_MIXED and o.refine_steps == 1

@@ -16,14 +16,14 @@ from oracle import dls, fit, models, varpro
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-COST_TOL = {"fp64": 1e-10, "fp64_sums": 1e-10, "mixed": 1e-5}
-GRAD_TOL = {"fp64": 1e-8, "fp64_sums": 1e-8, "mixed": 1e-4}
+COST_TOL = {"fp64": 1e-10, "fp64_sums": 1e-10, "mixed": 1e-5, "mixed_table": 1e-5}
+GRAD_TOL = {"fp64": 1e-8, "fp64_sums": 1e-8, "mixed": 1e-4, "mixed_table": 1e-4}
 # Weights, relative to the largest weight of the candidate. The cost is stationary
 # in the weights, the weights are not: FP64 carries the Cholesky solve's rounding
 # (~1e-13 of the scale at the damped condition number kappa <= (n + lam)/lam);
 # mixed precision the FP32 factor's error after one refinement step,
 # (kappa 2^-24)^2 ~ 1.6e-6 at n = 21, lam = 1e-3.
-WEIGHT_TOL = {"fp64": 1e-10, "fp64_sums": 1e-10, "mixed": 1e-5}
+WEIGHT_TOL = {"fp64": 1e-10, "fp64_sums": 1e-10, "mixed": 1e-5, "mixed_table": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -81,8 +81,10 @@ def test_synth_matches_oracle(D):
 # ------------------------------------------------------------------ per-candidate cost
 
 # the mixed path's small-system solve in both forms: one thread per candidate
-# (solve_lanes 1) and one warp per candidate (32, the default at these sizes)
-PREC_LANES = [("fp64", 0), ("fp64_sums", 0), ("mixed", 1), ("mixed", 32)]
+# (solve_lanes 1) and one warp per candidate (32, the default at these sizes), with
+# the column sums swept directly (mixed) and read from the Chebyshev tables (mixed_table)
+PREC_LANES = [("fp64", 0), ("fp64_sums", 0), ("mixed", 1), ("mixed", 32), ("mixed_table", 1),
+              ("mixed_table", 32)]
 
 
 @pytest.mark.parametrize("prec,lanes", PREC_LANES)
@@ -106,8 +108,9 @@ def test_eval_population_ragged(D, prec, lanes):
         assert np.all(w[s, :, b.n_poles[s] + 1:] == 0)
 
 
+@pytest.mark.parametrize("prec", ["mixed", "mixed_table"])
 @pytest.mark.parametrize("cb", [32, 128])
-def test_eval_one_lane_per_candidate_every_n(D, cb):
+def test_eval_one_lane_per_candidate_every_n(D, cb, prec):
     # a forced block size gives one lane per candidate (the full-population layout): the
     # column-sum solve then runs per pole count with the system in registers for N up to
     # 12, and in the general kernel above; costs, weights and gradients for N = 1..20
@@ -116,14 +119,14 @@ def test_eval_one_lane_per_candidate_every_n(D, cb):
     th = W.population(b, 70, seed=9)
     ref, wref = oracle_costs(b, re, im, th)
     sp = spectra_for(D, b, re, im)
-    with D.Handle("mixed", cands_per_block=cb) as h:
+    with D.Handle(prec, cands_per_block=cb) as h:
         cost, w = D.debye_eval_population(h, sp, torch.as_tensor(th, device="cuda"), weights=True)
         cost2, grad = D.debye_cost_grad(h, sp, torch.as_tensor(th, device="cuda"))
         D.debye_sync(h)
     cost, w, cost2, grad = cost.cpu().numpy(), w.cpu().numpy(), cost2.cpu().numpy(), grad.cpu().numpy()
-    assert (np.abs(cost - ref) / ref).max() <= COST_TOL["mixed"]
-    assert (np.abs(cost2 - ref) / ref).max() <= COST_TOL["mixed"]
-    assert (np.abs(w - wref) / np.abs(wref).max(axis=2, keepdims=True)).max() <= WEIGHT_TOL["mixed"]
+    assert (np.abs(cost - ref) / ref).max() <= COST_TOL[prec]
+    assert (np.abs(cost2 - ref) / ref).max() <= COST_TOL[prec]
+    assert (np.abs(w - wref) / np.abs(wref).max(axis=2, keepdims=True)).max() <= WEIGHT_TOL[prec]
     checked = 0
     for s in range(b.S):
         a, c = b.offsets[s], b.offsets[s + 1]
@@ -134,9 +137,50 @@ def test_eval_one_lane_per_candidate_every_n(D, cb):
             if np.min(np.abs(x[1:])) < 1e-6 * np.abs(x).max():
                 continue
             _, gref = varpro.cost_grad(b.omega[a:c], re[a:c], im[a:c], th[s, p, :N])
-            assert np.linalg.norm(grad[s, p, :N] - gref) <= GRAD_TOL["mixed"] * np.linalg.norm(gref), (s, p)
+            assert np.linalg.norm(grad[s, p, :N] - gref) <= GRAD_TOL[prec] * np.linalg.norm(gref), (s, p)
             checked += 1
     assert checked >= 100
+
+
+@pytest.mark.parametrize("lanes", [1, 32])
+def test_table_box_edges_and_outside(D, lanes):
+    # The column-sum tables cover [lo, lo + 0.2 ceil((hi - lo) / 0.2)] decades: boxes
+    # narrower than one segment and spans that are no multiple of it; poles exactly on
+    # the bounds; and poles outside the box, which take a direct FP64 sweep. Costs,
+    # weights and gradients against the oracle.
+    b = W.mixed_batch(S=6, seed=23, P=40, K_range=(30, 400), N_range=(2, 8))
+    b.lo[:] = [-13.0, -11.0, -9.05, -12.0, -10.0, -8.0]
+    b.hi[:] = [-5.0, -10.93, -8.97, -4.71, -9.999, -6.66]
+    re, im = models.synthesize(b)
+    th = W.population(b, 40, seed=4)
+    th[:, 0, 0] = b.lo
+    th[:, 1, 0] = b.hi
+    th[:, 2, 1] = b.lo - 1.0
+    th[:, 3, 0] = b.hi + 0.5
+    for s in range(b.S):
+        th[s, 4, :b.n_poles[s]] = b.hi[s] + 2.0 + 0.1 * np.arange(b.n_poles[s])
+    ref, wref = oracle_costs(b, re, im, th)
+    sp = spectra_for(D, b, re, im)
+    with D.Handle("mixed_table", solve_lanes=lanes) as h:
+        cost, w = D.debye_eval_population(h, sp, torch.as_tensor(th, device="cuda"), weights=True)
+        cost2, grad = D.debye_cost_grad(h, sp, torch.as_tensor(th, device="cuda"))
+        D.debye_sync(h)
+    cost, w, cost2, grad = cost.cpu().numpy(), w.cpu().numpy(), cost2.cpu().numpy(), grad.cpu().numpy()
+    assert (np.abs(cost - ref) / ref).max() <= COST_TOL["mixed_table"]
+    assert (np.abs(cost2 - ref) / ref).max() <= COST_TOL["mixed_table"]
+    assert (np.abs(w - wref) / np.abs(wref).max(axis=2, keepdims=True)).max() <= WEIGHT_TOL["mixed_table"]
+    checked = 0
+    for s in range(b.S):
+        a, c = b.offsets[s], b.offsets[s + 1]
+        N = int(b.n_poles[s])
+        for p in range(10):
+            x = wref[s, p, :N + 1]
+            if np.min(np.abs(x[1:])) < 1e-6 * np.abs(x).max():
+                continue
+            _, gref = varpro.cost_grad(b.omega[a:c], re[a:c], im[a:c], th[s, p, :N])
+            assert np.linalg.norm(grad[s, p, :N] - gref) <= GRAD_TOL["mixed_table"] * np.linalg.norm(gref), (s, p)
+            checked += 1
+    assert checked >= 20
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -151,7 +195,7 @@ def test_eval_block_sizes(D, prec, cb):
     assert (np.abs(cost.cpu().numpy() - ref) / ref).max() <= COST_TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp64_sums", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64_sums", "mixed", "mixed_table"])
 def test_eval_full_size_sampled(D, prec):
     # the 1024-spectrum workload at full population, checked on a seeded sample
     b = W.workload("mixed_1024")
@@ -449,7 +493,7 @@ def test_fit_fp64_swarm_trace_matches_oracle(D, prec):
     assert out["evals"].item() == 64 * 101 * 50
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp64_sums", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64_sums", "mixed", "mixed_table"])
 def test_fit_with_polish_matches_oracle(D, prec):
     # Every spectrum: the fitted spectrum within 1e-4 relative RMS of the oracle's,
     # or a final cost at most the oracle's x (1 + 1e-6). FP64 follows the oracle's
@@ -470,7 +514,7 @@ def test_fit_with_polish_matches_oracle(D, prec):
         e_gpu = fitted(b.omega[a:c], out["eps_inf"][s].item(), out["d_eps"][s, :N].cpu().numpy(),
                        out["tau"][s, :N].cpu().numpy())
         gcost = out["final_cost"][s].item()
-        if prec != "mixed":
+        if not prec.startswith("mixed"):
             r = fit_oracle(b, re, im, s, 64, 60, 8, 40)
             assert fitcheck.agree(e_gpu, gcost, fit.fitted_eps(b.omega[a:c], r), r["cost_final"]), \
                 (s, dls.rel_rms(e_gpu, fit.fitted_eps(b.omega[a:c], r)), gcost, r["cost_final"])
