@@ -501,9 +501,21 @@ def config_tabulated(D, torch, dev, flush):
         res["value"] = r["evals"][0] / (r["times"][0] * 1e-3)
         res["unit"] = UNIT
         res["cand_k_per_step"] = r["evals"][0]
+        out_direct = host_out(r["out"])     # before the profiled run reuses the output buffers
         prof = profile(D, h, lambda: bn.fit(h, r["out"], iters=2, topk=0))
         res["roofline"] = roofline_mixed(bn, prof, "sums_tabulated_16384_k4096")
         res["per_kind_ms_3_generations"] = per_kind_ms(prof)
+    del r
+    with D.Handle("mixed_table") as h:
+        rt = timed_fits(bn, h, 1, 1, flush, warm_iters=1)
+        res["mixed_table"] = {"ms_per_step": float(rt["times"][0]), "unit": UNIT,
+                              "value": rt["evals"][0] / (rt["times"][0] * 1e-3),
+                              "speedup_over_direct_mixed": res["ms_per_step"] / float(rt["times"][0]),
+                              "fit_agreement_vs_direct_mixed": {
+                                  k: v for k, v in fit_agreement(bn.b, host_out(rt["out"]), out_direct).items()
+                                  if k != "fit_error_vs_target"}}
+        prof = profile(D, h, lambda: bn.fit(h, rt["out"], iters=2, topk=0))
+        res["mixed_table"]["per_kind_ms_3_generations"] = per_kind_ms(prof)
     return res
 
 
@@ -532,6 +544,30 @@ def fp64_arm(D, torch, bn: Bench, precision: str, steps: int, flush, red, mixed_
              "speedup_mixed_over_this": mixed_value / v, "roofline": roof}, out)
 
 
+def table_arm(D, torch, bn: Bench, steps: int, warmup: int, flush, red, mixed_value, out_mixed, out_fp64):
+    """The mixed path with the column sums read from per-spectrum Chebyshev tables
+    (DEBYE_PREC_MIXED_TABLE) on the headline fit: rate over `steps` timed fits, the
+    per-kind breakdown of one fit (kernel timing on), and the agreement of its fitted
+    spectra with the FP64 fit and with the direct mixed fit."""
+    h = D.Handle("mixed_table")
+    tuned = D.debye_autotune(h, bn.sp, bn.population(2))
+    r = timed_fits(bn, h, steps, warmup, flush, red.barrier)
+    v = red.sum(sum(r["evals"])) / red.max(sum(r["times"]) * 1e-3)
+    out = host_out(r["out"])
+    prof = profile(D, h, lambda: bn.fit(h, r["out"]))
+    h.close()
+    res = {"value": v, "unit": UNIT, "ms_per_step": float(np.mean(r["times"])), "steps": steps,
+           "speedup_over_direct_mixed": v / mixed_value, "autotune": tuned, "per_kind_ms": per_kind_ms(prof),
+           "what": "column sums S, a^T b and their theta derivatives of every pole interpolated from "
+                   "per-spectrum Chebyshev tables (0.2-decade segments, 12 coefficients, built once per "
+                   "fit from float-float node sums); same solve, cost and search as the direct mixed path"}
+    if out_fp64 is not None:
+        res["fit_agreement"] = fit_agreement(bn.b, out, out_fp64)
+    res["fit_agreement_vs_direct_mixed"] = {
+        k: v_ for k, v_ in fit_agreement(bn.b, out, out_mixed).items() if k != "fit_error_vs_target"}
+    return res
+
+
 # ------------------------------------------------------------------ main
 
 def main():
@@ -544,6 +580,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-table", action="store_true", help="skip the Chebyshev-table arm")
     ap.add_argument("--split", action="store_true",
                     help="with N > 1: split the one seed-0 batch across the ranks by work weight (strong "
                          "scaling) instead of one replica batch per rank (weak scaling, the default)")
@@ -671,6 +708,10 @@ def main():
         fp64_sums["fit_agreement_vs_fp64"] = {
             k: v for k, v in fit_agreement(b, out_sums, out_fp64).items() if k != "fit_error_vs_target"}
     hm.close()
+    table = None
+    if not args.no_table:
+        table = table_arm(D, torch, bn, args.steps, args.warmup, flush, red, value, out_mixed,
+                          None if args.no_fp64 else out_fp64)
 
     extra = {}
     if rank == 0 and world == 1:
@@ -710,6 +751,7 @@ def main():
         "cpu_baseline": cpu,
         "fp64_plain": fp64,
         "fp64_sums": fp64_sums,
+        "mixed_table": table,
         "eval_batching": batching,
         "configs": extra,
     }

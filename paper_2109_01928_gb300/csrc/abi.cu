@@ -205,7 +205,7 @@ int debye_ctx::build_tables(const debye_spectra* sp, const Plan& pl, cudaStream_
   if ((rc = named("tab.seg0", sizeof(int64_t) * S, &d_seg0)) || (rc = named("tab.nseg", sizeof(int32_t) * S, &d_nseg)) ||
       (rc = named("tab.qn0", sizeof(int32_t) * (S + 1), &d_qn0)) ||
       (rc = named("tab.theta", sizeof(double) * TAB_NODE_N * qn, &d_th)) ||
-      (rc = named("tab.G", sizeof(double) * TAB_NF * TAB_NODE_N * qn, &d_G)) ||
+      (rc = named("tab.G", sizeof(double) * 4 * TAB_NODE_N * qn, &d_G)) ||
       (rc = named("tab.x", sizeof(double) * TAB_NODE_N * qn, &d_x)) ||
       (rc = named("tab.coef", sizeof(float2) * TAB_NF * TAB_NC * segs, &d_coef)))
     return rc;
@@ -244,8 +244,8 @@ int debye_ctx::build_tables(const debye_spectra* sp, const Plan& pl, cudaStream_
   launch_tab_nodes(S, (const int32_t*)d_qn0, (const int32_t*)d_nseg, sp->lo, (double*)d_th, sms, st);
   if (an.n_units > 0)
     launch_pass(TAB_NODE_N, PH_SUMSG, an, std::max(1, std::min(an.n_units, sms * 16)), CBN * KSN, st);
-  launch_tab_coef(S, (const int32_t*)d_qn0, (const int32_t*)d_nseg, (const int64_t*)d_seg0, (const double*)d_G, qn,
-                  (float2*)d_coef, sms, st);
+  launch_tab_coef(S, (const int32_t*)d_qn0, (const int32_t*)d_nseg, (const int64_t*)d_seg0, (const double*)d_G,
+                  (const double*)d_x, qn, (float2*)d_coef, sms, st);
   if (prof_on) prof_end(pe, st);
   launches += 3;
   tab.coef = (const float2*)d_coef;
@@ -469,12 +469,19 @@ int debye_ctx::run_eval(EvalArgs a, const UnitGroups& g, bool mixed, int steps, 
   return DEBYE_OK;
 }
 
-// Common path of debye_eval_population / debye_cost_grad.
-static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n_max,
-                      const double* theta, double* cost, double* weights, double* grad,
-                      int32_t* n_failed, cudaStream_t st) {
-  if (!h) return DEBYE_EINVAL;
-  h->err.clear();
+// The device-side plan of one evaluation of debye_eval_population / debye_cost_grad:
+// the work units are on the device and `a` holds the arguments; h->run_eval launches
+// it (device work only, no host synchronisation). empty: nothing to evaluate.
+struct EvalSetup {
+  EvalArgs a{};
+  UnitGroups g;
+  int cb = 0;
+  bool empty = false;
+};
+
+// Validate, plan and upload one evaluation; `layout` (cb > 0) replaces the layout rule.
+static int setup_eval(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n_max, const double* theta,
+                      const double* cost, int32_t* n_failed, Layout layout, cudaStream_t st, EvalSetup& es) {
   if (P < 1) return h->fail(DEBYE_EINVAL, "P = %d < 1", P);
   if (n_max < 1 || n_max > NMAX) return h->fail(DEBYE_EINVAL, "n_max = %d outside 1..%d", n_max, NMAX);
   if (!sp) return h->fail(DEBYE_EINVAL, "spectra is NULL");
@@ -483,7 +490,8 @@ static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_
   Plan pl;
   if ((rc = h->load_plan(sp, pl, st))) return rc;
   if (pl.nmax_seen > n_max) return h->fail(DEBYE_EINVAL, "n_max = %d < largest N = %d", n_max, pl.nmax_seen);
-  if (pl.S == 0) return DEBYE_OK;
+  es.empty = pl.S == 0;
+  if (es.empty) return DEBYE_OK;
   if (!theta || !cost) return h->fail(DEBYE_EINVAL, "theta or cost is NULL");
   if ((rc = h->prep_spectra(sp, pl, st))) return rc;
   if ((rc = h->build_tables(sp, pl, st))) return rc;
@@ -493,19 +501,18 @@ static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_
     qe[s] = (int32_t)((s + 1) * P);
   }
   int cb, ks;
-  if (h->layout_override.cb > 0) {
-    cb = h->layout_override.cb;
-    ks = h->layout_override.ks;
+  if (layout.cb > 0) {
+    cb = layout.cb;
+    ks = layout.ks;
   } else {
     choose_layout(P, pl.S * (int64_t)P, h->sms, h->forced(), h->tuned, &cb, &ks);
   }
-  UnitGroups g;
-  build_units(pl, qb, qe, cb, g);
-  if ((rc = h->upload_units(g, h->ws_units, st))) return rc;
-  ScratchBufs& sb = h->sb_eval;
-  EvalArgs a{};
+  build_units(pl, qb, qe, cb, es.g);
+  if ((rc = h->upload_units(es.g, h->ws_units, st))) return rc;
+  EvalArgs& a = es.a;
+  a = EvalArgs{};
   const int64_t Q = pl.S * (int64_t)P;
-  if ((rc = h->ensure_scratch(Q, n_max, sb, a.sc))) return rc;
+  if ((rc = h->ensure_scratch(Q, n_max, h->sb_eval, a.sc))) return rc;
   a.units = (const Unit*)h->ws_units.p;
   a.theta = theta;
   a.kf32 = (const float4*)h->ws_kf32.p;
@@ -522,8 +529,25 @@ static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_
   a.ks = ks;
   a.lam = h->opt.lam_search;
   a.status = h->d_status;
-  const bool mixed = h->mixed();
-  return h->run_eval(a, g, mixed, h->eval_steps(grad != nullptr), cost, weights, grad, sb.g1, cb, st);
+  es.cb = cb;
+  return DEBYE_OK;
+}
+
+static int run_setup(debye_handle h, EvalSetup& es, double* cost, double* weights, double* grad, cudaStream_t st) {
+  if (es.empty) return DEBYE_OK;
+  return h->run_eval(es.a, es.g, h->mixed(), h->eval_steps(grad != nullptr), cost, weights, grad, h->sb_eval.g1,
+                     es.cb, st);
+}
+
+// Common path of debye_eval_population / debye_cost_grad.
+static int eval_entry(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n_max,
+                      const double* theta, double* cost, double* weights, double* grad,
+                      int32_t* n_failed, cudaStream_t st) {
+  if (!h) return DEBYE_EINVAL;
+  h->err.clear();
+  EvalSetup es;
+  int rc = setup_eval(h, sp, P, n_max, theta, cost, n_failed, Layout{}, st, es);
+  return rc ? rc : run_setup(h, es, cost, weights, grad, st);
 }
 
 // Refinement passes of an evaluation. With the mixed precision the gradient is
@@ -725,39 +749,44 @@ int debye_autotune(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n
     cudaGetLastError();
     return h->fail(DEBYE_ECUDA, "event creation failed");
   }
-  // time one evaluation (after a warm-up) of the given layout; eval() runs it
-  auto time_layout = [&](Layout l, auto eval, float* ms) -> int {
-    h->layout_override = l;
-    int rc = eval();
-    float tot = 0.f;
-    for (int rep = 0; rep < 2 && rc == DEBYE_OK; ++rep) {
-      cudaEventRecord(e0, st);
-      rc = eval();
-      cudaEventRecord(e1, st);
-      cudaEventSynchronize(e1);
-      float t = 0.f;
-      cudaEventElapsedTime(&t, e0, e1);
-      tot += t;
+  // Median device time of one evaluation per layout: every round plans each layout
+  // (host work and upload, outside the timed region), then times its launches alone
+  // between events; rounds interleave the layouts so that clock drift favours none.
+  constexpr int ROUNDS = 5;
+  auto tune = [&](const Layout* set, int n_set, int32_t Pe, const double* th, double* c, double* gr,
+                  Layout* best) -> int {
+    std::vector<float> t((size_t)n_set * ROUNDS, 0.f);
+    for (int round = -1; round < ROUNDS; ++round) {   // round -1: warm-up (workspaces, caches)
+      for (int li = 0; li < n_set; ++li) {
+        EvalSetup es;
+        int r = setup_eval(h, sp, Pe, n_max, th, c, nullptr, set[li], st, es);
+        if (r) return r;
+        cudaEventRecord(e0, st);
+        if ((r = run_setup(h, es, c, nullptr, gr, st))) return r;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return h->fail(DEBYE_ECUDA, "autotune timing failed");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (round >= 0) t[(size_t)li * ROUNDS + round] = ms;
+      }
     }
-    h->layout_override = Layout{};
-    *ms = tot;
-    return rc;
+    float best_ms = 0.f;
+    for (int li = 0; li < n_set; ++li) {
+      std::vector<float> v(t.begin() + (size_t)li * ROUNDS, t.begin() + (size_t)(li + 1) * ROUNDS);
+      std::nth_element(v.begin(), v.begin() + ROUNDS / 2, v.end());
+      const float med = v[ROUNDS / 2];
+      if (!best->cb || med < best_ms) {
+        *best = set[li];
+        best_ms = med;
+      }
+    }
+    return DEBYE_OK;
   };
   int rc = DEBYE_OK;
-  // full population: the caller's batch, cost only (the swarm's evaluations)
   Layout best_full, best_pol;
-  float best_ms = 0.f;
+  // full population: the caller's batch, cost only (the swarm's evaluations)
   static const Layout full_set[] = {{32, 1}, {64, 1}, {96, 1}, {128, 1}, {32, 2}, {64, 2}, {32, 4}};
-  for (const Layout& l : full_set) {
-    float ms = 0.f;
-    rc = time_layout(l, [&] { return debye_eval_population(h, sp, P, n_max, theta, cost, nullptr, nullptr, st); },
-                     &ms);
-    if (rc) break;
-    if (!best_full.cb || ms < best_ms) {
-      best_full = l;
-      best_ms = ms;
-    }
-  }
+  rc = tune(full_set, (int)(sizeof(full_set) / sizeof(full_set[0])), P, theta, cost, nullptr, &best_full);
   // the polish's accepted points: the first T = min(P, 8) candidates of every spectrum with
   // their gradient, over a range of lane splits
   const int T = std::min(P, 8);
@@ -770,19 +799,9 @@ int debye_autotune(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n
       if (e != cudaSuccess) rc = h->fail(DEBYE_ECUDA, "autotune copy: %s", cudaGetErrorString(e));
     }
     static const Layout pol_set[] = {{16, 4}, {8, 8}, {4, 16}, {2, 32}, {32, 4}, {16, 8}, {8, 16}, {4, 32}};
-    best_ms = 0.f;
-    for (const Layout& l : pol_set) {
-      if (rc) break;
-      float ms = 0.f;
-      rc = time_layout(l, [&] {
-        return debye_cost_grad(h, sp, T, n_max, (const double*)pt, (double*)pc, (double*)pg, nullptr, st);
-      }, &ms);
-      if (rc) break;
-      if (!best_pol.cb || ms < best_ms) {
-        best_pol = l;
-        best_ms = ms;
-      }
-    }
+    if (!rc)
+      rc = tune(pol_set, (int)(sizeof(pol_set) / sizeof(pol_set[0])), T, (const double*)pt, (double*)pc,
+                (double*)pg, &best_pol);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -64,17 +64,22 @@ struct Scratch {
 // Per-spectrum Chebyshev tables of the column sums (DEBYE_PREC_MIXED_TABLE). Over the
 // spectrum's log10(tau) box [lo, lo + nseg TAB_W], each column sum of one Debye pole
 // is a function of theta alone: S = sum_k re_k, h = a_i^T b and their theta
-// derivatives. Every term 1 / (1 + w_k^2 tau^2) is analytic in the strip
+// derivatives (tau = 10^theta is tabulated with them). Every term 1 / (1 + w_k^2 tau^2) is analytic in the strip
 // |Im ln tau^2| < pi whatever the samples, so on segments of TAB_W decades a
 // Chebyshev interpolant of degree TAB_NC - 1 reaches the float-float sums' rounding.
 constexpr double TAB_W = 0.2;    // decades of log10(tau) per segment
+constexpr double TAB_INV_W = 5.0;   // 1 / TAB_W
 constexpr int TAB_NC = 12;       // Chebyshev coefficients per segment and function
-constexpr int TAB_NF = 4;        // functions: S, h, dS/dtheta, dh/dtheta
+// Functions per segment: S, h and tau = 10^theta itself (an entire function, so its
+// series converges faster still), which the cost needs, then dS/dtheta and dh/dtheta
+// for the gradient.
+constexpr int TAB_NF = 5;
 constexpr int TAB_NODE_N = 20;   // nodes per pseudo-candidate of the table's node pass
 constexpr int TAB_MAX_SEG = 1000;   // segments per spectrum (a box of at most 200 decades)
 
 struct TabView {
-  const float2* coef;      // [sum_s nseg_s][TAB_NF][TAB_NC] coefficients (hi, lo), c_0 halved
+  const float2* coef;      // [sum_s nseg_s][TAB_NF][TAB_NC] coefficients (hi, lo), c_0 halved;
+                           //   functions S, h, tau, dS/dtheta, dh/dtheta
   const int64_t* seg0;     // [S] first segment of spectrum s
   const int32_t* nseg;     // [S] segments of spectrum s
   const double* lo;        // [S] table origin: the spectrum's lower bound

@@ -83,7 +83,6 @@ struct debye_ctx {
   int64_t launches = 0;  // kernel launches enqueued (graph replays count every node)
   debyefit::Layout tuned;         // full-population layout chosen by debye_autotune (unset: not tuned)
   debyefit::Layout tuned_polish;  // layout of the polish's accepted points (debye_autotune)
-  debyefit::Layout layout_override;  // set by debye_autotune while it times a layout
   debyefit::Layout forced() const { return debyefit::Layout{opt.cands_per_block, opt.lanes_per_candidate}; }
   bool prof_on = false;
   std::vector<ProfEntry> prof_pending;

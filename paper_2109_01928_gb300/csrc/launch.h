@@ -94,12 +94,12 @@ void launch_grad_finish(const EvalArgs& a, double* grad, int block, int sms, cud
 namespace debyefit {
 // Column-sum tables (tables.cu, DEBYE_PREC_MIXED_TABLE). Nodes: theta of every node of
 // every spectrum's table into theta_n[qn0[S]][TAB_NODE_N]; coefficients from the node
-// pass's sums G[4 TAB_NODE_N][Qn]; eval: the units' column sums (and with grad their
+// pass's sums G[4 TAB_NODE_N][Qn] and taus X[TAB_NODE_N][Qn]; eval: the units' column sums (and with grad their
 // theta derivatives) from a.tab into a.sc.x / a.sc.G, as the column-sum pass writes them.
 void launch_tab_nodes(int64_t S, const int32_t* qn0, const int32_t* nseg, const double* lo, double* theta_n,
                       int sms, cudaStream_t st);
 void launch_tab_coef(int64_t S, const int32_t* qn0, const int32_t* nseg, const int64_t* seg0, const double* G,
-                     int64_t Qn, float2* coef, int sms, cudaStream_t st);
+                     const double* X, int64_t Qn, float2* coef, int sms, cudaStream_t st);
 void launch_tab_eval(const EvalArgs& a, bool grad, int sms, cudaStream_t st);
 void launch_synth(int64_t S, const int64_t* offsets, const double* omega, const int32_t* model,
                   const double* params, const int64_t* pole_off, const double* ptau,

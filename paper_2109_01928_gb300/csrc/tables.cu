@@ -60,11 +60,12 @@ __global__ void k_tab_nodes(int64_t S, const int32_t* qn0, const int32_t* nseg, 
   }
 }
 
-// Coefficients of segment g and function f of spectrum s from the node pass's sums:
+// Coefficients of segment g and function f of spectrum s from the node pass's output:
 // for node n, pseudo-candidate q = qn0[s] + n / TAB_NODE_N and pole i = n % TAB_NODE_N,
-// the column-sum pass wrote function f at G[(f TAB_NODE_N + i) Qn + q] (S, h, dS, dh).
+// the column-sum pass wrote S, h, dS, dh at G[(r TAB_NODE_N + i) Qn + q], r = 0..3, and
+// tau at X[i Qn + q].
 __global__ void k_tab_coef(int64_t S, const int32_t* qn0, const int32_t* nseg, const int64_t* seg0,
-                           ChebConst cc, const double* G, int64_t Qn, float2* coef) {
+                           ChebConst cc, const double* G, const double* X, int64_t Qn, float2* coef) {
   for (int64_t s = blockIdx.x; s < S; s += gridDim.x) {
     const int items = nseg[s] * TAB_NF;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
@@ -74,7 +75,8 @@ __global__ void k_tab_coef(int64_t S, const int32_t* qn0, const int32_t* nseg, c
       for (int m = 0; m < TAB_NC; ++m) {
         const int n = g * TAB_NC + m;
         const int64_t q = qn0[s] + n / TAB_NODE_N;
-        v[m] = G[(int64_t)(f * TAB_NODE_N + n % TAB_NODE_N) * Qn + q];
+        const int i = n % TAB_NODE_N;
+        v[m] = f == 2 ? X[(int64_t)i * Qn + q] : G[(int64_t)((f < 2 ? f : f - 1) * TAB_NODE_N + i) * Qn + q];
       }
       float2* out = coef + ((seg0[s] + g) * TAB_NF + f) * TAB_NC;
 #pragma unroll
@@ -151,20 +153,23 @@ __global__ void __launch_bounds__(128) k_tab_eval(EvalArgs a) {
       const int j = p / nc, q = u.q0 + p % nc;
       if (a.active && !a.active[q]) continue;
       const double th = a.theta[(int64_t)q * a.sc.nmax + j];
-      const double tau = exp10(th);
-      const double uu = (th - l) / TAB_W;
-      double v[4] = {0.0, 0.0, 0.0, 0.0};
+      const double d = th - l;
+      const double uu = d * TAB_INV_W;
+      double tau, v[4] = {0.0, 0.0, 0.0, 0.0};
       if (uu >= 0.0 && uu <= (double)ns) {
+        // x = 2 (uu - g) - 1 in [-1, 1]; the FP64 work stays a handful of operations
         const int g = min((int)uu, ns - 1);
-        const ff x = ff_of(2.0 * (uu - (double)g) - 1.0);
+        const ff x = ff_of(fma(d, 2.0 * TAB_INV_W, -(double)(2 * g + 1)));
         const float2* c = cs + (int64_t)g * (TAB_NF * TAB_NC);
         v[0] = ff_dbl(cheb_ff(c, x));
         v[1] = ff_dbl(cheb_ff(c + TAB_NC, x));
+        tau = ff_dbl(cheb_ff(c + 2 * TAB_NC, x));
         if (GRAD) {
-          v[2] = ff_dbl(cheb_ff(c + 2 * TAB_NC, x));
-          v[3] = ff_dbl(cheb_ff(c + 3 * TAB_NC, x));
+          v[2] = ff_dbl(cheb_ff(c + 3 * TAB_NC, x));
+          v[3] = ff_dbl(cheb_ff(c + 4 * TAB_NC, x));
         }
       } else {
+        tau = exp10(th);
         direct_sums<GRAD>(a, u, tau, v);
       }
       a.sc.x[(int64_t)j * Q + q] = tau;
@@ -185,9 +190,9 @@ void launch_tab_nodes(int64_t S, const int32_t* qn0, const int32_t* nseg, const 
 }
 
 void launch_tab_coef(int64_t S, const int32_t* qn0, const int32_t* nseg, const int64_t* seg0, const double* G,
-                     int64_t Qn, float2* coef, int sms, cudaStream_t st) {
+                     const double* X, int64_t Qn, float2* coef, int sms, cudaStream_t st) {
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(S, (int64_t)sms * 32));
-  k_tab_coef<<<grid, 128, 0, st>>>(S, qn0, nseg, seg0, cheb_const(), G, Qn, coef);
+  k_tab_coef<<<grid, 128, 0, st>>>(S, qn0, nseg, seg0, cheb_const(), G, X, Qn, coef);
 }
 
 void launch_tab_eval(const EvalArgs& a, bool grad, int sms, cudaStream_t st) {

@@ -28,7 +28,8 @@ def constants():
 
 
 def column_sums(om, er, ei, theta):
-    """S, h, dS/dtheta, dh/dtheta of single Debye poles at log10 tau = theta (rows)."""
+    """S, h, tau, dS/dtheta, dh/dtheta of single Debye poles at log10 tau = theta (rows),
+    in the order of the tables."""
     tau = 10.0 ** np.asarray(theta)
     x = np.outer(tau, om)
     re_ = 1.0 / (1.0 + x * x)
@@ -38,7 +39,7 @@ def column_sums(om, er, ei, theta):
     # d re / d theta = -2 ln10 x^2 re^2, d im / d theta = ln10 x (1 - x^2) re^2
     dre = -2.0 * LN10 * x * x * re_ * re_
     dim = LN10 * x * (1.0 - x * x) * re_ * re_
-    return np.stack([S, h, dre.sum(1), dre @ er + dim @ ei])
+    return np.stack([S, h, tau, dre.sum(1), dre @ er + dim @ ei])
 
 
 def table(om, er, ei, lo, hi, w, nc):
@@ -59,7 +60,7 @@ def interpolate(coef, lo, w, theta):
     u = (theta - lo) / w
     g = np.minimum(u.astype(int), len(coef) - 1)
     x = 2.0 * (u - g) - 1.0
-    out = np.empty((4, len(theta)))
+    out = np.empty((5, len(theta)))
     for i in range(len(theta)):
         out[:, i] = np.polynomial.chebyshev.chebval(x[i], coef[g[i]].T)
     return out
@@ -69,7 +70,7 @@ def check_batch(b, spectra, n_theta=150):
     w, nc = constants()
     re_all, im_all = models.synthesize(b)
     rng = np.random.default_rng(11)
-    worst = np.zeros(4)
+    worst = np.zeros(5)
     for s in spectra:
         a, c = b.offsets[s], b.offsets[s + 1]
         om, er, ei = b.omega[a:c], re_all[a:c], im_all[a:c]
@@ -77,9 +78,9 @@ def check_batch(b, spectra, n_theta=150):
         coef = table(om, er, ei, lo, hi, w, nc)
         th = np.concatenate([rng.uniform(lo, hi, n_theta), [lo, hi]])
         got, ref = interpolate(coef, lo, w, th), column_sums(om, er, ei, th)
-        # S and h relative to themselves; the derivatives change sign: relative to their range
-        scale = np.stack([np.abs(ref[0]), np.abs(ref[1]),
-                          np.full(len(th), np.abs(ref[2]).max()), np.full(len(th), np.abs(ref[3]).max())])
+        # S, h and tau relative to themselves; the derivatives change sign: relative to their range
+        scale = np.stack([np.abs(ref[0]), np.abs(ref[1]), ref[2],
+                          np.full(len(th), np.abs(ref[3]).max()), np.full(len(th), np.abs(ref[4]).max())])
         worst = np.maximum(worst, (np.abs(got - ref) / scale).max(axis=1))
     return worst
 
@@ -87,13 +88,13 @@ def check_batch(b, spectra, n_theta=150):
 def test_table_shape_mixed_workload():
     b = W.workload("mixed_1024")
     worst = check_batch(b, [0, 4, 6, 3, 1, 400])   # HN, CC, CD, Jonscher, CRIM and one more
-    assert worst[:2].max() <= 1e-13 and worst[2:].max() <= 5e-13, worst
+    assert worst[:3].max() <= 1e-13 and worst[3:].max() <= 5e-13, worst
 
 
 def test_table_shape_tabulated_workload():
     b = W.tabulated_batch(S=4, K=1024, seed=3)            # 40 random poles, Jonscher tail, 1 % noise
     worst = check_batch(b, range(4))
-    assert worst[:2].max() <= 1e-13 and worst[2:].max() <= 5e-13, worst
+    assert worst[:3].max() <= 1e-13 and worst[3:].max() <= 5e-13, worst
 
 
 def test_coarser_table_is_not_enough():
