@@ -582,7 +582,9 @@ static int grid_for(int n_units, int sms, int per_sm) {
 // 32 blocks per SM keeps enough warps resident to hide that memory's latency.
 void launch_solve_sums(const EvalArgs& a, double* cost, double* weights, double* grad, int block, int sms,
                        cudaStream_t st) {
-  if (a.n_units) k_solve_sums_t<0, -1><<<grid_for(a.n_units, sms, 32), block, 0, st>>>(a, cost, weights, grad);
+  if (!a.n_units) return;
+  if (grad) k_solve_sums_t<0, 1><<<grid_for(a.n_units, sms, 32), block, 0, st>>>(a, cost, weights, grad);
+  else k_solve_sums_t<0, 0><<<grid_for(a.n_units, sms, 32), block, 0, st>>>(a, cost, weights, nullptr);
 }
 
 bool solve_sums_by_warp(int64_t Q, int lanes, int sms) {

@@ -625,6 +625,14 @@ __global__ void k_assemble(int64_t S, int nmax, const int32_t* n_poles, const do
 
 // ------------------------------------------------------------------ launchers
 static int g1d(int64_t n, int sms) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8)); }
+// Grid for one thread per item in blocks of `block` threads (at most 2048 resident per SM).
+static int g1d_b(int64_t n, int block, int sms) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + block - 1) / block, (int64_t)sms * (2048 / block)));
+}
+// The polish's per-line kernels run one thread per line through a dependent FP64
+// chain (the L-BFGS two-loop recursion, the Armijo tests): single-warp blocks spread
+// the lines over every SM.
+constexpr int POLISH_BLOCK = 32;
 
 void launch_pso_init(const SwarmArgs& a, int sms, cudaStream_t st) {
   k_pso_init<<<g1d((int64_t)a.S * a.P, sms), 256, 0, st>>>(a);
@@ -639,7 +647,7 @@ void launch_da_start(const SwarmArgs& a, int sms, cudaStream_t st) {
   k_da_start<<<g1d((int64_t)a.S * a.P, sms), 256, 0, st>>>(a);
 }
 void launch_da_visit(const SwarmArgs& a, int j, int sms, cudaStream_t st) {
-  k_da_visit<<<g1d((int64_t)a.S * a.P, sms), 128, 0, st>>>(a, j);
+  k_da_visit<<<g1d_b((int64_t)a.S * a.P, 128, sms), 128, 0, st>>>(a, j);
 }
 void launch_da_accept(const SwarmArgs& a, const double* cost, int j, int sms, cudaStream_t st) {
   k_da_accept<<<g1d((int64_t)a.S * a.P, sms), 256, 0, st>>>(a, cost, j);
@@ -666,18 +674,18 @@ void launch_polish_take0(const PolishArgs& pa, int sms, cudaStream_t st) {
 }
 void launch_polish_dir(const PolishArgs& pa, const int32_t* n_poles, const double* lo, const double* hi,
                        int sms, cudaStream_t st) {
-  k_polish_dir<<<g1d(pa.L, sms), 128, 0, st>>>(pa, n_poles, lo, hi);
+  k_polish_dir<<<g1d_b(pa.L, POLISH_BLOCK, sms), POLISH_BLOCK, 0, st>>>(pa, n_poles, lo, hi);
 }
 void launch_polish_first(const PolishArgs& pa, const int32_t* n_poles, const double* lo, const double* hi,
                          const int64_t* offsets, int sms, cudaStream_t st) {
-  k_polish_first<<<g1d(pa.L, sms), 128, 0, st>>>(pa, n_poles, lo, hi, offsets);
+  k_polish_first<<<g1d_b(pa.L, POLISH_BLOCK, sms), POLISH_BLOCK, 0, st>>>(pa, n_poles, lo, hi, offsets);
 }
 void launch_polish_accept(const PolishArgs& pa, const int32_t* n_poles, const double* lo, const double* hi,
                           const int64_t* offsets, int sms, cudaStream_t st) {
-  k_polish_accept<<<g1d(pa.L, sms), 128, 0, st>>>(pa, n_poles, lo, hi, offsets);
+  k_polish_accept<<<g1d_b(pa.L, POLISH_BLOCK, sms), POLISH_BLOCK, 0, st>>>(pa, n_poles, lo, hi, offsets);
 }
 void launch_polish_take(const PolishArgs& pa, const int32_t* n_poles, int sms, cudaStream_t st) {
-  k_polish_take<<<g1d(pa.L, sms), 128, 0, st>>>(pa, n_poles);
+  k_polish_take<<<g1d_b(pa.L, POLISH_BLOCK, sms), POLISH_BLOCK, 0, st>>>(pa, n_poles);
 }
 void launch_pick_best(const SwarmArgs& a, const PolishArgs& pa, double* out_theta, int sms, cudaStream_t st) {
   k_pick_best<<<g1d(a.S, sms), 256, 0, st>>>(a, pa, out_theta);

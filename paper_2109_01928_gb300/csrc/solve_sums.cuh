@@ -50,22 +50,35 @@ __device__ __forceinline__ ff gram_ff(int i, int j, const ff* tau, const ff* S, 
   return ff_quot(num, ff_sum(tau[i - 1], tau[j - 1]));
 }
 
-// (M v)_i in float-float, M = G + lam diag G. Every entry is formed where it is
-// used (once per product, serving both of its rows) rather than kept per
-// candidate, which keeps the per-thread state small.
-__device__ __forceinline__ void mvec_ff(int n, const ff* tau, const ff* S, ff kk, ff one_lam, const ff* v,
-                                        ff* out) {
+// Sources of the float-float Gram entries (i >= j): formed where they are used
+// (the per-N kernels, whose compiler keeps what fits), or read from a per-thread
+// packed table filled once (the general kernel, whose arrays are in local memory
+// anyway).
+struct GramRecompute {
+  const ff* tau;
+  const ff* S;
+  ff kk;
+  __device__ __forceinline__ ff operator()(int i, int j) const { return gram_ff(i, j, tau, S, kk); }
+};
+struct GramTable {
+  const ff* g;   // packed lower triangle, entry (i, j) at pk(i, j)
+  __device__ __forceinline__ ff operator()(int i, int j) const { return g[pk(i, j)]; }
+};
+
+// (M v)_i in float-float, M = G + lam diag G; each entry serves both of its rows.
+template <class GA>
+__device__ __forceinline__ void mvec_ff(int n, const GA& G, ff one_lam, const ff* v, ff* out) {
 #pragma unroll
   for (int i = 0; i < n; ++i) out[i] = ff{0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < n; ++i) {
 #pragma unroll
     for (int j = 0; j < i; ++j) {
-      const ff g = gram_ff(i, j, tau, S, kk);
+      const ff g = G(i, j);
       out[i] = ff_sum(out[i], ff_prod(g, v[j]));
       out[j] = ff_sum(out[j], ff_prod(g, v[i]));
     }
-    out[i] = ff_sum(out[i], ff_prod(ff_prod(gram_ff(i, i, tau, S, kk), one_lam), v[i]));
+    out[i] = ff_sum(out[i], ff_prod(ff_prod(G(i, i), one_lam), v[i]));
   }
 }
 
@@ -113,9 +126,9 @@ __device__ __forceinline__ void llt_solve_rdiag(LA L, float* v, int n) {
 
 // M^-1 rhs through the FP32 factor L of the scaled M (scaling dinv = diag(G)^-1/2),
 // refined `steps` times against the float-float M.
-template <class LA>
-__device__ __forceinline__ bool refined_solve(int n, LA L, const float* dinv, const ff* tau, const ff* S,
-                                              ff kk, ff one_lam, const ff* rhs, ff* x, ff* r, float* v, int steps) {
+template <class LA, class GA>
+__device__ __forceinline__ bool refined_solve(int n, LA L, const float* dinv, const GA& G, ff one_lam,
+                                              const ff* rhs, ff* x, ff* r, float* v, int steps) {
   bool ok = true;
 #pragma unroll
   for (int i = 0; i < n; ++i) x[i] = ff{0.f, 0.f};
@@ -126,7 +139,7 @@ __device__ __forceinline__ bool refined_solve(int n, LA L, const float* dinv, co
 #pragma unroll
       for (int i = 0; i < n; ++i) r[i] = rhs[i];
     } else {
-      mvec_ff(n, tau, S, kk, one_lam, x, r);
+      mvec_ff(n, G, one_lam, x, r);
 #pragma unroll
       for (int i = 0; i < n; ++i) r[i] = ff_sum(rhs[i], ff_neg(r[i]));
     }
@@ -153,12 +166,17 @@ __device__ __forceinline__ bool refined_solve(int n, LA L, const float* dinv, co
 //   (M_i)_{ij} = tau_i D_i / (tau_i + tau_j) + ln10 tau_i tau_j (S_i - S_j) / (tau_i + tau_j)^2
 // (the derivative of G_ij = (tau_i S_i + tau_j S_j)/(tau_i + tau_j), d tau_i = ln10 tau_i).
 //
-// NT = 0: any pole count (u.N at run time), the gradient when grad != nullptr; the
-// small systems live in per-thread local memory. NT > 0: every unit has NT poles
-// (one launch per pole bucket) and GRAD fixes whether the gradient is computed:
-// the loops have constant trip counts, unroll, and the systems stay in registers.
+// NT = 0: any pole count (u.N at run time); the small systems live in per-thread
+// local memory. NT > 0: every unit has NT poles (one launch per pole bucket), the
+// loops have constant trip counts, unroll, and the systems stay in registers.
+// GRAD (0 or 1) fixes whether the gradient is computed.
+// From N = 9 the per-N kernels are held to about 170 registers (3 resident blocks of
+// 128): with spills to L1 the extra resident warps hide more of the dependent chains
+// (measured on whole table-mode mixed_1024 fits: 136.4 -> 132.2 ms; 128 registers:
+// 130.7 ms, but 0.6 % slower in the direct mode, where the solve overlaps the passes).
 template <int NT, int GRAD>
-__global__ void __launch_bounds__(256) k_solve_sums_t(EvalArgs a, double* cost, double* weights, double* grad) {
+__global__ void __launch_bounds__(128, (NT >= 9 ? 3 : 1)) k_solve_sums_t(EvalArgs a, double* cost, double* weights,
+                                                                      double* grad) {
   const int64_t Q = a.sc.Q;
   const int nmax = a.sc.nmax, nm1 = nmax + 1;
   const bool with_grad = GRAD < 0 ? grad != nullptr : GRAD > 0;
@@ -189,17 +207,31 @@ __global__ void __launch_bounds__(256) k_solve_sums_t(EvalArgs a, double* cost, 
     hv[0] = ff_of(a.h0[u.s]);
     const ff kk = ff_of((double)(u.k1 - u.k0));
     const ff one_lam = ff_of(1.0 + a.lam);
+    // the general kernel's gradient variant keeps the entries in a table: its five
+    // products with M outweigh the table's local-memory traffic (measured on N = 20:
+    // cost and gradient 40.6 -> 35.5 ms; cost only, two products, 6.0 -> 7.5 ms)
+    constexpr bool G_TABLE = NT == 0 && GRAD > 0;
+    ff gtab[G_TABLE ? NPACK_MAX : 1];
+    const auto G = [&] {
+      if constexpr (!G_TABLE) {
+        return GramRecompute{tau, S, kk};
+      } else {
+        for (int i = 0; i < n; ++i)
+          for (int j = 0; j <= i; ++j) gtab[pk(i, j)] = gram_ff(i, j, tau, S, kk);
+        return GramTable{gtab};
+      }
+    }();
     // FP32 Cholesky of the Marquardt-scaled damped matrix (unit diagonal + lam)
 #pragma unroll
-    for (int i = 0; i < n; ++i) dinv[i] = __frsqrt_rn(gram_ff(i, i, tau, S, kk).h);   // diag(G)^-1/2
+    for (int i = 0; i < n; ++i) dinv[i] = __frsqrt_rn(G(i, i).h);   // diag(G)^-1/2
 #pragma unroll
     for (int i = 0; i < n; ++i) {
 #pragma unroll
-      for (int j = 0; j < i; ++j) L[pk(i, j)] = __fmul_rn(__fmul_rn(gram_ff(i, j, tau, S, kk).h, dinv[i]), dinv[j]);
+      for (int j = 0; j < i; ++j) L[pk(i, j)] = __fmul_rn(__fmul_rn(G(i, j).h, dinv[i]), dinv[j]);
       L[pk(i, i)] = (float)(1.0 + a.lam);
     }
     bool ok = cholesky_rdiag(L, n);
-    if (ok) ok = refined_solve(n, L, dinv, tau, S, kk, one_lam, hv, x, r, v, with_grad ? SUMS_REFINE : SUMS_REFINE_COST);
+    if (ok) ok = refined_solve(n, L, dinv, G, one_lam, hv, x, r, v, with_grad ? SUMS_REFINE : SUMS_REFINE_COST);
     record_fail(a, q, u.s, ok);
     if (!ok) {
       if (cost) cost[q] = INFINITY;
@@ -216,7 +248,7 @@ __global__ void __launch_bounds__(256) k_solve_sums_t(EvalArgs a, double* cost, 
       sgn[i] = (i > 0 && x[i].h < 0.f) ? -1.f : 1.f;
       if (sgn[i] < 0.f) x[i] = ff_neg(x[i]);
     }
-    mvec_ff(n, tau, S, kk, one_lam, x, r);   // r = M x_hat
+    mvec_ff(n, G, one_lam, x, r);   // r = M x_hat
     ff c = ff_of(a.bb[u.s]);
 #pragma unroll
     for (int i = 0; i < n; ++i) {
@@ -240,7 +272,7 @@ __global__ void __launch_bounds__(256) k_solve_sums_t(EvalArgs a, double* cost, 
       r[i] = ff_sum(r[i], ff_neg(hv[i]));
       if (sgn[i] < 0.f) r[i] = ff_neg(r[i]);
     }
-    if (!refined_solve(n, L, dinv, tau, S, kk, one_lam, r, w, rw, v, SUMS_REFINE)) {
+    if (!refined_solve(n, L, dinv, G, one_lam, r, w, rw, v, SUMS_REFINE)) {
       for (int j = 0; j < nmax; ++j) grad[(int64_t)q * nmax + j] = 0.0;
       continue;
     }
