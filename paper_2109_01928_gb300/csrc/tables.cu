@@ -4,9 +4,9 @@
 // leaves, per pole, the column sums S(theta) = sum_k re_k and h(theta) = a^T b (and
 // their theta derivatives for the gradient): four functions of one variable per
 // spectrum, whatever the candidate. They are tabulated once per call as piecewise
-// Chebyshev interpolants over the spectrum's log10(tau) box, and every candidate's
-// sums are then read off by a float-float Clenshaw recurrence: O(TAB_NC) per pole
-// instead of O(K).
+// Chebyshev interpolants over the spectrum's log10(tau) box (stored as polynomials in
+// the segment's coordinate), and every candidate's sums are then read off by
+// float-float Horner steps: O(TAB_NC) per pole instead of O(K).
 //
 // Accuracy: with s = ln tau^2, each term 1 / (1 + w_k^2 e^s) has its poles at
 // Im s = +-pi, so every column sum is analytic in the strip |Im s| < pi and bounded
@@ -22,10 +22,12 @@
 
 namespace debyefit {
 
-// Chebyshev points of the first kind and the matching discrete cosine transform.
+// Chebyshev points of the first kind, the matching discrete cosine transform, and the
+// monomial coefficients of the Chebyshev polynomials (integers, exact in FP64).
 struct ChebConst {
   double xm[TAB_NC];            // x_m = cos(pi (m + 1/2) / NC)
   double dct[TAB_NC][TAB_NC];   // (2 / NC) cos(pi k (m + 1/2) / NC), row 0 halved
+  double mono[TAB_NC][TAB_NC];  // T_j(x) = sum_k mono[j][k] x^k
 };
 
 static const ChebConst& cheb_const() {
@@ -36,6 +38,12 @@ static const ChebConst& cheb_const() {
     for (int k = 0; k < TAB_NC; ++k)
       for (int m = 0; m < TAB_NC; ++m)
         r.dct[k][m] = (k == 0 ? 1.0 : 2.0) / TAB_NC * std::cos(pi * k * (m + 0.5) / TAB_NC);
+    // T_0 = 1, T_1 = x, T_{j+1} = 2 x T_j - T_{j-1}
+    r.mono[0][0] = 1.0;
+    if (TAB_NC > 1) r.mono[1][1] = 1.0;
+    for (int j = 1; j + 1 < TAB_NC; ++j)
+      for (int k = 0; k < TAB_NC; ++k)
+        r.mono[j + 1][k] = (k > 0 ? 2.0 * r.mono[j][k - 1] : 0.0) - r.mono[j - 1][k];
     return r;
   }();
   return c;
@@ -78,33 +86,39 @@ __global__ void k_tab_coef(int64_t S, const int32_t* qn0, const int32_t* nseg, c
         const int i = n % TAB_NODE_N;
         v[m] = f == 2 ? X[(int64_t)i * Qn + q] : G[(int64_t)((f < 2 ? f : f - 1) * TAB_NODE_N + i) * Qn + q];
       }
+      double c[TAB_NC];
+#pragma unroll
+      for (int k = 0; k < TAB_NC; ++k) {
+        c[k] = 0.0;
+#pragma unroll
+        for (int m = 0; m < TAB_NC; ++m) c[k] = fma(cc.dct[k][m], v[m], c[k]);
+      }
+      // monomial coefficients in x (the series' coefficients fall by ~20 a degree, the
+      // Chebyshev polynomials' monomial coefficients grow by at most 1 + sqrt 2: the
+      // monomial form is as well conditioned on [-1, 1])
       float2* out = coef + ((seg0[s] + g) * TAB_NF + f) * TAB_NC;
 #pragma unroll
       for (int k = 0; k < TAB_NC; ++k) {
-        double c = 0.0;
+        double a = 0.0;
 #pragma unroll
-        for (int m = 0; m < TAB_NC; ++m) c = fma(cc.dct[k][m], v[m], c);
-        const float hi = __double2float_rn(c);
-        out[k] = make_float2(hi, __double2float_rn(c - (double)hi));
+        for (int j = k; j < TAB_NC; ++j) a = fma(cc.mono[j][k], c[j], a);
+        const float hi = __double2float_rn(a);
+        out[k] = make_float2(hi, __double2float_rn(a - (double)hi));
       }
     }
   }
 }
 
-// f(x) = sum_k c_k T_k(x) for x in [-1, 1] (c_0 stored halved) by Clenshaw's
-// recurrence b_k = c_k + 2 x b_{k+1} - b_{k+2}, in float-float.
-__device__ __forceinline__ ff cheb_ff(const float2* __restrict__ c, ff x) {
-  const ff x2{2.f * x.h, 2.f * x.l};
-  ff b1{0.f, 0.f}, b2{0.f, 0.f};
+// f(x) = sum_k a_k x^k for x in [-1, 1] by Horner's rule in float-float.
+__device__ __forceinline__ ff poly_ff(const float2* __restrict__ a, ff x) {
+  const float2 top = __ldg(a + TAB_NC - 1);
+  ff acc{top.x, top.y};
 #pragma unroll
-  for (int k = TAB_NC - 1; k >= 1; --k) {
-    const float2 ck = __ldg(c + k);
-    const ff b0 = ff_sum(ff_sum(ff_prod(x2, b1), ff_neg(b2)), ff{ck.x, ck.y});
-    b2 = b1;
-    b1 = b0;
+  for (int k = TAB_NC - 2; k >= 0; --k) {
+    const float2 ak = __ldg(a + k);
+    acc = ff_sum(ff_prod(acc, x), ff{ak.x, ak.y});
   }
-  const float2 c0 = __ldg(c);
-  return ff_sum(ff_sum(ff_prod(x, b1), ff_neg(b2)), ff{c0.x, c0.y});
+  return acc;
 }
 
 // The four column sums of one pole directly over the spectrum's samples in FP64, for a
@@ -161,12 +175,12 @@ __global__ void __launch_bounds__(128) k_tab_eval(EvalArgs a) {
         const int g = min((int)uu, ns - 1);
         const ff x = ff_of(fma(d, 2.0 * TAB_INV_W, -(double)(2 * g + 1)));
         const float2* c = cs + (int64_t)g * (TAB_NF * TAB_NC);
-        v[0] = ff_dbl(cheb_ff(c, x));
-        v[1] = ff_dbl(cheb_ff(c + TAB_NC, x));
-        tau = ff_dbl(cheb_ff(c + 2 * TAB_NC, x));
+        v[0] = ff_dbl(poly_ff(c, x));
+        v[1] = ff_dbl(poly_ff(c + TAB_NC, x));
+        tau = ff_dbl(poly_ff(c + 2 * TAB_NC, x));
         if (GRAD) {
-          v[2] = ff_dbl(cheb_ff(c + 3 * TAB_NC, x));
-          v[3] = ff_dbl(cheb_ff(c + 4 * TAB_NC, x));
+          v[2] = ff_dbl(poly_ff(c + 3 * TAB_NC, x));
+          v[3] = ff_dbl(poly_ff(c + 4 * TAB_NC, x));
         }
       } else {
         tau = exp10(th);

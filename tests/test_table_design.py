@@ -3,8 +3,9 @@
 Per spectrum, the pole-wise column sums S(theta) = sum_k 1/(1 + w_k^2 tau^2),
 h(theta) = a(theta)^T b and their theta derivatives are interpolated on segments
 of TAB_W decades by TAB_NC Chebyshev coefficients (values at the Chebyshev points
-of the first kind, discrete cosine transform). The constants are read from the
-kernel source; the interpolants, built here in numpy from exact FP64 sums, must
+of the first kind, discrete cosine transform), stored as polynomials in the
+segment's coordinate x in [-1, 1] as the kernels store them. The constants are
+read from the kernel source; the interpolants, built here in numpy from exact FP64 sums, must
 reproduce the direct sums to well below the float-float rounding of the GPU's
 own sums (~1e-12 relative) on spectra of the benchmark workloads.
 """
@@ -52,7 +53,8 @@ def table(om, er, ei, lo, hi, w, nc):
         F = column_sums(om, er, ei, lo + w * (g + 0.5 + 0.5 * xm))
         c = 2.0 / nc * F @ T.T
         c[:, 0] *= 0.5
-        coef.append(c)
+        # stored, as on the GPU, as a polynomial in the segment's coordinate x
+        coef.append(np.array([np.polynomial.chebyshev.cheb2poly(row) for row in c]))
     return np.array(coef)
 
 
@@ -62,7 +64,7 @@ def interpolate(coef, lo, w, theta):
     x = 2.0 * (u - g) - 1.0
     out = np.empty((5, len(theta)))
     for i in range(len(theta)):
-        out[:, i] = np.polynomial.chebyshev.chebval(x[i], coef[g[i]].T)
+        out[:, i] = np.polynomial.polynomial.polyval(x[i], coef[g[i]].T)
     return out
 
 
