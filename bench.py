@@ -591,8 +591,11 @@ def main():
     ap.add_argument("--kernel-case", type=int, default=0, metavar="S",
                     help="profiling case: evaluate the first S spectra of the workload at full "
                          "population twice (debye_eval_population) and exit")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
-                    help="precision of --kernel-case")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp64_sums", "mixed_table"],
+                    help="precision of --kernel-case and --fit-case")
+    ap.add_argument("--fit-case", action="store_true",
+                    help="profiling case: one short warm-up fit and one whole fit of the workload in --precision, "
+                         "then exit")
     ap.add_argument("--kernel-n", type=int, default=0, metavar="N",
                     help="--kernel-case: fit every spectrum with N poles (one pass kernel fills the GPU)")
     args = ap.parse_args()
@@ -608,6 +611,8 @@ def main():
         return reference_arm(args, rank, world)
     if args.kernel_case:
         return kernel_case(args.kernel_case, args.precision, SETTINGS[WORKLOAD][0], args.kernel_n)
+    if args.fit_case:
+        return fit_case(args.precision)
 
     # the oracle baselines run first, in spawned processes, before any CUDA call
     cpu, cpu_tab = None, None
@@ -782,6 +787,20 @@ def kernel_case(S: int, precision: str, P: int, n_poles: int = 0):
         D.debye_sync(h)
     print(json.dumps({"kernel_case": WORKLOAD, "spectra": S, "P": P, "n_poles": n_poles, "precision": precision,
                       "mean_cost": float(c.mean())}))
+
+
+def fit_case(precision: str):
+    """A fixed case for launch-list captures: the workload's targets, one short warm-up fit
+    (2 generations, 2 polish iterations) and one whole fit on one handle."""
+    import torch
+    from paper_2109_01928_gb300 import debyefit as D
+    bn = Bench(D, torch, torch.device("cuda", 0), WORKLOAD)
+    with D.Handle(precision) as h:
+        out = D.debye_fit_batch(h, bn.sp, P=bn.P, iters=2, seed=0, polish_topk=bn.topk, polish_iters=2,
+                                n_max=bn.b.n_max)
+        out = bn.fit(h, out)
+        D.debye_sync(h)
+    print(json.dumps({"fit_case": WORKLOAD, "precision": precision, "sum_final_cost": float(out["final_cost"].sum())}))
 
 
 def workload_desc(b, iters) -> str:

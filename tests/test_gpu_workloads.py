@@ -1,6 +1,7 @@
 """Full-size workloads on the GPU, checked on sampled outputs the oracle computes
 one by one: the 256-spectrum K=2000 differentiation workload (costs, gradients,
-polish-only fit) and the 16384-spectrum K=4096 tabulated workload (costs)."""
+polish-only fit) and the 16384-spectrum K=4096 tabulated workload (costs), in FP64
+and in mixed precision with direct and tabulated column sums."""
 import numpy as np
 import pytest
 
@@ -11,8 +12,8 @@ from oracle import dls, fit, models, varpro
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-COST_TOL = {"fp64": 1e-10, "mixed": 1e-5}
-GRAD_TOL = {"fp64": 1e-8, "mixed": 1e-4}
+COST_TOL = {"fp64": 1e-10, "mixed": 1e-5, "mixed_table": 1e-5}
+GRAD_TOL = {"fp64": 1e-8, "mixed": 1e-4, "mixed_table": 1e-4}
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +35,7 @@ def _spectra(D, b, re, im):
     return D.make_spectra(b.offsets, b.omega, re, im, b.n_poles, b.lo, b.hi, device="cuda")
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_table"])
 def test_hn256_cost_grad_sampled(D, hn256, prec):
     b, re, im = hn256
     th = W.population(b, 4096, seed=0)
@@ -81,13 +82,15 @@ def test_hn256_polish_fit_sampled(D, hn256):
     print(how)
 
 
-def test_tabulated_full_size_sampled(D):
-    # 16384 spectra x 4096 frequencies, N = 20, 512 candidates each (mixed precision)
+@pytest.mark.parametrize("prec", ["mixed", "mixed_table"])
+def test_tabulated_full_size_sampled(D, prec):
+    # 16384 spectra x 4096 frequencies, N = 20, 512 candidates each (mixed precision, the
+    # column sums swept directly and read from the tables)
     b = W.workload("tabulated_16384_k4096")
     tt = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
     om = tt(b.omega)
     offs = tt(b.offsets, torch.int64)
-    with D.Handle("mixed") as h:
+    with D.Handle(prec) as h:
         er, ei = D.debye_synth_targets(h, offs, om, tt(b.model, torch.int32), tt(b.params),
                                        tt(b.pole_offsets, torch.int64), tt(b.pole_tau), tt(b.pole_deps),
                                        tt(b.noise_re), tt(b.noise_im))
@@ -107,10 +110,11 @@ def test_tabulated_full_size_sampled(D):
         i = idx[int(s)]
         a, c = sub.offsets[i], sub.offsets[i + 1]
         ref = float(dls.cost(sub.omega[a:c], re[a:c], im[a:c], th[s, p]))
-        assert abs(cost[s, p] - ref) <= COST_TOL["mixed"] * ref, (s, p, cost[s, p], ref)
+        assert abs(cost[s, p] - ref) <= COST_TOL[prec] * ref, (s, p, cost[s, p], ref)
 
 
-@pytest.mark.parametrize("prec,lanes", [("fp64", 0), ("mixed", 1), ("mixed", 32)])
+@pytest.mark.parametrize("prec,lanes", [("fp64", 0), ("mixed", 1), ("mixed", 32), ("mixed_table", 1),
+                                        ("mixed_table", 32)])
 def test_tabulated_cost_grad_sampled(D, prec, lanes):
     # N = 20, K = 4096 noisy Debye-sum spectra: cost and gradient of sampled candidates
     # (mixed: the small-system solve one thread and one warp per candidate)
