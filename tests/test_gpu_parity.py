@@ -697,6 +697,32 @@ def test_fit_da_with_polish_ragged_batch(D):
         assert rr <= 1e-4 or gcost <= r["cost_final"] * (1 + 1e-6), (s, rr, gcost, r["cost_final"])
 
 
+@pytest.mark.parametrize("method", ["pso", "de", "da"])
+def test_table_search_trace_follows_direct(D, method):
+    # The tabulated column sums change each candidate's cost by ~1e-12 relative against
+    # the direct sums, far below any gap between two candidates the searches compare: the
+    # per-generation best costs of the same seeded search (no polish) agree within the
+    # mixed cost tolerance, and the final fits agree.
+    b = W.mixed_batch(S=6, seed=43, P=32, K_range=(50, 300), N_range=(2, 8))
+    re, im = models.synthesize(b)
+    sp = spectra_for(D, b, re, im)
+    out = {}
+    for prec in ("mixed", "mixed_table"):
+        with D.Handle(prec) as h:
+            out[prec] = D.debye_fit_batch(h, sp, P=32, iters=12, seed=7, polish_topk=0, trace=True, method=method)
+            D.debye_sync(h)
+    ta, tb = out["mixed"]["trace"].cpu().numpy(), out["mixed_table"]["trace"].cpu().numpy()
+    np.testing.assert_allclose(tb, ta, rtol=COST_TOL["mixed"], atol=0)
+    for s in range(b.S):
+        a, c = b.offsets[s], b.offsets[s + 1]
+        N = int(b.n_poles[s])
+        ea = fitted(b.omega[a:c], out["mixed"]["eps_inf"][s].item(), out["mixed"]["d_eps"][s, :N].cpu().numpy(),
+                    out["mixed"]["tau"][s, :N].cpu().numpy())
+        eb = fitted(b.omega[a:c], out["mixed_table"]["eps_inf"][s].item(),
+                    out["mixed_table"]["d_eps"][s, :N].cpu().numpy(), out["mixed_table"]["tau"][s, :N].cpu().numpy())
+        assert dls.rel_rms(eb, ea) <= 1e-4, (method, s)
+
+
 def test_da_rejects_too_many_iterations(D):
     b = W.single_hn()
     re, im = models.synthesize(b)

@@ -18,13 +18,13 @@ from oracle import dls, models
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "mixed": 1e-5}
+TOL = {"fp64": 1e-10, "mixed": 1e-5, "mixed_table": 1e-5}
 # The two entry points may split candidates over different numbers of lanes (the
 # handle path sizes the split to the batch), so sums run in different orders and
 # the weights, which are not stationary like the cost, differ by rounding: FP64
 # weights to ~1e-12 of their scale, mixed ones to the refinement bound
 # (kappa 2^-24)^2 ~ 1.6e-6 with kappa <= (n + lam) / lam (n = 21, lam = 1e-3).
-WTOL = {"fp64": 1e-10, "mixed": 1e-5}
+WTOL = {"fp64": 1e-10, "mixed": 1e-5, "mixed_table": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -49,7 +49,8 @@ def oracle_costs(b, re, im, th):
 LAYOUTS = [(24, 0), (64, 0), (64, 128)]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+# mixed_table: the entry point takes the direct column sums, the handle the tables
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_table"])
 @pytest.mark.parametrize("P,cb", LAYOUTS)
 def test_noalloc_matches_eval_population_twice(D, prec, P, cb):
     # a ragged batch with every kernel bucket (N = 1..20), small enough for the fixed scratch
