@@ -238,7 +238,7 @@ def main(argv=None) -> int:
     import argparse
     ap = argparse.ArgumentParser(description="Fit gprMax dispersive-material commands with multi-Debye poles")
     ap.add_argument("input", help="text file with #havriliak_negami / #jonscher / #crim / #raw_data commands")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=sorted(D.PRECISIONS))
     ap.add_argument("--method", default="pso", choices=["pso", "de", "da"])
     ap.add_argument("--population", type=int, default=64)
     ap.add_argument("--iters", type=int, default=100)
