@@ -73,7 +73,9 @@ extern "C" {
                                  coefficients per segment, ~1e-14 relative); each candidate's
                                  sums then cost O(1) per pole instead of O(K). A theta outside
                                  the box takes a direct FP64 sweep. Same solve and tolerances
-                                 as DEBYE_PREC_MIXED; needs hi - lo <= 200 decades.
+                                 as DEBYE_PREC_MIXED; needs finite bounds with lo < hi <=
+                                 lo + 200 (DEBYE_EINVAL otherwise). Each call reads lo and hi
+                                 back to the host (one stream synchronisation).
                                  debye_eval_population_noalloc takes the direct sums. */
 
 #define DEBYE_MAX_POLES 20    /* largest N accepted */

@@ -40,6 +40,16 @@ __global__ void k_pso_init(SwarmArgs a) {
   }
 }
 
+// A draw's 53-bit integer u (the uniform is u 2^-53) as a double, built from its
+// IEEE-754 fields with integer operations (exact for u < 2^53): on GB300 an FP64
+// conversion costs as much as any other FP64 operation.
+__device__ __forceinline__ double u53_double(uint64_t u) {
+  if (u == 0) return 0.0;
+  const int e = 63 - __clzll((long long)u);   // position of the top bit, 0..52
+  const uint64_t mant = (u << (52 - e)) & 0x000FFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)(((uint64_t)(e + 1023) << 52) | mant));
+}
+
 __global__ void k_pso_move(SwarmArgs a) {
   const int64_t Q = (int64_t)a.S * a.P;
   const int gen = *a.gen;
@@ -51,13 +61,17 @@ __global__ void k_pso_move(SwarmArgs a) {
     const int64_t gq = s * a.P + a.gbest[s];
     const uint64_t p1 = rng_prefix(a.seed, TAG_R1, key_id(a, s), (uint64_t)gen);
     const uint64_t p2 = rng_prefix(a.seed, TAG_R2, key_id(a, s), (uint64_t)gen);
+    // phi r = phi (u 2^-53) = (phi 2^-53) u: the scaling by 2^-53 is exact, so both round
+    // the same exact product once and the update stays bit-identical to phi * r (for any
+    // |phi| >= 2^-969, where phi 2^-53 is still a normal number)
+    const double cp = __dmul_rn(a.phi_p, 0x1p-53), cg = __dmul_rn(a.phi_g, 0x1p-53);
     for (int d = 0; d < N; ++d) {
       const double x = a.x[q * a.nmax + d], v = a.v[q * a.nmax + d];
       const double pb = a.pbx[q * a.nmax + d], gb = a.pbx[gq * a.nmax + d];
-      const double r1 = rng_uniform(p1, p, d), r2 = rng_uniform(p2, p, d);
+      const double u1 = u53_double(rng_key(p1, p, d) >> 11), u2 = u53_double(rng_key(p2, p, d) >> 11);
       const double t1 = __dmul_rn(a.omega, v);
-      const double t2 = __dmul_rn(__dmul_rn(a.phi_p, r1), __dsub_rn(pb, x));
-      const double t3 = __dmul_rn(__dmul_rn(a.phi_g, r2), __dsub_rn(gb, x));
+      const double t2 = __dmul_rn(__dmul_rn(cp, u1), __dsub_rn(pb, x));
+      const double t3 = __dmul_rn(__dmul_rn(cg, u2), __dsub_rn(gb, x));
       const double vn = __dadd_rn(__dadd_rn(t1, t2), t3);
       a.v[q * a.nmax + d] = vn;
       a.x[q * a.nmax + d] = fmin(fmax(__dadd_rn(x, vn), lo), hi);

@@ -183,6 +183,23 @@ def test_table_box_edges_and_outside(D, lanes):
     assert checked >= 20
 
 
+def test_table_rejects_bad_boxes(D):
+    # the tables need finite bounds with lo < hi <= lo + 200 decades
+    b = W.mixed_batch(S=3, seed=2, P=8, K_range=(20, 40), N_range=(2, 3))
+    re, im = models.synthesize(b)
+    th = torch.as_tensor(W.population(b, 8, seed=1), device="cuda")
+    for lo, hi in ((-9.0, -9.0), (-8.0, -9.0), (-210.0, -5.0), (float("nan"), -5.0), (-13.0, float("inf"))):
+        bb = W.mixed_batch(S=3, seed=2, P=8, K_range=(20, 40), N_range=(2, 3))
+        bb.lo[1], bb.hi[1] = lo, hi
+        with D.Handle("mixed_table") as h:
+            with pytest.raises(D.DebyeError) as e:
+                D.debye_eval_population(h, spectra_for(D, bb, re, im), th)
+            assert e.value.code == D.DEBYE_EINVAL, (lo, hi)
+    with D.Handle("mixed_table") as h:   # the handle stays usable after the refusals
+        D.debye_eval_population(h, spectra_for(D, b, re, im), th)
+        D.debye_sync(h)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("cb", [32, 96, 128])
 def test_eval_block_sizes(D, prec, cb):
