@@ -329,6 +329,13 @@ int debye_sync(debye_handle h, cudaStream_t stream);
 #define DEBYE_KERNEL_TABLE_EVAL    11  /* DEBYE_PREC_MIXED_TABLE: candidates' sums from the tables */
 #define DEBYE_KERNEL_KINDS         12
 
+/* Failure-path check of the bounded device-side waits: one block runs the column-sum
+ * pass's staging wait (an mbarrier wait bounded by about 1 s of SM clock) on a buffer
+ * that no copy will fill. The wait gives up, records DEBYE_ETIMEOUT in the handle's
+ * status word (returned by the next debye_sync) and the kernel ends; the context and
+ * the handle stay usable. Enqueued on `stream`; returns DEBYE_OK once launched. */
+int debye_check_bounded_wait(debye_handle h, cudaStream_t stream);
+
 /* Number of kernel launches the handle has enqueued (a CUDA-graph replay counts
  * each of its kernel nodes); reset != 0 sets the counter to zero afterwards. */
 int debye_launch_count(debye_handle h, int64_t* count, int32_t reset);

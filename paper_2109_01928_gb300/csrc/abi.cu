@@ -818,6 +818,14 @@ int debye_autotune(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n
   return DEBYE_OK;
 }
 
+int debye_check_bounded_wait(debye_handle h, cudaStream_t st) {
+  if (!h) return DEBYE_EINVAL;
+  h->err.clear();
+  launch_stage_wait_check(h->d_status, nullptr, st);
+  h->launches += 1;
+  return h->check_launch("bounded-wait check");
+}
+
 int debye_launch_count(debye_handle h, int64_t* count, int32_t reset) {
   if (!h) return DEBYE_EINVAL;
   if (count) *count = h->launches;

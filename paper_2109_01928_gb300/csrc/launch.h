@@ -101,6 +101,10 @@ void launch_tab_nodes(int64_t S, const int32_t* qn0, const int32_t* nseg, const 
 void launch_tab_coef(int64_t S, const int32_t* qn0, const int32_t* nseg, const int64_t* seg0, const double* G,
                      const double* X, int64_t Qn, float2* coef, int sms, cudaStream_t st);
 void launch_tab_eval(const EvalArgs& a, bool grad, int sms, cudaStream_t st);
+// One block running the column-sum pass's bounded staging wait with nothing to wait
+// for (waitcheck.cu): it records DEBYE_ETIMEOUT after the wait's clock budget;
+// waited_ok (device, or nullptr) receives 0.
+void launch_stage_wait_check(int* status, int* waited_ok, cudaStream_t st);
 void launch_synth(int64_t S, const int64_t* offsets, const double* omega, const int32_t* model,
                   const double* params, const int64_t* pole_off, const double* ptau,
                   const double* pdeps, const double* nre, const double* nim, double* er, double* ei,

@@ -99,6 +99,7 @@ def lib() -> ctypes.CDLL:
     L.debye_fit_auto.argtypes = [_VP, ctypes.POINTER(SpectraC), ctypes.POINTER(SearchC), ctypes.c_int32,
                                  ctypes.c_double, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP]
     L.debye_sync.argtypes = [_VP, _VP]
+    L.debye_check_bounded_wait.argtypes = [_VP, _VP]
     L.debye_last_error.argtypes = [_VP]
     L.debye_last_error.restype = ctypes.c_char_p
     L.debye_version.restype = ctypes.c_char_p
@@ -113,7 +114,8 @@ def lib() -> ctypes.CDLL:
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     for f in ("debye_fit_init", "debye_fit_destroy", "debye_synth_targets", "debye_eval_population",
               "debye_cost_grad", "debye_fit_batch", "debye_sync", "debye_profile_enable",
-              "debye_profile_read", "debye_launch_count", "debye_autotune", "debye_eval_population_noalloc"):
+              "debye_profile_read", "debye_launch_count", "debye_autotune", "debye_eval_population_noalloc",
+              "debye_check_bounded_wait"):
         getattr(L, f).restype = _I
     _lib = L
     return L
@@ -335,6 +337,12 @@ def debye_fit_auto(h: Handle, sp: Spectra, P: int, iters: int, seed: int = 0, po
 
 def debye_sync(h: Handle, stream=None):
     h.check(lib().debye_sync(h.ptr, _stream(stream)))
+
+
+def debye_check_bounded_wait(h: Handle, stream=None):
+    """Enqueue the failure-path check of the bounded device waits: the next debye_sync
+    raises DebyeError with code DEBYE_ETIMEOUT (after about 1 s)."""
+    h.check(lib().debye_check_bounded_wait(h.ptr, _stream(stream)))
 
 
 KERNEL_KINDS = {"gram": 0, "refine": 1, "grad": 2, "solve": 3, "finish": 4, "gram_masked": 5,

@@ -413,6 +413,29 @@ def test_input_errors(D):
         assert c.shape == (0, 4)
 
 
+def test_bounded_wait_gives_up_and_context_survives(D):
+    # a staging wait with nothing to wait for (no copy issued): it gives up after its clock
+    # budget (about 1 s), the status word reports DEBYE_ETIMEOUT, and afterwards the same
+    # handle evaluates correctly
+    import time
+    with D.Handle("mixed") as h:
+        t0 = time.perf_counter()
+        D.debye_check_bounded_wait(h)
+        with pytest.raises(D.DebyeError) as e:
+            D.debye_sync(h)
+        dt = time.perf_counter() - t0
+        assert e.value.code == D.DEBYE_ETIMEOUT
+        assert 0.2 < dt < 30.0, dt
+        D.debye_sync(h)   # the status was cleared
+        b = W.mixed_batch(S=3, seed=5, P=32, K_range=(40, 120), N_range=(2, 5))
+        re, im = models.synthesize(b)
+        th = W.population(b, 32, seed=2)
+        cost = D.debye_eval_population(h, spectra_for(D, b, re, im), torch.as_tensor(th, device="cuda"))
+        D.debye_sync(h)
+    ref, _ = oracle_costs(b, re, im, th)
+    assert (np.abs(cost.cpu().numpy() - ref) / ref).max() <= COST_TOL["mixed"]
+
+
 # ------------------------------------------------------------------ gradient
 
 @pytest.mark.parametrize("prec,lanes", PREC_LANES)
