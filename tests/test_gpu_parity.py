@@ -688,6 +688,27 @@ def test_fit_auto_matches_oracle_and_is_wave_independent(D):
         assert (out["frac_err"][s].item() < 5.0) or N == b.n_poles[s]
 
 
+def test_fit_auto_table_precision_is_wave_independent(D):
+    # the automatic pole count with tabulated column sums: the same choices and results
+    # whether the pole counts are tried two at a time or all at once, every reported error
+    # below 5 % unless the cap is reached, and nothing beyond the chosen N
+    b = W.mixed_batch(S=4, seed=53, P=32, K_range=(60, 150), N_range=(2, 7))
+    re, im = models.synthesize(b)
+    sp = spectra_for(D, b, re, im)
+    with D.Handle("mixed_table") as h:
+        out = D.debye_fit_auto(h, sp, P=32, iters=20, seed=0, polish_topk=4, polish_iters=20, wave=2)
+        one = D.debye_fit_auto(h, sp, P=32, iters=20, seed=0, polish_topk=4, polish_iters=20, wave=20)
+        D.debye_sync(h)
+    nch = out["n_chosen"].cpu().numpy()
+    np.testing.assert_array_equal(nch, one["n_chosen"].cpu().numpy())
+    np.testing.assert_allclose(out["final_cost"].cpu().numpy(), one["final_cost"].cpu().numpy(), rtol=1e-12)
+    for s in range(b.S):
+        N = int(nch[s])
+        assert 1 <= N <= b.n_poles[s]
+        assert (out["frac_err"][s].item() < 5.0) or N == b.n_poles[s]
+        assert np.all(out["d_eps"][s, N:].cpu().numpy() == 0) and np.all(out["d_eps"][s, :N].cpu().numpy() >= 0)
+
+
 def test_fit_auto_single_debye_picks_one_pole(D):
     om = W.log_grid(1e6, 1e11, 120)
     e = models.multi_debye(om, 3.0, np.array([20.0]), np.array([1e-9]))
