@@ -109,14 +109,21 @@ __global__ void k_tab_coef(int64_t S, const int32_t* qn0, const int32_t* nseg, c
   }
 }
 
-// f(x) = sum_k a_k x^k for x in [-1, 1] by Horner's rule in float-float.
+// f(x) = sum_k a_k x^k for x in [-1, 1] by Horner's rule in float-float. The
+// coefficients are read two at a time (16-byte loads: every function's TAB_NC
+// coefficients start on a multiple of TAB_NC * 8 = 96 bytes from the allocation),
+// halving the load instructions, which bound this kernel on the L1 pipe.
+static_assert(TAB_NC % 2 == 0 && (TAB_NC * sizeof(float2)) % 16 == 0, "paired coefficient loads");
 __device__ __forceinline__ ff poly_ff(const float2* __restrict__ a, ff x) {
-  const float2 top = __ldg(a + TAB_NC - 1);
-  ff acc{top.x, top.y};
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  float4 c[TAB_NC / 2];
+#pragma unroll
+  for (int i = 0; i < TAB_NC / 2; ++i) c[i] = __ldg(a4 + i);
+  ff acc{c[TAB_NC / 2 - 1].z, c[TAB_NC / 2 - 1].w};
 #pragma unroll
   for (int k = TAB_NC - 2; k >= 0; --k) {
-    const float2 ak = __ldg(a + k);
-    acc = ff_sum(ff_prod(acc, x), ff{ak.x, ak.y});
+    const float4 q = c[k / 2];
+    acc = ff_sum(ff_prod(acc, x), (k & 1) ? ff{q.z, q.w} : ff{q.x, q.y});
   }
   return acc;
 }
