@@ -285,9 +285,10 @@ int debye_eval_population_noalloc(const debye_options* opt, const debye_spectra*
  * accepted points: times debye_cost_grad on the first min(P, 8) candidates of
  * every spectrum for (cb, lanes) in {(16,4), (8,8), (4,16), (2,32), (32,4),
  * (16,8), (8,16), (4,32)}. Each layout's evaluation is planned and uploaded
- * outside the timed interval and its launches timed alone (CUDA events), over a
- * warm-up and 5 rounds that interleave the layouts; the layout with the lowest
- * median time of each shape is kept for this handle and used
+ * outside the timed interval, 4 evaluations are captured in a CUDA graph (as a fit
+ * replays its generations) and one replay is timed (CUDA events), over a warm-up and
+ * 5 rounds that interleave the layouts; the layout with the lowest median time of
+ * each shape is kept for this handle and used
  * by later calls whose options leave cands_per_block and lanes_per_candidate at
  * 0. cache_path (may be NULL) is a text file of "key | cb lanes polish_cb
  * polish_lanes" lines keyed by the device's SM count, precision, S, P, n_max and

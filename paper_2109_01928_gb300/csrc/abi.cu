@@ -749,10 +749,13 @@ int debye_autotune(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n
     cudaGetLastError();
     return h->fail(DEBYE_ECUDA, "event creation failed");
   }
-  // Median device time of one evaluation per layout: every round plans each layout
-  // (host work and upload, outside the timed region), then times its launches alone
-  // between events; rounds interleave the layouts so that clock drift favours none.
-  constexpr int ROUNDS = 5;
+  // Median device time of an evaluation per layout, as a fit runs it: every round plans
+  // each layout (host work and upload, outside the timed region), captures REPS
+  // evaluations in a CUDA graph (the fit replays its generations from a graph) and
+  // times one replay between events; rounds interleave the layouts so that clock
+  // drift favours none. Measured on whole mixed_1024 fits, the graph replay ranks the
+  // layouts as the fits do, where single evaluations launched one by one did not.
+  constexpr int ROUNDS = 5, REPS = 4;
   auto tune = [&](const Layout* set, int n_set, int32_t Pe, const double* th, double* c, double* gr,
                   Layout* best) -> int {
     std::vector<float> t((size_t)n_set * ROUNDS, 0.f);
@@ -761,13 +764,32 @@ int debye_autotune(debye_handle h, const debye_spectra* sp, int32_t P, int32_t n
         EvalSetup es;
         int r = setup_eval(h, sp, Pe, n_max, th, c, nullptr, set[li], st, es);
         if (r) return r;
-        cudaEventRecord(e0, st);
-        if ((r = run_setup(h, es, c, nullptr, gr, st))) return r;
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) return h->fail(DEBYE_ECUDA, "autotune timing failed");
+        if ((r = run_setup(h, es, c, nullptr, gr, st))) return r;   // untimed: first launch of each kernel
+        // captured and replayed on the handle's own stream (the caller's may be the legacy
+        // default stream, which cannot be captured), ordered after the caller's work
+        const cudaStream_t ws = h->work_stream;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e = cudaEventRecord(h->ev_in, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ws, h->ev_in, 0);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(ws, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return h->fail(DEBYE_ECUDA, "autotune capture: %s", cudaGetErrorString(e));
+        h->capturing_stream = ws;
+        for (int k = 0; k < REPS && !r; ++k) r = run_setup(h, es, c, nullptr, gr, ws);
+        e = cudaStreamEndCapture(ws, &graph);
+        h->capturing_stream = nullptr;
+        if (!r && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (!r && e == cudaSuccess) e = cudaEventRecord(e0, ws);
+        if (!r && e == cudaSuccess) e = cudaGraphLaunch(exec, ws);
+        if (!r && e == cudaSuccess) e = cudaEventRecord(e1, ws);
+        if (!r && e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (r) return r;
+        if (e != cudaSuccess) return h->fail(DEBYE_ECUDA, "autotune timing: %s", cudaGetErrorString(e));
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (round >= 0) t[(size_t)li * ROUNDS + round] = ms;
+        if (round >= 0) t[(size_t)li * ROUNDS + round] = ms / REPS;
       }
     }
     float best_ms = 0.f;
